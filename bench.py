@@ -1,0 +1,406 @@
+#!/usr/bin/env python
+"""Throughput of one shape-fit step of the mesh-Fourier renderer on one B300.
+
+A step is one pass of the whole hot path on the single-cell workload (icosphere
+level 4 = 5120 triangles, SH l <= 6 deformation, 128^3 grid of (0.5, 0.5, 1) um
+voxels, Gaussian PSF sigma = (0.2, 0.2, 0.6) um, narrow band h_hat > 1e-3):
+narrow band, triangle records, mesh transform over every (band frequency,
+triangle) pair, transfer-function multiply, inverse 3D DFT, MSE loss and
+residual, forward 3D DFT of the residual, dL/dsigma, the adjoint mesh transform,
+per-vertex assembly, and the Adam update of the vertices.
+
+Metric: forward + backward (triangle x frequency) terms per second,
+2 * M * n_t / step time. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd tri*freq terms/s; served fits/s & p99 vs plain FP64 path at <=1e-4 err"
+UNIT = "terms/s"
+# Algorithmic work per (frequency, triangle) term on the FP32 pipe (lane operations) and on
+# the MUFU (sin/cos/rcp) pipe: evaluating Eq. 8 once (forward) and Eq. 8 + Eq. 10 with the
+# contraction into the per-triangle sums (adjoint).
+OPS_PER_TERM = {"fwd": 45, "adj": 110}
+MUFU_PER_TERM = {"fwd": 7, "adj": 7}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["c2", "c3", "c1", "c2s"], default="c2",
+                   help="c2: 128^3 single cell (default); c3: 256x256x128, 20480 triangles; c1: 32^3 icosphere; "
+                   "c2s: the c2 cell on a 64^3 grid of doubled voxels (small profiling case)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def make_case(name):
+    import synth
+
+    if name == "c2":
+        return synth.config_c2()
+    if name == "c3":
+        return synth.config_c3()
+    if name == "c2s":
+        c = synth.config_c2()
+        c.grid = synth.Grid(n=(64, 64, 64), h=(1.0, 1.0, 2.0))
+        c.name = "c2s_cell_sh6_64cube_profile"
+        return c
+    return synth.config_c1()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        return {
+            "sm_mhz": float(np.median(sm)) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons,
+            "samples": len(rows),
+        }
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+def oracle_sample(case, n_freq: int, seed: int = 0):
+    """A seeded random subset of the band (all triangles kept) for timing the CPU oracle."""
+    import oracle
+
+    nvec, _ = oracle.half_spectrum(case.grid.n)
+    xi_all = oracle.wavevectors(nvec, case.grid)
+    band = oracle.band_mask(oracle.otf(xi_all, case.psf), case.psf.band_tau)
+    idx = np.nonzero(band)[0]
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(idx, size=min(n_freq, len(idx)), replace=False))
+    G = (rng.normal(size=len(sel)) + 1j * rng.normal(size=len(sel))) / len(sel)
+    return xi_all[sel], G, int(band.sum())
+
+
+def time_oracle_step(case, xi, G):
+    import oracle
+
+    Vs = case.V_init - np.asarray(case.grid.origin)
+    t0 = time.perf_counter()
+    oracle.mesh_ft(Vs, case.F, xi)
+    oracle.mesh_ft_adjoint(Vs, case.F, xi, G)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(case, n_freq=16384):
+    import oracle
+
+    xi, G, _ = oracle_sample(case, n_freq)
+    dt = time_oracle_step(case, xi, G)
+    terms = 2.0 * len(xi) * case.F.shape[0]
+    return {
+        "value": terms / dt,
+        "unit": UNIT,
+        "cores": oracle.num_threads(),
+        "kind": "oracle",
+        "sample": f"FP64 oracle forward + adjoint on {len(xi)} seeded random band frequencies x all "
+        f"{case.F.shape[0]} triangles ({dt:.1f} s, OpenMP over frequencies/triangles)",
+    }
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    case = make_case(args.workload)
+    n_freq = 384
+    xi, G, M = oracle_sample(case, n_freq)
+    for _ in range(args.warmup):
+        time_oracle_step(case, xi, G)
+    total = 0.0
+    for _ in range(args.steps):
+        total += time_oracle_step(case, xi, G)
+    terms = 2.0 * len(xi) * case.F.shape[0] * args.steps
+    value = terms / total
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(case, M, "oracle step = sampled band frequencies x all triangles"),
+        "cpu_baseline": {
+            "value": value,
+            "unit": UNIT,
+            "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"each step: FP64 oracle forward + adjoint on {len(xi)} seeded random band frequencies x "
+            f"all {case.F.shape[0]} triangles",
+        },
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def workload_config(case, M, l2):
+    return {
+        "workload": case.name,
+        "grid": list(case.grid.n),
+        "voxel_um": list(case.grid.h),
+        "n_triangles": int(case.F.shape[0]),
+        "n_vertices": int(case.V_init.shape[0]),
+        "band_size": int(M),
+        "band_tau": case.psf.band_tau,
+        "psf_sigma_um": list(case.psf.sigma),
+        "loss": "mse",
+        "optimizer": "adam(vertices)",
+        "l2": l2,
+    }
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2303_10440_b300 import Renderer
+
+    case = make_case(args.workload)
+    grid, psf = case.grid, case.psf
+    r = Renderer("fp32", device=local)
+    M = len(r.band(grid, psf))
+    n_t = case.F.shape[0]
+    terms_step = 2.0 * M * n_t
+
+    Fd = torch.as_tensor(case.F).to(dev)
+    T = r.render(torch.as_tensor(case.V_true).to(dev), Fd, grid, psf)  # target: the deformed cell
+    Vd = torch.as_tensor(case.V_init).to(dev).clone()
+    dVd = torch.empty_like(Vd)
+    Ld = torch.empty(1, dtype=torch.float64, device=dev)
+    dpsfd = torch.empty(3, dtype=torch.float64, device=dev)
+    mom = torch.zeros_like(Vd)
+    vel = torch.zeros_like(Vd)
+    lr = 1e-2 * min(grid.h)
+    stream = torch.cuda.current_stream(dev)
+    step_no = [0]
+
+    def step():
+        r.loss_and_grad(Vd, Fd, grid, psf, T, "mse", L_out=Ld, dV_out=dVd, dpsf_out=dpsfd, stream=stream)
+        step_no[0] += 1
+        r.adam(Vd, dVd, mom, vel, step_no[0], lr, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    r.profile(True)
+    r.profile_read()
+    launches0 = r.kernel_launches()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict L2 between timed steps (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    launches = r.kernel_launches() - launches0
+    stages = r.profile_read()
+    r.profile(False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = world * terms_step * args.steps / (t_max / 1e3)
+
+    # roofline of the dominant kernel (event-timed inside the library on this stream)
+    dom = max(("fwd", "adj"), key=lambda s: stages[s][0])
+    dom_ms = stages[dom][0] / max(stages[dom][1], 1)
+    terms_launch = M * n_t
+    f_mhz = clk.get("sm_mhz") or 1920.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 128.0 * sms * f_mhz * 1e6 / 1e12  # FP32-pipe lane operations per second (Tops/s)
+    achieved = terms_launch * OPS_PER_TERM[dom] / (dom_ms / 1e3) / 1e12
+    roofline = {
+        "bound": "alu",
+        "kernel": "k_adj_f32" if dom == "adj" else "k_fwd_f32",
+        "achieved": achieved,
+        "peak": peak,
+        "unit": "Tops/s",
+        "frac": achieved / peak,
+        "traffic": None,
+        "ops_per_term": OPS_PER_TERM[dom],
+        "mufu_per_term": MUFU_PER_TERM[dom],
+        "terms_per_launch": terms_launch,
+        "launch_ms": dom_ms,
+        "peak_basis": f"128 FP32 lanes x {sms} SMs x median SM clock {f_mhz:.0f} MHz under load",
+        "fwd_terms_per_s": terms_launch / (stages["fwd"][0] / max(stages["fwd"][1], 1) / 1e3),
+        "adj_terms_per_s": terms_launch / (stages["adj"][0] / max(stages["adj"][1], 1) / 1e3),
+        "stage_ms_per_step": {k: v[0] / max(args.steps, 1) for k, v in stages.items() if v[1]},
+    }
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(case, M, "flushed (256 MB write) between timed steps, outside the events"),
+        "roofline": roofline,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = e2e_through_host_buffers(r, case, grid, psf, T, terms_step, args, dev, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(case)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def e2e_through_host_buffers(r, case, grid, psf, T_dev, terms_step, args, dev, world):
+    """Same metric through dm_loss_and_grad with pinned HOST buffers: every step copies the mesh
+    and the target image to the device and the loss, dL/dV and dL/dsigma back."""
+    import torch
+
+    Vh = torch.as_tensor(case.V_init).pin_memory()
+    Fh = torch.as_tensor(case.F).pin_memory()
+    Th = T_dev.cpu().pin_memory()
+    Lh = torch.empty(1, dtype=torch.float64).pin_memory()
+    dVh = torch.empty_like(Vh).pin_memory()
+    dph = torch.empty(3, dtype=torch.float64).pin_memory()
+    for _ in range(max(args.warmup, 1)):
+        r.loss_and_grad(Vh, Fh, grid, psf, Th, "mse", L_out=Lh, dV_out=dVh, dpsf_out=dph)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.loss_and_grad(Vh, Fh, grid, psf, Th, "mse", L_out=Lh, dV_out=dVh, dpsf_out=dph)
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    t = torch.tensor([dt], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    h2d = Vh.numel() * 8 + Fh.numel() * 4 + Th.numel() * 4
+    d2h = 8 + dVh.numel() * 8 + 3 * 8
+    return {
+        "value": world * terms_step * args.steps / float(t.item()),
+        "unit": UNIT,
+        "h2d_bytes_per_step": int(h2d),
+        "d2h_bytes_per_step": int(d2h),
+        "call": "dm_loss_and_grad (host V, F, target; host L, dV, dpsf)",
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

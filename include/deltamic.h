@@ -1,0 +1,220 @@
+/*
+ * deltamic.h — C ABI of the B300 (sm_103a) mesh-Fourier fluorescence renderer.
+ *
+ * The library renders a 3D fluorescence image from a triangle mesh and a
+ * Gaussian PSF entirely in Fourier space and differentiates it:
+ *
+ *   u_hat(xi)  = S(xi) / |Lambda|,   S(xi) = sum_T int_T exp(-i x.xi) dS        (Eq. 5, 7-8)
+ *   h_hat(xi)  = exp(-1/2 xi^T Sigma xi)                                        (Eq. 2)
+ *   I_j        = (1/(Lx Ly Lz)) sum_{n in band} c_n Re(u_hat h_hat exp(i xi_n.x_j)) (Eq. 1)
+ *   loss       = ||I - T||^2, its mean, or <(I - T)^2, T>                        (Sec. 5.1-5.2)
+ *   dL/dV, dL/dSigma                                                            (Eq. 6, 9-10)
+ *
+ * Paper: S. Ichbiah, A. Sinha, F. Delbary, H. Turlier, "Inverse 3D Microscopy
+ * Rendering for Cell Shape Inference with Active Mesh" (arXiv 2303.10440).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid: N = (Nx, Ny, Nz) voxels of size h; voxel j sits at origin + j*h; the
+ *   image is periodic with period L = N*h. Real images are C-ordered [x][y][z].
+ * Frequencies: xi_n = 2*pi*n/L (elementwise). The half spectrum H holds
+ *   n_x in fftfreq(Nx), n_y in fftfreq(Ny), n_z in 0..Nz/2, stored C-ordered as
+ *   [Nx][Ny][Nz/2+1] complex (index ix -> n_x = ix < (Nx+1)/2 ? ix : ix - Nx).
+ *   c_n = 1 on the planes n_z = 0 and (even Nz) n_z = Nz/2, else 2.
+ * Band: {n in H : h_hat(xi_n) > band_tau} (Sec. 5.1 narrow band); band_tau <= 0
+ *   selects all of H. Band entries are ordered by their index in H.
+ * Mesh: V[n_v][3] double, F[n_t][3] int32 (0-based), faces counter-clockwise
+ *   seen from outside. label 0 = surface-labelled (density on the triangles,
+ *   normalised by total area); label 1 = volume-labelled (uniform density inside
+ *   a closed mesh, normalised by enclosed volume).
+ * Precision (dm_options.precision): DM_FP64 computes everything in double and
+ *   uses double image buffers; DM_FP32_MIXED runs the (frequency, triangle) sums
+ *   in FP32 with exact integer phase reduction and compensated accumulation,
+ *   keeps reductions in FP64, and uses float image buffers.
+ * Memory: every pointer argument may be device memory or host memory; the
+ *   library tells them apart with cudaPointerGetAttributes. Host inputs are
+ *   copied to the context's workspace on the call's stream; host outputs are
+ *   written back and the stream is synchronised before the call returns.
+ *   The caller owns every buffer it passes; the library never frees them.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream). All device
+ *   work of a call is enqueued on it; device outputs are valid in stream order.
+ * Errors: calls return DM_OK (0) or a negative dm_status; dm_last_error() gives
+ *   a message. Faults detected on the device (a bad face index, a wait that
+ *   timed out) are reported by the next call that synchronises, or by dm_sync().
+ * Threads: a context is used by one host thread at a time.
+ */
+#ifndef DELTAMIC_H
+#define DELTAMIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dm_status;
+#define DM_OK 0
+#define DM_ERR_ARG (-1)         /* null pointer, size <= 0, NaN/Inf, sigma <= 0, index out of range */
+#define DM_ERR_OOM (-2)         /* device memory could not be reserved */
+#define DM_ERR_DEGENERATE (-3)  /* zero total area (surface) or non-positive volume (volume mode) */
+#define DM_ERR_OPEN_MESH (-4)   /* volume mode on a mesh that is not edge-manifold closed */
+#define DM_ERR_TIMEOUT (-5)     /* a bounded device-side wait expired */
+#define DM_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+#define DM_ERR_UNSUPPORTED (-7) /* grid axis longer than 1024 or with a prime factor > 5 */
+
+#define DM_FP64 0
+#define DM_FP32_MIXED 1
+
+#define DM_SURFACE 0
+#define DM_VOLUME 1
+
+#define DM_LOSS_L2 0       /* sum_j (I_j - T_j)^2                   (Sec. 5.2) */
+#define DM_LOSS_MSE 1      /* (1/N) sum_j (I_j - T_j)^2                        */
+#define DM_LOSS_WEIGHTED 2 /* sum_j T_j (I_j - T_j)^2               (Sec. 5.1) */
+
+#define DM_PSF_DIAG 0 /* Sigma = diag(sigma^2); gradient w.r.t. sigma[3]      */
+#define DM_PSF_FULL 1 /* Sigma from cov = (xx, yy, zz, xy, xz, yz); gradient w.r.t. cov[6] */
+
+typedef struct dm_ctx dm_ctx;
+
+typedef struct {
+    int32_t precision;     /* DM_FP64 or DM_FP32_MIXED */
+    int32_t device;        /* CUDA device ordinal */
+    int32_t deterministic; /* reductions are always deterministic; kept for ABI growth */
+    int32_t reserved;
+} dm_options;
+
+typedef struct {
+    int32_t n[3];      /* voxels per axis; each axis 1..1024 with prime factors 2, 3, 5 */
+    double h[3];       /* voxel size per axis (> 0) */
+    double origin[3];  /* position of voxel (0,0,0) */
+} dm_grid;
+
+typedef struct {
+    int32_t kind;      /* DM_PSF_DIAG or DM_PSF_FULL */
+    double sigma[3];   /* spatial standard deviations (kind DIAG), > 0 */
+    double cov[6];     /* spatial covariance (kind FULL), positive definite */
+    double band_tau;   /* narrow-band threshold on h_hat; <= 0 keeps the whole half spectrum */
+} dm_psf;
+
+typedef struct {
+    const double* V;          /* [n_v][3] vertex positions */
+    int64_t n_v;
+    const int32_t* F;         /* [n_t][3] 0-based vertex indices, CCW from outside */
+    int64_t n_t;
+    const float* tri_weight;  /* optional [n_t] fluorophore density per triangle (NULL = 1);
+                                 surface mode only (Sec. 3.3: interfaces carry density 2) */
+    int32_t label;            /* DM_SURFACE or DM_VOLUME */
+    int32_t reserved;
+} dm_mesh;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to opt->device. *ctx receives the handle. */
+dm_status dm_create(dm_ctx** ctx, const dm_options* opt);
+/* Release the context and its workspace. Safe on NULL. */
+dm_status dm_destroy(dm_ctx* ctx);
+/* Message describing the last failure of a call on ctx ("" if none). Owned by ctx. */
+const char* dm_last_error(const dm_ctx* ctx);
+/* Bytes of device workspace a loss_and_grad call needs for this grid and mesh size. */
+dm_status dm_workspace_size(const dm_ctx* ctx, const dm_grid* grid, int64_t n_v, int64_t n_t, size_t* bytes);
+/* Grow the workspace to at least `bytes` now (so later calls do not allocate). */
+dm_status dm_reserve(dm_ctx* ctx, size_t bytes);
+/* Synchronise `stream` and report any device-side fault recorded since the last check. */
+dm_status dm_sync(dm_ctx* ctx, void* stream);
+/* Number of this library's kernels launched since the library was loaded (instrumentation). */
+int64_t dm_kernel_launches(const dm_ctx* ctx);
+
+/* Stage timing (instrumentation). While enabled, every call records a CUDA event pair on its
+ * stream around each stage; dm_profile_read synchronises on them and returns, per stage,
+ * the accumulated milliseconds and the number of timed executions since the previous read. */
+#define DM_STAGE_PARAMS 0   /* PSF parameters to the device                 */
+#define DM_STAGE_PREP 1     /* triangle records and normaliser (Sec. 4.1.2) */
+#define DM_STAGE_BAND 2     /* narrow band (Sec. 5.1)                       */
+#define DM_STAGE_FWD 3      /* mesh transform sum (Eq. 5, 7-8)              */
+#define DM_STAGE_SCATTER 4  /* transfer-function multiply (Eq. 1-2)         */
+#define DM_STAGE_C2R 5      /* inverse real 3D DFT                          */
+#define DM_STAGE_LOSS 6     /* loss and residual (Sec. 5.1-5.2)             */
+#define DM_STAGE_R2C 7      /* forward real 3D DFT of the residual          */
+#define DM_STAGE_GATHER 8   /* adjoint records, dL/dpsf                     */
+#define DM_STAGE_ADJ 9      /* mesh transform adjoint sum (Eq. 9-10)        */
+#define DM_STAGE_REDUCE 10  /* per-chunk sums                               */
+#define DM_STAGE_ASSEMBLE 11 /* per-vertex gradient (Eq. 6)                 */
+#define DM_STAGE_ADAM 12    /* optimiser update                             */
+#define DM_NUM_STAGES 13
+dm_status dm_profile_enable(dm_ctx* ctx, int32_t enable);
+/* ms, calls: arrays of DM_NUM_STAGES (either may be NULL). */
+dm_status dm_profile_read(dm_ctx* ctx, double* ms, int64_t* calls);
+
+/* ---------------------------------------------------------------- stages */
+
+/* Narrow band (Sec. 5.1). Writes the band's indices into H (ordered) to idx_out
+ * (nullable; capacity Nx*Ny*(Nz/2+1)) and its size to *M_out (host). Synchronises. */
+dm_status dm_band(dm_ctx* ctx, const dm_psf* psf, const dm_grid* grid, int32_t* idx_out, int64_t* M_out, void* stream);
+
+/* Raw mesh spectrum at M integer frequencies (Eq. 5 numerator, Eq. 7-8):
+ *   S_m = sum_T w_T int_T exp(-i x'.xi_m) dS   (surface; w_T = tri_weight or 1)
+ *   S_m = int_V exp(-i x'.xi_m) dV            (volume)
+ * with x' = x - grid.origin and xi_m = 2 pi n_m / L. freq_n: [M][3] int32.
+ * S_out: [M] complex (interleaved re, im) in double (DM_FP64) or float. */
+dm_status dm_meshft(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* grid, const int32_t* freq_n, int64_t M,
+                    void* S_out, void* stream);
+
+/* Vertex adjoint of dm_meshft: dV[v] = sum_m Re(conj(G_m) dS_m/dv) (Eq. 9-10 summed per
+ * vertex, without the area quotient of Eq. 6). G: [M] complex (double or float, as S_out).
+ * dV_out: [n_v][3] double, overwritten. */
+dm_status dm_meshft_adjoint(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* grid, const int32_t* freq_n,
+                            int64_t M, const void* G, double* dV_out, void* stream);
+
+/* Unnormalised inverse real 3D DFT: out_j = sum_{n in H} c_n Re(spec_n exp(2 pi i n.j/N)).
+ * spec: [Nx][Ny][Nz/2+1] complex, image: [Nx][Ny][Nz] real (double or float). */
+dm_status dm_c2r(dm_ctx* ctx, const dm_grid* grid, const void* spec, void* image, void* stream);
+/* Unnormalised forward real 3D DFT onto H: spec_n = sum_j image_j exp(-2 pi i n.j/N). */
+dm_status dm_r2c(dm_ctx* ctx, const dm_grid* grid, const void* image, void* spec, void* stream);
+
+/* ---------------------------------------------------------------- renderer */
+
+/* Render the image (Eq. 1 via I_hat = u_hat h_hat) into image[Nx][Ny][Nz]. */
+dm_status dm_render(dm_ctx* ctx, const dm_mesh* mesh, const dm_psf* psf, const dm_grid* grid, void* image,
+                    void* stream);
+
+/* Render, compare with target[Nx][Ny][Nz] under `loss`, and differentiate.
+ * L (nullable): 1 double. dV (nullable): [n_v][3] double dL/dV.
+ * dpsf (nullable): 3 doubles dL/dsigma (DIAG) or 6 doubles dL/dcov (FULL).
+ * image_out (nullable): the rendered image. */
+dm_status dm_loss_and_grad(dm_ctx* ctx, const dm_mesh* mesh, const dm_psf* psf, const dm_grid* grid,
+                           const void* target, int32_t loss, double* L, double* dV, double* dpsf, void* image_out,
+                           void* stream);
+
+/* Adjoint of dm_render for a given dL/dI[Nx][Ny][Nz] (autograd backward): the spectrum
+ * is recomputed, not stored. dV, dpsf as in dm_loss_and_grad (nullable). */
+dm_status dm_render_adjoint(dm_ctx* ctx, const dm_mesh* mesh, const dm_psf* psf, const dm_grid* grid,
+                            const void* dL_dI, double* dV, double* dpsf, void* stream);
+
+/* ---------------------------------------------------------------- optimisation */
+
+/* One Adam step (Kingma & Ba) on n doubles, in place: m, v are the moment buffers
+ * (device, caller-owned, zero before step 1); step >= 1. */
+dm_status dm_adam(dm_ctx* ctx, double* param, const double* grad, double* m, double* v, int64_t n, double lr,
+                  double beta1, double beta2, double eps, int64_t step, void* stream);
+
+typedef struct {
+    int32_t steps;        /* Adam iterations */
+    int32_t loss;         /* DM_LOSS_* */
+    double lr_vertex;     /* Adam learning rate for vertex positions */
+    double lr_psf;        /* Adam learning rate for sigma (0 = keep the PSF fixed) */
+    double beta1, beta2, eps;
+} dm_fit_options;
+
+/* Fit vertices (and sigma when lr_psf > 0) to target by Adam, entirely on the device.
+ * V_io: [n_v][3] initial positions in, fitted positions out. psf_io->sigma updated in place
+ * (host struct). loss_history (nullable): [steps] doubles, the loss before each step. */
+dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
+                 const void* target, const dm_fit_options* opt, double* loss_history, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DELTAMIC_H */

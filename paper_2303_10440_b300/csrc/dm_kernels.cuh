@@ -1,0 +1,171 @@
+// Internal interface between the C ABI (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dm_common.cuh"
+
+namespace dm {
+
+// ---------------------------------------------------------------- records
+// Per-triangle record of the FP32 path (48 B; staged into shared memory in tiles).
+//   U   : fixed-point fraction of (v1 - origin)/L per axis (2^32 = one period), so the
+//         phase of vertex 1 at integer frequency n is 2 pi (n . U mod 2^32) / 2^32, exactly.
+//   e21 : v2 - v1,  e31 : v3 - v1   (physical units)
+//   w   : surface: (density * 2A, 0, 0);  volume: n_T = (v2 - v1) x (v3 - v1)
+struct __align__(16) TriF32 {
+    uint32_t U[3];
+    float e21x;
+    float e21y, e21z, e31x, e31y;
+    float e31z, w0, w1, w2;
+};
+static_assert(sizeof(TriF32) == 48, "TriF32 layout");
+
+// FP64 path: same fields, 64-bit fixed point and doubles (96 B).
+struct __align__(16) TriF64 {
+    uint64_t U[3];
+    double e21[3];
+    double e31[3];
+    double w[3];
+};
+static_assert(sizeof(TriF64) == 96, "TriF64 layout");
+
+// Per-frequency record of the adjoint: integer frequency, wavevector and the complex
+// weight Gw the per-triangle sums contract with (32 B FP32 / 64 B FP64).
+struct __align__(16) FreqF32 {
+    int32_t n[3];
+    float Gr;
+    float xi[3];
+    float Gi;
+};
+static_assert(sizeof(FreqF32) == 32, "FreqF32 layout");
+
+struct __align__(16) FreqF64 {
+    int32_t n[3];
+    int32_t pad;
+    double xi[3];
+    double Gr, Gi;
+    double pad2;
+};
+static_assert(sizeof(FreqF64) == 64, "FreqF64 layout");
+
+constexpr int FWD_TILE = 128;   // triangles per shared-memory tile (FP32 forward)
+constexpr int FWD_THREADS = 256;
+constexpr int ADJ_FTILE = 256;  // frequencies per shared-memory tile (FP32 adjoint)
+constexpr int ADJ_THREADS = 128;
+constexpr int F64_THREADS = 128;
+
+// Accumulators per triangle in the adjoint: surface {a, b1[3], b2[3], b3[3]};
+// volume {alpha[3], b1[3], b2[3], b3[3]}.
+constexpr int NACC_SURF = 10;
+constexpr int NACC_VOL = 12;
+
+// Frequency source for the forward transform: explicit triples, or band indices into H
+// (idx == nullptr means the identity band, m = index in H).
+struct FreqSrc {
+    const int32_t* nlist;  // [M][3] or nullptr
+    const int32_t* idx;    // [M] band indices or nullptr
+    const int64_t* dM;     // device band size (nullptr: use M)
+    int64_t M;             // host-side upper bound / exact size
+    int Nx, Ny, Nzh, Nz;
+};
+
+struct Geom {
+    double L[3];       // periods
+    double origin[3];  // grid origin
+};
+
+// ---------------------------------------------------------------- launchers (return cudaGetLastError())
+// Mesh transform (FP32 mixed path).
+cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const FreqSrc& fs, const Geom& g,
+                           const double* d_vol, float2* S, int* d_err, cudaStream_t st);
+cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_t_pad, const FreqF32* fr,
+                           const int64_t* dM, int64_t M_max, float* partial, int n_chunks, int* d_err, cudaStream_t st);
+int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count);
+
+// Mesh transform (FP64 plain path).
+cudaError_t launch_fwd_f64(int mode, const TriF64* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
+                           const double* d_vol, double2* S, cudaStream_t st);
+cudaError_t launch_adj_f64(int mode, const TriF64* tris, int64_t n_t, const FreqF64* fr, const int64_t* dM,
+                           int64_t M_max, double* partial, int n_chunks, cudaStream_t st);
+int adj_chunks_f64(int64_t n_t, int64_t M_max, int sm_count);
+
+// Triangle records and per-triangle normaliser (area*density or signed volume).
+template <class Rec>
+cudaError_t launch_tri_prep(int mode, const double* V, int64_t n_v, const int32_t* F, int64_t n_t, const float* wts,
+                            const Geom& g, Rec* rec, int64_t n_t_pad, double* norm_partial, int* n_blocks_out,
+                            int* d_err, cudaStream_t st);
+
+// Deterministic sum of `n` doubles into out[0] (one block).
+cudaError_t launch_sum(const double* x, int64_t n, int stride, int count, double* out, cudaStream_t st);
+
+// Narrow band: writes indices of H with h_hat > tau into idx (ordered), size into dM.
+cudaError_t launch_band(const double* d_psf, int psf_kind, double tau, int Nx, int Ny, int Nz, const Geom& g,
+                        int32_t* idx, int64_t* dM, int64_t* block_counts, cudaStream_t st);
+
+// spec[H] = 0 outside the band, S_m / norm * h_hat / (Lx Ly Lz) on it.
+template <class R>
+cudaError_t launch_scatter(const Cx<R>* S, const FreqSrc& fs, const double* d_psf, int psf_kind,
+                           const double* d_norm, const Geom& g, Cx<R>* spec, bool zero_first, cudaStream_t st);
+
+// Loss and residual; per-block FP64 partials of the loss.
+template <class R>
+cudaError_t launch_loss(const R* I, const R* T, int64_t n, int kind, R* resid, double* partial, int* n_blocks_out,
+                        cudaStream_t st);
+
+// After the forward real DFT of the residual: build adjoint frequency records (Gw), and
+// per-block partials of dL/dpsf (3 or 6) and of cq = sum Re(conj(Gu) u_hat).
+template <class R, class FR>
+cudaError_t launch_gather(int mode, const Cx<R>* spec, const Cx<R>* S, const FreqSrc& fs, const double* d_psf,
+                          int psf_kind, const double* d_norm, const Geom& g, FR* fr, int64_t M_pad, double* partial,
+                          int* n_blocks_out, cudaStream_t st);
+
+// Raw adjoint records from a caller's G on explicit frequencies (dm_meshft_adjoint).
+template <class R, class FR>
+cudaError_t launch_prep_raw(int mode, const Cx<R>* G, const int32_t* nlist, int64_t M, const Geom& g, FR* fr,
+                            int64_t M_pad, double* partial, int* n_blocks_out, cudaStream_t st);
+
+// Sum per-chunk partial accumulators: acc[t][k] = sum_c partial[c][k][t].
+template <class R>
+cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
+                                 cudaStream_t st);
+
+// Per-corner gradient contributions, then the per-vertex gather through the vertex star.
+cudaError_t launch_assemble(int mode, const double* V, const int32_t* F, int64_t n_t, int64_t n_v, const float* wts,
+                            const Geom& g, const double* acc, const double* d_coef, double* contrib, cudaStream_t st);
+cudaError_t launch_csr(const int32_t* F, int64_t n_t, int64_t n_v, int32_t* cnt, int32_t* ptr, int32_t* ent,
+                       int* d_err, cudaStream_t st);
+cudaError_t launch_vertex_gather(const int32_t* ptr, const int32_t* ent, const double* contrib, int64_t n_v,
+                                 double* dV, cudaStream_t st);
+
+// Adam update on n doubles.
+cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2,
+                        double eps, int64_t step, cudaStream_t st);
+cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1,
+                                 double b2, double eps, const int64_t* d_step, cudaStream_t st);
+
+// FFT (own radix-2/3/4/5 Stockham in shared memory).
+struct FFTAxis {
+    int N;
+    int nf;
+    int radix[16];
+    const void* tw;  // N twiddles exp(-2 pi i k / N), double2 or float2
+};
+template <class R>
+cudaError_t launch_c2r(const Cx<R>* spec_in, Cx<R>* work, R* out, int Nx, int Ny, int Nz, const FFTAxis* ax,
+                       cudaStream_t st);
+template <class R>
+cudaError_t launch_r2c(const R* in, Cx<R>* spec_out, int Nx, int Ny, int Nz, const FFTAxis* ax, cudaStream_t st);
+bool fft_factor(int N, FFTAxis& a);
+size_t fft_smem_bytes(int N, int elem_bytes);
+
+// Small helpers.
+cudaError_t launch_fill_zero_f64(double* p, int64_t n, cudaStream_t st);
+struct Params16 {
+    double v[16];
+};
+// Write up to 16 doubles passed by value into device memory (stream ordered, no host staging).
+cudaError_t launch_set_params(double* dst, Params16 p, int n, cudaStream_t st);
+
+}  // namespace dm

@@ -1,0 +1,696 @@
+// Stage kernels around the two mesh-transform sums: triangle records, narrow band,
+// transfer-function multiply, loss and residual, adjoint records, deterministic
+// reductions, per-vertex assembly (Eq. 6 quotient rule) and Adam.
+//
+// Every reduction here is a fixed-order tree in FP64 (no floating-point atomics),
+// so repeated runs are bitwise identical.
+#include <cmath>
+
+#include "dm_kernels.cuh"
+
+namespace dm {
+
+namespace {
+
+constexpr int NT = 256;
+
+// ---------------------------------------------------------------- triangle records
+__device__ __forceinline__ void fixed32(double u, uint32_t& U) {
+    u -= floor(u);
+    U = (uint32_t)(uint64_t)llrint(u * 4294967296.0);  // 2^32 wraps to 0
+}
+__device__ __forceinline__ void fixed64(double u, uint64_t& U) {
+    u -= floor(u);
+    const double s = u * 4294967296.0;
+    const double hi = floor(s);
+    const double lo = (s - hi) * 4294967296.0;
+    U = ((uint64_t)hi << 32) + (uint64_t)llrint(lo);
+}
+
+__device__ __forceinline__ void store_rec(TriF32& r, const double* v1, const double* e21, const double* e31,
+                                          const double* w, const Geom& g) {
+    for (int a = 0; a < 3; ++a) fixed32(v1[a] / g.L[a], r.U[a]);
+    r.e21x = (float)e21[0];
+    r.e21y = (float)e21[1];
+    r.e21z = (float)e21[2];
+    r.e31x = (float)e31[0];
+    r.e31y = (float)e31[1];
+    r.e31z = (float)e31[2];
+    r.w0 = (float)w[0];
+    r.w1 = (float)w[1];
+    r.w2 = (float)w[2];
+}
+__device__ __forceinline__ void store_rec(TriF64& r, const double* v1, const double* e21, const double* e31,
+                                          const double* w, const Geom& g) {
+    for (int a = 0; a < 3; ++a) {
+        fixed64(v1[a] / g.L[a], r.U[a]);
+        r.e21[a] = e21[a];
+        r.e31[a] = e31[a];
+        r.w[a] = w[a];
+    }
+}
+
+template <class Rec>
+__global__ void __launch_bounds__(NT) k_tri_prep(int mode, const double* __restrict__ V, int64_t n_v,
+                                                 const int32_t* __restrict__ F, int64_t n_t,
+                                                 const float* __restrict__ wts, Geom g, Rec* __restrict__ rec,
+                                                 int64_t n_t_pad, double* __restrict__ partial, int* err) {
+    __shared__ double scratch[32];
+    const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
+    double contrib = 0.0;
+    if (t < n_t_pad) {
+        Rec r;
+        memset(&r, 0, sizeof(Rec));
+        if (t < n_t) {
+            const int32_t i0 = F[3 * t], i1 = F[3 * t + 1], i2 = F[3 * t + 2];
+            const bool ok = i0 >= 0 && i0 < n_v && i1 >= 0 && i1 < n_v && i2 >= 0 && i2 < n_v;
+            if (!ok) {
+                atomicOr(err, ERR_BAD_INDEX);
+            } else {
+                double v[3][3];
+                bool fin = true;
+                for (int a = 0; a < 3; ++a) {
+                    v[0][a] = V[3 * (int64_t)i0 + a] - g.origin[a];
+                    v[1][a] = V[3 * (int64_t)i1 + a] - g.origin[a];
+                    v[2][a] = V[3 * (int64_t)i2 + a] - g.origin[a];
+                    fin = fin && isfinite(v[0][a]) && isfinite(v[1][a]) && isfinite(v[2][a]);
+                }
+                if (!fin) {
+                    atomicOr(err, ERR_NONFINITE);
+                } else {
+                    double e21[3], e31[3], n[3], w[3];
+                    for (int a = 0; a < 3; ++a) {
+                        e21[a] = v[1][a] - v[0][a];
+                        e31[a] = v[2][a] - v[0][a];
+                    }
+                    n[0] = e21[1] * e31[2] - e21[2] * e31[1];
+                    n[1] = e21[2] * e31[0] - e21[0] * e31[2];
+                    n[2] = e21[0] * e31[1] - e21[1] * e31[0];
+                    if (mode == 0) {
+                        const double A = 0.5 * sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                        const double rho = wts ? (double)wts[t] : 1.0;
+                        w[0] = 2.0 * A * rho;
+                        w[1] = w[2] = 0.0;
+                        contrib = rho * A;
+                    } else {
+                        w[0] = n[0];
+                        w[1] = n[1];
+                        w[2] = n[2];
+                        // signed volume of the cone from the origin: v1 . (v2 x v3) / 6
+                        contrib = (v[0][0] * (v[1][1] * v[2][2] - v[1][2] * v[2][1]) +
+                                   v[0][1] * (v[1][2] * v[2][0] - v[1][0] * v[2][2]) +
+                                   v[0][2] * (v[1][0] * v[2][1] - v[1][1] * v[2][0])) /
+                                  6.0;
+                    }
+                    store_rec(r, v[0], e21, e31, w, g);
+                }
+            }
+        }
+        rec[t] = r;
+    }
+    const double s = block_sum<NT>(contrib, scratch);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// out[k] = sum_{b < n} x[b * count + k]  (one block per k, fixed order)
+__global__ void __launch_bounds__(1024) k_sum(const double* __restrict__ x, int64_t n, int count,
+                                              double* __restrict__ out) {
+    __shared__ double scratch[32];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < n; b += 1024) s += x[b * count + k];
+    s = block_sum<1024>(s, scratch);
+    if (threadIdx.x == 0) out[k] = s;
+}
+
+// ---------------------------------------------------------------- narrow band
+__device__ __forceinline__ double otf_expo(const double* psf, int kind, double x, double y, double z) {
+    if (kind == 0) return psf[0] * psf[0] * x * x + psf[1] * psf[1] * y * y + psf[2] * psf[2] * z * z;
+    const double* c = psf + 3;  // xx, yy, zz, xy, xz, yz
+    return c[0] * x * x + c[1] * y * y + c[2] * z * z + 2.0 * (c[3] * x * y + c[4] * x * z + c[5] * y * z);
+}
+
+struct BandArgs {
+    const double* psf;
+    int kind;
+    double tau;
+    int Nx, Ny, Nz, Nzh;
+    double tp[3];
+    int64_t nH;
+};
+
+__device__ __forceinline__ bool in_band(const BandArgs& b, int64_t idx) {
+    int nx, ny, nz;
+    decode_h(idx, b.Nx, b.Ny, b.Nzh, nx, ny, nz);
+    const double e = otf_expo(b.psf, b.kind, nx * b.tp[0], ny * b.tp[1], nz * b.tp[2]);
+    return exp(-0.5 * e) > b.tau;
+}
+
+__global__ void __launch_bounds__(NT) k_band_count(BandArgs b, int64_t* __restrict__ counts) {
+    const int64_t idx = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int flag = idx < b.nH ? (int)in_band(b, idx) : 0;
+    const int c = __syncthreads_count(flag);
+    if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+// In-place exclusive scan of n int64 values (one block); total into *total.
+__global__ void __launch_bounds__(1024) k_scan_i64(int64_t* __restrict__ x, int64_t n, int64_t* __restrict__ total) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t b0 = threadIdx.x * per, b1 = min(b0 + per, n);
+    int64_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += x[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int64_t v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        if (total) *total = run;
+    }
+    __syncthreads();
+    int64_t run = part[threadIdx.x];
+    for (int64_t i = b0; i < b1; ++i) {
+        const int64_t v = x[i];
+        x[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_band_write(BandArgs b, const int64_t* __restrict__ offsets,
+                                                   int32_t* __restrict__ idx_out) {
+    __shared__ int warp_tot[NT / 32];
+    const int64_t idx = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const bool flag = idx < b.nH && in_band(b, idx);
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_tot[wid] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < wid; ++w) before += warp_tot[w];
+    before += __popc(bal & ((1u << lane) - 1u));
+    if (flag) idx_out[offsets[blockIdx.x] + before] = (int32_t)idx;
+}
+
+// ---------------------------------------------------------------- transfer function and image
+template <class R>
+__global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, FreqSrc fs, const double* __restrict__ psf,
+                                                int kind, const double* __restrict__ d_norm, double tpx, double tpy,
+                                                double tpz, double inv_VL, Cx<R>* __restrict__ spec) {
+    const int64_t M = fs.dM ? *fs.dM : fs.M;
+    const int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (m >= M) return;
+    const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
+    int nx, ny, nz;
+    decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, nx, ny, nz);
+    const double hh = exp(-0.5 * otf_expo(psf, kind, nx * tpx, ny * tpy, nz * tpz));
+    const R sc = (R)(hh * inv_VL / *d_norm);
+    const Cx<R> s = S[m];
+    spec[idx] = Cx<R>{s.x * sc, s.y * sc};
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* __restrict__ T, int64_t n, int kind,
+                                             R* __restrict__ resid, double* __restrict__ partial) {
+    __shared__ double scratch[32];
+    double l = 0.0;
+    const double inv_n = 1.0 / (double)n;
+    for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
+        const double d = (double)I[j] - (double)T[j];
+        double w = 1.0, s = 2.0;
+        if (kind == 1) s = 2.0 * inv_n;
+        if (kind == 2) w = (double)T[j];
+        l += w * d * d;
+        resid[j] = (R)(s * w * d);
+    }
+    if (kind == 1) l *= inv_n;
+    l = block_sum<NT>(l, scratch);
+    if (threadIdx.x == 0) partial[blockIdx.x] = l;
+}
+
+template <class R>
+__device__ __forceinline__ void set_rec(FreqF32& r, int nx, int ny, int nz, double x, double y, double z, double gr,
+                                        double gi) {
+    r.n[0] = nx;
+    r.n[1] = ny;
+    r.n[2] = nz;
+    r.xi[0] = (float)x;
+    r.xi[1] = (float)y;
+    r.xi[2] = (float)z;
+    r.Gr = (float)gr;
+    r.Gi = (float)gi;
+}
+template <class R>
+__device__ __forceinline__ void set_rec(FreqF64& r, int nx, int ny, int nz, double x, double y, double z, double gr,
+                                        double gi) {
+    r.n[0] = nx;
+    r.n[1] = ny;
+    r.n[2] = nz;
+    r.pad = 0;
+    r.xi[0] = x;
+    r.xi[1] = y;
+    r.xi[2] = z;
+    r.Gr = gr;
+    r.Gi = gi;
+    r.pad2 = 0.0;
+}
+
+// Partials per block: [0..5] dL/dpsf (3 used for kind DIAG), [6] coefficient of d(norm)/dv.
+constexpr int NPART = 8;
+
+template <class R, class FR>
+__global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ S,
+                                               FreqSrc fs, const double* __restrict__ psf, int kind,
+                                               const double* __restrict__ d_norm, double tpx, double tpy, double tpz,
+                                               double inv_VL, FR* __restrict__ fr, int64_t M_pad,
+                                               double* __restrict__ partial) {
+    __shared__ double scratch[32];
+    const int64_t M = fs.dM ? *fs.dM : fs.M;
+    const int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x;
+    double part[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (m < M) {
+        const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
+        int nx, ny, nz;
+        decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, nx, ny, nz);
+        const double x = nx * tpx, y = ny * tpy, z = nz * tpz;
+        const double c = (nz == 0 || 2 * nz == fs.Nz) ? 1.0 : 2.0;
+        const Cx<R> F = spec[idx];
+        const double Gx = c * inv_VL * (double)F.x, Gy = c * inv_VL * (double)F.y;  // dL/dX
+        const double hh = exp(-0.5 * otf_expo(psf, kind, x, y, z));
+        const double norm = *d_norm;
+        const double ux = (double)S[m].x / norm, uy = (double)S[m].y / norm;  // u_hat
+        const double g = (Gx * ux + Gy * uy) * hh;                              // Re(conj(G) X)
+        if (kind == 0) {
+            part[0] = -g * psf[0] * x * x;
+            part[1] = -g * psf[1] * y * y;
+            part[2] = -g * psf[2] * z * z;
+        } else {
+            part[0] = -0.5 * g * x * x;
+            part[1] = -0.5 * g * y * y;
+            part[2] = -0.5 * g * z * z;
+            part[3] = -g * x * y;
+            part[4] = -g * x * z;
+            part[5] = -g * y * z;
+        }
+        double Gur = Gx * hh / norm, Gui = Gy * hh / norm;  // dL/du_hat / norm
+        const bool zero = nx == 0 && ny == 0 && nz == 0;
+        if (zero) {
+            Gur = Gui = 0.0;  // u_hat(0) = 1 for every mesh: no gradient through xi = 0
+        } else {
+            part[6] = -(Gur * ux + Gui * uy);  // -cq
+        }
+        double wr = Gur, wi = Gui;
+        if (mode == 1 && !zero) {  // volume: Gw = -i Gu / |xi|^2
+            const double ik2 = 1.0 / (x * x + y * y + z * z);
+            wr = Gui * ik2;
+            wi = -Gur * ik2;
+        }
+        set_rec<R>(fr[m], nx, ny, nz, x, y, z, wr, wi);
+    } else if (m < M_pad) {
+        set_rec<R>(fr[m], 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
+    }
+    for (int k = 0; k < 7; ++k) {
+        const double s = block_sum<NT>(part[k], scratch);
+        if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = s;
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x * NPART + 7] = 0.0;
+}
+
+template <class R, class FR>
+__global__ void __launch_bounds__(NT) k_prep_raw(int mode, const Cx<R>* __restrict__ G, const int32_t* __restrict__ nl,
+                                                 int64_t M, double tpx, double tpy, double tpz, FR* __restrict__ fr,
+                                                 int64_t M_pad, double* __restrict__ partial) {
+    __shared__ double scratch[32];
+    const int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x;
+    double k0 = 0.0;
+    if (m < M) {
+        const int nx = nl[3 * m], ny = nl[3 * m + 1], nz = nl[3 * m + 2];
+        const double x = nx * tpx, y = ny * tpy, z = nz * tpz;
+        double wr = (double)G[m].x, wi = (double)G[m].y;
+        if (mode == 1) {
+            if (nx == 0 && ny == 0 && nz == 0) {
+                k0 = wr;  // S(0) = enclosed volume: its derivative goes through d(Vol)/dv
+                wr = wi = 0.0;
+            } else {
+                const double ik2 = 1.0 / (x * x + y * y + z * z);
+                const double tr = wi * ik2, ti = -wr * ik2;
+                wr = tr;
+                wi = ti;
+            }
+        }
+        set_rec<R>(fr[m], nx, ny, nz, x, y, z, wr, wi);
+    } else if (m < M_pad) {
+        set_rec<R>(fr[m], 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
+    }
+    const double s = block_sum<NT>(k0, scratch);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NPART; ++k) partial[blockIdx.x * NPART + k] = 0.0;
+        partial[blockIdx.x * NPART + 6] = s;
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(NT) k_reduce_chunks(const R* __restrict__ partial, int n_chunks, int nacc,
+                                                      int64_t n_t, int64_t n_t_pad, double* __restrict__ acc) {
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= n_t * nacc) return;
+    const int64_t t = i % n_t;
+    const int k = (int)(i / n_t);
+    double s = 0.0;
+    for (int c = 0; c < n_chunks; ++c) s += (double)partial[((int64_t)c * nacc + k) * n_t_pad + t];
+    acc[t * nacc + k] = s;
+}
+
+// ---------------------------------------------------------------- gradient assembly
+__device__ __forceinline__ void cross(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// contrib[t][p][3]: the corner (t, p) share of dL/dv_p (Eq. 6, 9).
+__global__ void __launch_bounds__(NT) k_assemble(int mode, const double* __restrict__ V, const int32_t* __restrict__ F,
+                                                 int64_t n_t, int64_t n_v, const float* __restrict__ wts, Geom g,
+                                                 const double* __restrict__ acc, const double* __restrict__ d_coef,
+                                                 double* __restrict__ contrib) {
+    const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (t >= n_t) return;
+    double out[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    int32_t id[3] = {F[3 * t], F[3 * t + 1], F[3 * t + 2]};
+    const bool ok = id[0] >= 0 && id[0] < n_v && id[1] >= 0 && id[1] < n_v && id[2] >= 0 && id[2] < n_v;
+    if (ok) {
+        double v[3][3];
+        for (int p = 0; p < 3; ++p)
+            for (int a = 0; a < 3; ++a) v[p][a] = V[3 * (int64_t)id[p] + a] - g.origin[a];
+        double e[3][3];  // e1 = v3 - v2, e2 = v1 - v3, e3 = v2 - v1
+        for (int a = 0; a < 3; ++a) {
+            e[0][a] = v[2][a] - v[1][a];
+            e[1][a] = v[0][a] - v[2][a];
+            e[2][a] = v[1][a] - v[0][a];
+        }
+        const double coef = *d_coef;
+        if (mode == 0) {
+            const int NA = NACC_SURF;
+            const double* ac = acc + t * NA;
+            double n[3];
+            cross(e[2], e[0], n);
+            const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            const double A = 0.5 * nn;
+            const double rho = wts ? (double)wts[t] : 1.0;
+            double N[3] = {0, 0, 0};
+            if (nn > 0)
+                for (int a = 0; a < 3; ++a) N[a] = n[a] / nn;
+            for (int p = 0; p < 3; ++p) {
+                double w[3] = {0, 0, 0};
+                if (nn > 0) cross(e[p], N, w);  // w_p = e_p x N
+                for (int a = 0; a < 3; ++a)
+                    out[p][a] = rho * (-w[a] * ac[0] + 2.0 * A * ac[1 + 3 * p + a]) + coef * (-0.5 * rho * w[a]);
+            }
+        } else {
+            const int NA = NACC_VOL;
+            const double* ac = acc + t * NA;
+            const double alpha[3] = {ac[0], ac[1], ac[2]};
+            for (int p = 0; p < 3; ++p) {
+                double ax[3], dvol[3];
+                cross(alpha, e[p], ax);
+                cross(v[(p + 1) % 3], v[(p + 2) % 3], dvol);
+                for (int a = 0; a < 3; ++a) out[p][a] = ax[a] + ac[3 + 3 * p + a] + coef * dvol[a] / 6.0;
+            }
+        }
+    }
+    for (int p = 0; p < 3; ++p)
+        for (int a = 0; a < 3; ++a) contrib[(3 * t + p) * 3 + a] = out[p][a];
+}
+
+__global__ void __launch_bounds__(NT) k_csr_count(const int32_t* __restrict__ F, int64_t n3, int64_t n_v,
+                                                  int32_t* __restrict__ cnt, int* err) {
+    const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= n3) return;
+    const int32_t v = F[e];
+    if (v >= 0 && v < n_v)
+        atomicAdd(&cnt[v], 1);
+    else
+        atomicOr(err, ERR_BAD_INDEX);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_i32(const int32_t* __restrict__ cnt, int64_t n,
+                                                   int32_t* __restrict__ ptr) {
+    __shared__ int32_t part[1024];
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t b0 = threadIdx.x * per, b1 = min(b0 + per, n);
+    int32_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int i = 0; i < 1024; ++i) {
+            const int32_t v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        ptr[n] = run;
+    }
+    __syncthreads();
+    int32_t run = part[threadIdx.x];
+    for (int64_t i = b0; i < b1; ++i) {
+        ptr[i] = run;
+        run += cnt[i];
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_csr_fill(const int32_t* __restrict__ F, int64_t n3, int64_t n_v,
+                                                 const int32_t* __restrict__ ptr, int32_t* __restrict__ cursor,
+                                                 int32_t* __restrict__ ent) {
+    const int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (e >= n3) return;
+    const int32_t v = F[e];
+    if (v < 0 || v >= n_v) return;
+    const int32_t pos = atomicAdd(&cursor[v], 1);
+    ent[ptr[v] + pos] = (int32_t)e;
+}
+
+// Sort each vertex's corner list so the per-vertex sum has a fixed order.
+__global__ void __launch_bounds__(NT) k_csr_sort(const int32_t* __restrict__ ptr, int64_t n_v, int32_t* __restrict__ ent) {
+    const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (v >= n_v) return;
+    const int32_t b = ptr[v], e = ptr[v + 1];
+    for (int32_t i = b + 1; i < e; ++i) {
+        const int32_t x = ent[i];
+        int32_t j = i - 1;
+        while (j >= b && ent[j] > x) {
+            ent[j + 1] = ent[j];
+            --j;
+        }
+        ent[j + 1] = x;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_vertex_gather(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+                                                      const double* __restrict__ contrib, int64_t n_v,
+                                                      double* __restrict__ dV) {
+    const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (v >= n_v) return;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int32_t i = ptr[v]; i < ptr[v + 1]; ++i) {
+        const int64_t c = (int64_t)ent[i] * 3;
+        s0 += contrib[c];
+        s1 += contrib[c + 1];
+        s2 += contrib[c + 2];
+    }
+    dV[3 * v] = s0;
+    dV[3 * v + 1] = s1;
+    dV[3 * v + 2] = s2;
+}
+
+// ---------------------------------------------------------------- Adam
+__global__ void __launch_bounds__(NT) k_adam(double* __restrict__ p, const double* __restrict__ g, double* __restrict__ m,
+                                             double* __restrict__ v, int64_t n, double lr, double b1, double b2,
+                                             double eps, int64_t step, const int64_t* __restrict__ d_step) {
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    const double t = (double)(d_step ? *d_step : step);
+    const double gi = g[i];
+    const double mi = b1 * m[i] + (1.0 - b1) * gi;
+    const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const double mh = mi / (1.0 - pow(b1, t));
+    const double vh = vi / (1.0 - pow(b2, t));
+    p[i] -= lr * mh / (sqrt(vh) + eps);
+}
+
+__global__ void k_set_params(double* dst, Params16 p, int n) {
+    if (threadIdx.x < n) dst[threadIdx.x] = p.v[threadIdx.x];
+}
+
+__global__ void k_zero_f64(double* p, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i < n) p[i] = 0.0;
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + NT - 1) / NT); }
+
+}  // namespace
+
+template <class Rec>
+cudaError_t launch_tri_prep(int mode, const double* V, int64_t n_v, const int32_t* F, int64_t n_t, const float* wts,
+                            const Geom& g, Rec* rec, int64_t n_t_pad, double* norm_partial, int* n_blocks_out,
+                            int* d_err, cudaStream_t st) {
+    const unsigned b = nblk(n_t_pad);
+    *n_blocks_out = (int)b;
+    k_tri_prep<Rec><<<b, NT, 0, st>>>(mode, V, n_v, F, n_t, wts, g, rec, n_t_pad, norm_partial, d_err);
+    return cudaGetLastError();
+}
+template cudaError_t launch_tri_prep<TriF32>(int, const double*, int64_t, const int32_t*, int64_t, const float*,
+                                             const Geom&, TriF32*, int64_t, double*, int*, int*, cudaStream_t);
+template cudaError_t launch_tri_prep<TriF64>(int, const double*, int64_t, const int32_t*, int64_t, const float*,
+                                             const Geom&, TriF64*, int64_t, double*, int*, int*, cudaStream_t);
+
+cudaError_t launch_sum(const double* x, int64_t n, int stride, int count, double* out, cudaStream_t st) {
+    (void)stride;
+    k_sum<<<count, 1024, 0, st>>>(x, n, count, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band(const double* d_psf, int psf_kind, double tau, int Nx, int Ny, int Nz, const Geom& g,
+                        int32_t* idx, int64_t* dM, int64_t* block_counts, cudaStream_t st) {
+    BandArgs b;
+    b.psf = d_psf;
+    b.kind = psf_kind;
+    b.tau = tau;
+    b.Nx = Nx;
+    b.Ny = Ny;
+    b.Nz = Nz;
+    b.Nzh = Nz / 2 + 1;
+    for (int a = 0; a < 3; ++a) b.tp[a] = 2.0 * M_PI / g.L[a];
+    b.nH = (int64_t)Nx * Ny * b.Nzh;
+    const unsigned nb = nblk(b.nH);
+    k_band_count<<<nb, NT, 0, st>>>(b, block_counts);
+    k_scan_i64<<<1, 1024, 0, st>>>(block_counts, nb, dM);
+    k_band_write<<<nb, NT, 0, st>>>(b, block_counts, idx);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_scatter(const Cx<R>* S, const FreqSrc& fs, const double* d_psf, int psf_kind, const double* d_norm,
+                           const Geom& g, Cx<R>* spec, bool zero_first, cudaStream_t st) {
+    const int64_t nH = (int64_t)fs.Nx * fs.Ny * fs.Nzh;
+    if (zero_first) {
+        cudaError_t e = cudaMemsetAsync(spec, 0, nH * sizeof(Cx<R>), st);
+        if (e != cudaSuccess) return e;
+    }
+    const double VL = g.L[0] * g.L[1] * g.L[2];
+    k_scatter<R><<<nblk(fs.M), NT, 0, st>>>(S, fs, d_psf, psf_kind, d_norm, 2.0 * M_PI / g.L[0], 2.0 * M_PI / g.L[1],
+                                            2.0 * M_PI / g.L[2], 1.0 / VL, spec);
+    return cudaGetLastError();
+}
+template cudaError_t launch_scatter<float>(const Cx<float>*, const FreqSrc&, const double*, int, const double*,
+                                           const Geom&, Cx<float>*, bool, cudaStream_t);
+template cudaError_t launch_scatter<double>(const Cx<double>*, const FreqSrc&, const double*, int, const double*,
+                                            const Geom&, Cx<double>*, bool, cudaStream_t);
+
+template <class R>
+cudaError_t launch_loss(const R* I, const R* T, int64_t n, int kind, R* resid, double* partial, int* n_blocks_out,
+                        cudaStream_t st) {
+    int64_t b = nblk(n);
+    if (b > 4096) b = 4096;
+    *n_blocks_out = (int)b;
+    k_loss<R><<<(unsigned)b, NT, 0, st>>>(I, T, n, kind, resid, partial);
+    return cudaGetLastError();
+}
+template cudaError_t launch_loss<float>(const float*, const float*, int64_t, int, float*, double*, int*, cudaStream_t);
+template cudaError_t launch_loss<double>(const double*, const double*, int64_t, int, double*, double*, int*,
+                                         cudaStream_t);
+
+template <class R, class FR>
+cudaError_t launch_gather(int mode, const Cx<R>* spec, const Cx<R>* S, const FreqSrc& fs, const double* d_psf,
+                          int psf_kind, const double* d_norm, const Geom& g, FR* fr, int64_t M_pad, double* partial,
+                          int* n_blocks_out, cudaStream_t st) {
+    const unsigned b = nblk(M_pad);
+    *n_blocks_out = (int)b;
+    const double VL = g.L[0] * g.L[1] * g.L[2];
+    k_gather<R, FR><<<b, NT, 0, st>>>(mode, spec, S, fs, d_psf, psf_kind, d_norm, 2.0 * M_PI / g.L[0],
+                                      2.0 * M_PI / g.L[1], 2.0 * M_PI / g.L[2], 1.0 / VL, fr, M_pad, partial);
+    return cudaGetLastError();
+}
+template cudaError_t launch_gather<float, FreqF32>(int, const Cx<float>*, const Cx<float>*, const FreqSrc&,
+                                                   const double*, int, const double*, const Geom&, FreqF32*, int64_t,
+                                                   double*, int*, cudaStream_t);
+template cudaError_t launch_gather<double, FreqF64>(int, const Cx<double>*, const Cx<double>*, const FreqSrc&,
+                                                    const double*, int, const double*, const Geom&, FreqF64*, int64_t,
+                                                    double*, int*, cudaStream_t);
+
+template <class R, class FR>
+cudaError_t launch_prep_raw(int mode, const Cx<R>* G, const int32_t* nlist, int64_t M, const Geom& g, FR* fr,
+                            int64_t M_pad, double* partial, int* n_blocks_out, cudaStream_t st) {
+    const unsigned b = nblk(M_pad);
+    *n_blocks_out = (int)b;
+    k_prep_raw<R, FR><<<b, NT, 0, st>>>(mode, G, nlist, M, 2.0 * M_PI / g.L[0], 2.0 * M_PI / g.L[1],
+                                        2.0 * M_PI / g.L[2], fr, M_pad, partial);
+    return cudaGetLastError();
+}
+template cudaError_t launch_prep_raw<float, FreqF32>(int, const Cx<float>*, const int32_t*, int64_t, const Geom&,
+                                                     FreqF32*, int64_t, double*, int*, cudaStream_t);
+template cudaError_t launch_prep_raw<double, FreqF64>(int, const Cx<double>*, const int32_t*, int64_t, const Geom&,
+                                                      FreqF64*, int64_t, double*, int*, cudaStream_t);
+
+template <class R>
+cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
+                                 cudaStream_t st) {
+    k_reduce_chunks<R><<<nblk(n_t * nacc), NT, 0, st>>>(partial, n_chunks, nacc, n_t, n_t_pad, acc);
+    return cudaGetLastError();
+}
+template cudaError_t launch_reduce_chunks<float>(const float*, int, int, int64_t, int64_t, double*, cudaStream_t);
+template cudaError_t launch_reduce_chunks<double>(const double*, int, int, int64_t, int64_t, double*, cudaStream_t);
+
+cudaError_t launch_assemble(int mode, const double* V, const int32_t* F, int64_t n_t, int64_t n_v, const float* wts,
+                            const Geom& g, const double* acc, const double* d_coef, double* contrib, cudaStream_t st) {
+    k_assemble<<<nblk(n_t), NT, 0, st>>>(mode, V, F, n_t, n_v, wts, g, acc, d_coef, contrib);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr(const int32_t* F, int64_t n_t, int64_t n_v, int32_t* cnt, int32_t* ptr, int32_t* ent,
+                       int* d_err, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(cnt, 0, n_v * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_csr_count<<<nblk(3 * n_t), NT, 0, st>>>(F, 3 * n_t, n_v, cnt, d_err);
+    k_scan_i32<<<1, 1024, 0, st>>>(cnt, n_v, ptr);
+    e = cudaMemsetAsync(cnt, 0, n_v * sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_csr_fill<<<nblk(3 * n_t), NT, 0, st>>>(F, 3 * n_t, n_v, ptr, cnt, ent);
+    k_csr_sort<<<nblk(n_v), NT, 0, st>>>(ptr, n_v, ent);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vertex_gather(const int32_t* ptr, const int32_t* ent, const double* contrib, int64_t n_v,
+                                 double* dV, cudaStream_t st) {
+    k_vertex_gather<<<nblk(n_v), NT, 0, st>>>(ptr, ent, contrib, n_v, dV);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2,
+                        double eps, int64_t step, cudaStream_t st) {
+    k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, step, nullptr);
+    return cudaGetLastError();
+}
+cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1,
+                                 double b2, double eps, const int64_t* d_step, cudaStream_t st) {
+    k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, 0, d_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_params(double* dst, Params16 p, int n, cudaStream_t st) {
+    k_set_params<<<1, 32, 0, st>>>(dst, p, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_zero_f64(double* p, int64_t n, cudaStream_t st) {
+    k_zero_f64<<<nblk(n), NT, 0, st>>>(p, n);
+    return cudaGetLastError();
+}
+
+}  // namespace dm

@@ -1,0 +1,240 @@
+"""CUDA path vs the FP64 CPU oracle, element by element, through the C ABI.
+
+Tolerances (the benchmark spec): relative L2 image error <= 1e-10 on the FP64 path and
+<= 1e-4 on the FP32 path; gradients <= 1e-3 relative L2 on the FP32 path. The
+FP64 path's gradients are held to 1e-9. Spectra are compared relative to their
+L2 norm and maximum (single small entries of a cancelling sum carry no relative
+accuracy in FP32).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@pytest.fixture(scope="module")
+def r64():
+    from paper_2303_10440_b300 import Renderer
+
+    r = Renderer("fp64")
+    yield r
+    r.close()
+
+
+@pytest.fixture(scope="module")
+def r32():
+    from paper_2303_10440_b300 import Renderer
+
+    r = Renderer("fp32")
+    yield r
+    r.close()
+
+
+def _cuda(x, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _meshes():
+    out = {}
+    out["sh_sphere"] = synth.sh_deformed_sphere(2, 6.0, (8.0, 7.5, 9.0), lmax=4, coef_sigma=0.6, seed=1)
+    out["box"] = synth.box_mesh((3.0, 4.0, 2.0), (11.0, 9.0, 14.0))  # edges on the axes: e.xi = 0 on grid
+    Vt, Ft = synth.random_triangles(40, seed=2, extent=6.0, center=(8, 8, 8))
+    out["soup"] = (Vt, Ft)
+    # slivers and tiny triangles
+    rng = np.random.default_rng(3)
+    V = []
+    for k in range(30):
+        a = rng.uniform(4, 12, 3)
+        d = rng.normal(size=3)
+        V += [a, a + d * 2.0, a + d * 2.0 + rng.normal(size=3) * (1e-4 if k % 2 else 1e-2)]
+    out["slivers"] = (np.array(V), np.arange(90, dtype=np.int32).reshape(30, 3))
+    return out
+
+
+GRID = synth.Grid(n=(16, 16, 16), h=(1.0, 1.0, 1.25), origin=(0.25, -0.5, 0.0))
+
+
+def _freqs(seed=0, M=300):
+    nvec, _ = oracle.half_spectrum(GRID.n)
+    rng = np.random.default_rng(seed)
+    sel = np.concatenate([[0], rng.choice(len(nvec), size=M - 1, replace=False)])
+    return nvec[sel].astype(np.int32)
+
+
+@pytest.mark.parametrize("name", ["sh_sphere", "box", "soup", "slivers"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_meshft_matches_oracle(name, prec, r64, r32):
+    V, F = _meshes()[name]
+    fn = _freqs()
+    xi = oracle.wavevectors(fn, GRID)
+    ref = oracle.mesh_ft(V - np.asarray(GRID.origin), F, xi)
+    r = r64 if prec == "fp64" else r32
+    S = r.meshft(_cuda(V), _cuda(F), GRID, _cuda(fn)).cpu().numpy()
+    tol = 1e-11 if prec == "fp64" else 2e-6
+    assert rel(S, ref) < tol
+    assert np.max(np.abs(S - ref)) < tol * 10 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_meshft_volume_matches_oracle(prec, r64, r32):
+    V, F = synth.sh_deformed_sphere(2, 5.0, (8.0, 8.0, 9.0), lmax=3, coef_sigma=0.4, seed=5)
+    fn = _freqs(1)
+    xi = oracle.wavevectors(fn, GRID)
+    ref = oracle.mesh_ft(V - np.asarray(GRID.origin), F, xi, "volume", c0=0.5 * GRID.L)
+    r = r64 if prec == "fp64" else r32
+    S = r.meshft(_cuda(V), _cuda(F), GRID, _cuda(fn), label="volume").cpu().numpy()
+    assert rel(S, ref) < (1e-11 if prec == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("label", ["surface", "volume"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_meshft_adjoint_matches_oracle(label, prec, r64, r32):
+    if label == "surface":
+        V, F = _meshes()["sh_sphere"]
+    else:
+        V, F = synth.sh_deformed_sphere(2, 5.0, (8.0, 8.0, 9.0), lmax=3, coef_sigma=0.4, seed=5)
+    fn = _freqs(2, M=200)
+    xi = oracle.wavevectors(fn, GRID)
+    rng = np.random.default_rng(9)
+    G = (rng.normal(size=len(fn)) + 1j * rng.normal(size=len(fn))) / np.sqrt(len(fn))
+    ref = oracle.mesh_ft_adjoint(V - np.asarray(GRID.origin), F, xi, G, label, c0=0.5 * GRID.L)
+    r = r64 if prec == "fp64" else r32
+    dV = r.meshft_adjoint(_cuda(V), _cuda(F), GRID, _cuda(fn), _cuda(G), label=label).cpu().numpy()
+    assert rel(dV, ref) < (1e-10 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("n", [(16, 16, 16), (12, 10, 9), (8, 6, 15), (32, 24, 20), (1, 4, 8), (96, 8, 6)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fft_matches_direct_definition(n, prec, r64, r32):
+    r = r64 if prec == "fp64" else r32
+    grid = synth.Grid(n=n, h=(1, 1, 1))
+    X = synth.random_half_spectrum(n, seed=4)
+    nvec, c = oracle.half_spectrum(n)
+    # oracle image definition times the box volume: unnormalised inverse on H with weights c
+    ref = oracle.spectrum_to_image(X.ravel(), nvec, c, grid) * np.prod(grid.L)
+    img = r.c2r(grid, torch.as_tensor(X).cuda()).cpu().numpy()
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert rel(img, ref) < tol
+    R = np.random.default_rng(5).normal(size=n)
+    refG = np.fft.fftn(R)[nvec[:, 0] % n[0], nvec[:, 1] % n[1], nvec[:, 2] % n[2]]
+    spec = r.r2c(grid, torch.as_tensor(R).cuda()).cpu().numpy().ravel()
+    assert rel(spec, refG) < tol
+
+
+@pytest.mark.parametrize("tau", [1e-3, 1e-2, 0.3])
+def test_band_is_bit_exact(tau, r64):
+    grid = synth.Grid(n=(24, 20, 16), h=(0.5, 0.5, 1.0))
+    psf = synth.Psf(sigma=(0.9, 1.2, 2.0), band_tau=tau)
+    nvec, _ = oracle.half_spectrum(grid.n)
+    mask = oracle.band_mask(oracle.otf(oracle.wavevectors(nvec, grid), psf), tau)
+    idx = r64.band(grid, psf).numpy()
+    assert np.array_equal(idx, np.nonzero(mask)[0].astype(np.int32))
+
+
+def _case_small(mode="surface", tau=0.0, n=(16, 12, 10)):
+    grid = synth.Grid(n=n, h=(1.0, 1.0, 1.5), origin=(0.5, -0.25, 1.0))
+    psf = synth.Psf(sigma=(0.8, 1.0, 1.4), band_tau=tau)
+    V, F = synth.sh_deformed_sphere(2, 4.0, grid.center, lmax=4, coef_sigma=0.4, seed=7)
+    Vt = synth.scale_about(V, (1.1, 0.9, 1.0), grid.center)
+    T = oracle.render(Vt, F, grid, psf, mode)["image"]
+    T = synth.add_gaussian_noise(T, 0.05, seed=0)
+    return grid, psf, V, F, T
+
+
+@pytest.mark.parametrize("mode", ["surface", "volume"])
+@pytest.mark.parametrize("tau", [0.0, 1e-2])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_render_matches_oracle(mode, tau, prec, r64, r32):
+    grid, psf, V, F, _ = _case_small(mode, tau)
+    ref = oracle.render(V, F, grid, psf, mode)["image"]
+    r = r64 if prec == "fp64" else r32
+    img = r.render(_cuda(V), _cuda(F), grid, psf, label=mode).cpu().numpy()
+    assert rel(img, ref) < (1e-10 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("kind", ["mse", "l2", "weighted"])
+@pytest.mark.parametrize("mode", ["surface", "volume"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_loss_and_grad_matches_oracle(kind, mode, prec, r64, r32):
+    grid, psf, V, F, T = _case_small(mode)
+    L0, dV0, dpsf0, _ = oracle.loss_and_grad(V, F, grid, psf, T, kind, mode)
+    r = r64 if prec == "fp64" else r32
+    L, dV, dpsf, img = r.loss_and_grad(_cuda(V), _cuda(F), grid, psf, _cuda(T), loss=kind, label=mode, want_image=True)
+    tl, tg = (1e-10, 1e-9) if prec == "fp64" else (2e-4, 1e-3)
+    assert abs(L - L0) <= tl * abs(L0)
+    assert rel(dV.cpu().numpy(), dV0) < tg
+    assert rel(dpsf.numpy(), dpsf0) < tg
+
+
+def test_case1_fp64_matches_oracle(r64):
+    case = synth.config_c1()
+    T = oracle.render(case.V_true, case.F, case.grid, case.psf)["image"]
+    T = synth.add_gaussian_noise(T, 0.05, seed=0)
+    L0, dV0, dpsf0, r0 = oracle.loss_and_grad(case.V_init, case.F, case.grid, case.psf, T, "mse")
+    L, dV, dpsf, img = r64.loss_and_grad(_cuda(case.V_init), _cuda(case.F), case.grid, case.psf, _cuda(T), "mse",
+                                         want_image=True)
+    assert rel(img.cpu().numpy(), r0["image"]) < 1e-10
+    assert abs(L - L0) < 1e-10 * L0
+    assert rel(dV.cpu().numpy(), dV0) < 1e-9
+    assert rel(dpsf.numpy(), dpsf0) < 1e-9
+
+
+def test_render_adjoint_is_the_loss_gradient(r64):
+    grid, psf, V, F, T = _case_small()
+    L, dV, dpsf, img = r64.loss_and_grad(_cuda(V), _cuda(F), grid, psf, _cuda(T), "l2", want_image=True)
+    dLdI = 2.0 * (img - _cuda(T))
+    dV2, dpsf2 = r64.render_adjoint(_cuda(V), _cuda(F), grid, psf, dLdI)
+    assert rel(dV2.cpu().numpy(), dV.cpu().numpy()) < 1e-12
+    assert rel(dpsf2.numpy(), dpsf.numpy()) < 1e-12
+
+
+def test_host_buffers_match_device_buffers(r32):
+    grid, psf, V, F, T = _case_small()
+    a = r32.loss_and_grad(_cuda(V), _cuda(F), grid, psf, _cuda(T), "mse")
+    b = r32.loss_and_grad(torch.as_tensor(V), torch.as_tensor(F), grid, psf, torch.as_tensor(T), "mse")
+    assert a[0] == b[0]
+    assert torch.equal(a[1].cpu(), b[1])
+
+
+def test_repeat_runs_are_bitwise_identical(r32):
+    case = synth.config_c2()
+    grid, psf = case.grid, case.psf
+    T = torch.zeros(tuple(grid.n), dtype=torch.float32, device="cuda")
+    Vd, Fd = _cuda(case.V_true), _cuda(case.F)
+    a = r32.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
+    b = r32.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
+    assert a[0] == b[0] and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+
+
+def test_argument_errors_are_reported(r32):
+    from paper_2303_10440_b300 import DeltaMicError
+
+    grid, psf, V, F, T = _case_small()
+    bad = F.copy()
+    bad[3, 1] = V.shape[0] + 5
+    with pytest.raises(DeltaMicError, match="DM_ERR_ARG"):
+        r32.render(torch.as_tensor(V), torch.as_tensor(bad), grid, psf)
+    with pytest.raises(DeltaMicError, match="DM_ERR_ARG"):
+        r32.render(_cuda(V), _cuda(F), grid, synth.Psf(sigma=(1.0, -1.0, 1.0)))
+    with pytest.raises(DeltaMicError, match="DM_ERR_UNSUPPORTED"):
+        r32.render(_cuda(V), _cuda(F), synth.Grid(n=(14, 14, 14), h=(1, 1, 1)), psf)
+    # an out-of-range index in device memory is caught by the kernels' bounds checks
+    with pytest.raises(DeltaMicError, match="DM_ERR_ARG"):
+        r32.loss_and_grad(_cuda(V), _cuda(bad), grid, psf, torch.as_tensor(T), "mse")
+    # the context stays usable afterwards
+    img = r32.render(_cuda(V), _cuda(F), grid, psf)
+    assert torch.isfinite(img).all()
