@@ -173,6 +173,24 @@ dm_status dm_c2r(dm_ctx* ctx, const dm_grid* grid, const void* spec, void* image
 /* Unnormalised forward real 3D DFT onto H: spec_n = sum_j image_j exp(-2 pi i n.j/N). */
 dm_status dm_r2c(dm_ctx* ctx, const dm_grid* grid, const void* image, void* spec, void* stream);
 
+/* Allocation-free variant of dm_meshft (FP32 mixed path). The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory after start-up (a server
+ * that reserves all of its memory up front, or a framework that owns every allocation through
+ * its own pool), since dm_meshft grows a context workspace with cudaMalloc. It takes no context
+ * and calls no allocating routine: its scratch (triangle records, partial sums, fault flags) is a
+ * file-scope device array of DM_NOALLOC_SCRATCH_BYTES per device, held until the process exits.
+ * Arguments as dm_meshft; S_out is [M] complex float. Every pointer must be device memory of
+ * the calling thread's current device. fault_flags (nullable, device int) receives 0, or bit 2
+ * for a face index outside [0, n_v), bit 4 for a non-finite vertex (stream ordered).
+ * Returns DM_ERR_ARG for NULL or host pointers, n_t > DM_NOALLOC_MAX_TRIANGLES or bad sizes;
+ * DM_ERR_CUDA if a launch fails. The first call on a device looks up the scratch address
+ * (once per device), so make it before any stream capture. All calls on a device share the
+ * scratch: calls that overlap on the GPU race and must be serialised by the caller. */
+#define DM_NOALLOC_MAX_TRIANGLES 65536
+#define DM_NOALLOC_SCRATCH_BYTES (4u << 20)
+dm_status dm_meshft_noalloc(const dm_mesh* mesh, const dm_grid* grid, const int32_t* freq_n, int64_t M, void* S_out,
+                            int32_t* fault_flags, void* stream);
+
 /* ---------------------------------------------------------------- renderer */
 
 /* Render the image (Eq. 1 via I_hat = u_hat h_hat) into image[Nx][Ny][Nz]. */

@@ -25,6 +25,7 @@ DM_FP64, DM_FP32_MIXED = 0, 1
 DM_SURFACE, DM_VOLUME = 0, 1
 LOSSES = {"l2": 0, "mse": 1, "weighted": 2}
 DM_PSF_DIAG, DM_PSF_FULL = 0, 1
+DM_NOALLOC_MAX_TRIANGLES = 65536
 STAGES = ("params", "prep", "band", "fwd", "scatter", "c2r", "loss", "r2c", "gather", "adj", "reduce", "assemble",
           "adam")
 
@@ -78,6 +79,7 @@ _SIGS = {
     "dm_band": (c_i32, [c_p, ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p, ctypes.POINTER(c_i64), c_p]),
     "dm_meshft": (c_i32, [c_p, ctypes.POINTER(dm_mesh), ctypes.POINTER(dm_grid), c_p, c_i64, c_p, c_p]),
     "dm_meshft_adjoint": (c_i32, [c_p, ctypes.POINTER(dm_mesh), ctypes.POINTER(dm_grid), c_p, c_i64, c_p, c_p, c_p]),
+    "dm_meshft_noalloc": (c_i32, [ctypes.POINTER(dm_mesh), ctypes.POINTER(dm_grid), c_p, c_i64, c_p, c_p, c_p]),
     "dm_c2r": (c_i32, [c_p, ctypes.POINTER(dm_grid), c_p, c_p, c_p]),
     "dm_r2c": (c_i32, [c_p, ctypes.POINTER(dm_grid), c_p, c_p, c_p]),
     "dm_render": (c_i32, [c_p, ctypes.POINTER(dm_mesh), ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p, c_p]),
