@@ -187,7 +187,7 @@ dm_status dm_r2c(dm_ctx* ctx, const dm_grid* grid, const void* image, void* spec
  * (once per device), so make it before any stream capture. All calls on a device share the
  * scratch: calls that overlap on the GPU race and must be serialised by the caller. */
 #define DM_NOALLOC_MAX_TRIANGLES 65536
-#define DM_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define DM_NOALLOC_SCRATCH_BYTES (8u << 20)
 dm_status dm_meshft_noalloc(const dm_mesh* mesh, const dm_grid* grid, const int32_t* freq_n, int64_t M, void* S_out,
                             int32_t* fault_flags, void* stream);
 

@@ -289,7 +289,7 @@ size_t layout(const Sizes& z, Arena& A, Bufs& b, bool stageV, bool stageF, bool 
     b.spec = A.take<char>(z.nH * 2 * R);
     b.image = A.take<char>(z.N * R);
     b.resid = A.take<char>(z.N * R);
-    b.fr = A.take<char>(z.M_pad * (z.f64 ? sizeof(FreqF64) : sizeof(FreqF32)));
+    b.fr = A.take<char>(z.M_pad * (z.f64 ? sizeof(FreqF64) : sizeof(FreqPairF32) / 2));
     b.adjp = A.take<char>((size_t)z.n_chunks * z.nacc * z.n_t_pad * R);
     b.acc = A.take<double>(z.n_t * z.nacc);
     b.contrib = A.take<double>(z.n_t * 9);
@@ -785,7 +785,7 @@ size_t raw_layout(const dm_ctx* ctx, int64_t n_v, int64_t n_t, int64_t M, int la
     b.nlist = A.take<int32_t>(3 * M);
     b.S = A.take<char>(M * 2 * R);
     b.G = A.take<char>(M * 2 * R);
-    b.fr = A.take<char>(M_pad * (f64 ? sizeof(FreqF64) : sizeof(FreqF32)));
+    b.fr = A.take<char>(M_pad * (f64 ? sizeof(FreqF64) : sizeof(FreqPairF32) / 2));
     b.adjp = A.take<char>((size_t)nc * nacc * n_t_pad * R);
     b.acc = A.take<double>(n_t * nacc);
     b.contrib = A.take<double>(9 * n_t);

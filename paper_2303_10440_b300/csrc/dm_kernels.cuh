@@ -9,18 +9,22 @@
 namespace dm {
 
 // ---------------------------------------------------------------- records
-// Per-triangle record of the FP32 path (48 B; staged into shared memory in tiles).
+// Per-triangle record of the FP32 path (96 B; staged into shared memory in tiles).
 //   U   : fixed-point fraction of (v1 - origin)/L per axis (2^32 = one period), so the
 //         phase of vertex 1 at integer frequency n is 2 pi (n . U mod 2^32) / 2^32, exactly.
 //   e21 : v2 - v1,  e31 : v3 - v1   (physical units)
 //   w   : surface: (density * 2A, 0, 0);  volume: n_T = (v2 - v1) x (v3 - v1)
+// Every float field is stored twice (x, x) so that two terms evaluated together with
+// paired FP32 instructions can use it as one 8-byte operand.
 struct __align__(16) TriF32 {
     uint32_t U[3];
-    float e21x;
-    float e21y, e21z, e31x, e31y;
-    float e31z, w0, w1, w2;
+    uint32_t pad;
+    float2 e21x, e21y, e21z;
+    float2 e31x, e31y, e31z;
+    float2 w0, w1, w2;
+    float2 pad2;
 };
-static_assert(sizeof(TriF32) == 48, "TriF32 layout");
+static_assert(sizeof(TriF32) == 96, "TriF32 layout");
 
 // FP64 path: same fields, 64-bit fixed point and doubles (96 B).
 struct __align__(16) TriF64 {
@@ -31,15 +35,17 @@ struct __align__(16) TriF64 {
 };
 static_assert(sizeof(TriF64) == 96, "TriF64 layout");
 
-// Per-frequency record of the adjoint: integer frequency, wavevector and the complex
-// weight Gw the per-triangle sums contract with (32 B FP32 / 64 B FP64).
-struct __align__(16) FreqF32 {
-    int32_t n[3];
-    float Gr;
-    float xi[3];
-    float Gi;
+// Adjoint records. FP32: two frequencies (lanes A, B) per 64 B record, so a thread evaluates
+// both against its triangle with paired FP32 instructions: integer frequencies, wavevectors and
+// the complex weight Gw the per-triangle sums contract with. FP64: one frequency per record.
+struct __align__(16) FreqPairF32 {
+    int32_t nA[3];
+    int32_t nB[3];
+    float2 x, y, z;   // (A, B)
+    float2 Gr, Gi;    // (A, B)
 };
-static_assert(sizeof(FreqF32) == 32, "FreqF32 layout");
+static_assert(sizeof(FreqPairF32) == 64, "FreqPairF32 layout");
+typedef FreqPairF32 FreqF32;  // the FP32 adjoint record type
 
 struct __align__(16) FreqF64 {
     int32_t n[3];
@@ -52,7 +58,7 @@ static_assert(sizeof(FreqF64) == 64, "FreqF64 layout");
 
 constexpr int FWD_TILE = 128;   // triangles per shared-memory tile (FP32 forward)
 constexpr int FWD_THREADS = 256;
-constexpr int ADJ_FTILE = 256;  // frequencies per shared-memory tile (FP32 adjoint)
+constexpr int ADJ_FTILE = 256;  // frequencies per shared-memory tile (FP32 adjoint; 128 pair records)
 constexpr int ADJ_THREADS = 128;
 constexpr int F64_THREADS = 128;
 

@@ -1,20 +1,30 @@
 // FP32 mixed-precision mesh Fourier transform (Eq. 5, 7-8) and its adjoint (Eq. 6, 9-10).
 //
-// Forward: one thread per band frequency, holding its integer frequency n and
-// wavevector xi in registers; the block walks the triangle list in tiles of
-// FWD_TILE records that a bulk (TMA) copy stages into shared memory, double
-// buffered on two mbarriers. Every thread reads the same record (broadcast).
-// Per term: exact phase of vertex 1 by integer arithmetic, two FP32 dot
-// products for the phase differences, the local divided difference
-// (meshft_math.cuh), three sincos and one reciprocal. Sums are FP32 within a
-// tile and compensated (Kahan) across tiles.
+// Both sums are bound by instruction issue, so each thread evaluates two
+// (frequency, triangle) terms at once ("lanes" A and B) with paired FP32
+// instructions (__ffma2_rn / __fadd2_rn / __fmul2_rn on float2 = (A, B)); MUFU
+// ops, comparisons and selects stay per lane.
 //
-// Adjoint: one thread per triangle (record in registers); the block walks a
-// chunk of the band in tiles of ADJ_FTILE frequency records staged the same
-// way. Each thread accumulates its triangle's 10 (surface) or 12 (volume) sums
-// over the chunk's frequencies in registers, so the reduction over frequencies
-// needs no inter-thread communication; chunks are summed afterwards in FP64 in
-// a fixed order (deterministic).
+// Per term, in the frame of the triangle's middle vertex (the one whose phase lies
+// between the other two): with the node gaps d1 = phi_m - phi_lo, d2 = phi_hi - phi_m,
+// s = d1 + d2, E(d) = (1 - e^{-id})/(id), q(d) = (E(d) - 1)/d, r(d) = -i E(d) - q(d):
+//   f_T          = e^{-i phi_m} i (E(d2) - conj E(d1)) / s                    (Eq. 8)
+//   df/dphi_lo   = e^{-i phi_m} (f_m + i conj r(d1)) / s
+//   df/dphi_mid  = e^{-i phi_m} i (q(d2) + conj q(d1)) / s                    (Eq. 10)
+//   df/dphi_hi   = e^{-i phi_m} (i r(d2) - f_m) / s
+// (f_m = i (E(d2) - conj E(d1)) / s). E and q switch to their Taylor series for
+// gaps below TG; terms whose three phases lie within TS of each other take the
+// series branch of meshft_math.cuh. phi_m = phi_1 + (phi_m - phi_1), where phi_1
+// comes from exact integer reduction (n . U mod 2^32) and the offset from the
+// FP32 edge projections.
+//
+// Forward: a thread holds two band frequencies in registers; the block walks the
+// triangle list in tiles bulk-copied (TMA) into shared memory, double buffered on
+// two mbarriers. FP32 sums within a tile, Kahan across tiles.
+// Adjoint: a thread holds one triangle; the block walks a chunk of the band in
+// tiles of frequency-pair records bulk-copied the same way, keeping the triangle's
+// 10 (surface) or 12 (volume) sums in registers; chunks are summed afterwards in
+// FP64 in a fixed order (deterministic).
 #include "dm_kernels.cuh"
 #include "meshft_math.cuh"
 
@@ -23,6 +33,32 @@ namespace dm {
 namespace {
 
 constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;  // 2 pi / 2^32
+constexpr float TS = MathCfg<float>::TS;
+constexpr float TG = MathCfg<float>::TG;
+
+typedef float2 F2;
+__device__ __forceinline__ F2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return __ffma2_rn(b, mk(-1.f, -1.f), a); }  // a - b
+__device__ __forceinline__ F2 fms2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, mk(-c.x, -c.y)); }  // a*b - c
+__device__ __forceinline__ F2 sel2(bool ca, bool cb, F2 t, F2 f) { return mk(ca ? t.x : f.x, cb ? t.y : f.y); }
+
+// Taylor polynomials pr(t), pi(t) of meshft_math.cuh (t = d^2) for a pair of gaps.
+__device__ __forceinline__ void taylor2(F2 t, F2& pr, F2& pi) {
+    pr = mk((float)inv_fact(9), (float)inv_fact(9));
+    pr = fma2(pr, t, mk(-(float)inv_fact(7), -(float)inv_fact(7)));
+    pr = fma2(pr, t, mk((float)inv_fact(5), (float)inv_fact(5)));
+    pr = fma2(pr, t, mk(-(float)inv_fact(3), -(float)inv_fact(3)));
+    pi = mk((float)inv_fact(10), (float)inv_fact(10));
+    pi = fma2(pi, t, mk(-(float)inv_fact(8), -(float)inv_fact(8)));
+    pi = fma2(pi, t, mk((float)inv_fact(6), (float)inv_fact(6)));
+    pi = fma2(pi, t, mk(-(float)inv_fact(4), -(float)inv_fact(4)));
+    pi = fma2(pi, t, mk((float)inv_fact(2), (float)inv_fact(2)));
+    pi = mk(-pi.x, -pi.y);
+}
+static_assert(MathCfg<float>::NPR == 4 && MathCfg<float>::NPI == 5, "taylor2 is written for these orders");
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     const float y = v - c;
@@ -31,6 +67,70 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     s = t;
 }
 
+// Node ordering of (0, a, b) for one lane: lo, mid, hi and the vertex-identity flags.
+struct Order {
+    float lo, mid, hi;
+    bool lo1, hi1, ab;  // vertex 1 is lowest / highest; a <= b
+};
+__device__ __forceinline__ Order order3(float a, float b) {
+    Order o;
+    const float mn = fminf(a, b), mx = fmaxf(a, b);
+    o.lo = fminf(mn, 0.f);
+    o.hi = fmaxf(mx, 0.f);
+    o.mid = fmaxf(mn, fminf(mx, 0.f));
+    o.lo1 = 0.f <= mn;
+    o.hi1 = mx <= 0.f;
+    o.ab = a <= b;
+    return o;
+}
+
+// Gap functions for both lanes of both gaps: E(d1), E(d2) and (adjoint) q(d1), q(d2).
+template <bool ADJ>
+struct Gaps {
+    F2 E1x, E1y, E2x, E2y;
+    F2 q1x, q1y, q2x, q2y;
+    F2 invs;
+};
+template <bool ADJ>
+__device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
+    float s1a, c1a, s1b, c1b, s2a, c2a, s2b, c2b;
+    __sincosf(d1.x, &s1a, &c1a);
+    __sincosf(d1.y, &s1b, &c1b);
+    __sincosf(d2.x, &s2a, &c2a);
+    __sincosf(d2.y, &s2b, &c2b);
+    const bool m1a = d1.x < TG, m1b = d1.y < TG, m2a = d2.x < TG, m2b = d2.y < TG;
+    const F2 d1c = mk(m1a ? 1.f : d1.x, m1b ? 1.f : d1.y);
+    const F2 d2c = mk(m2a ? 1.f : d2.x, m2b ? 1.f : d2.y);
+    const F2 t12 = mul2(d1c, d2c);
+    const F2 prod = mul2(t12, s);
+    const F2 r = mk(__fdividef(1.f, prod.x), __fdividef(1.f, prod.y));
+    const F2 rs = mul2(r, s);
+    const F2 inv1 = mul2(rs, d2c), inv2 = mul2(rs, d1c);
+    g.invs = mul2(r, t12);
+    const F2 t1 = mul2(d1, d1), t2 = mul2(d2, d2);
+    F2 pr1, pi1, pr2, pi2;
+    taylor2(t1, pr1, pi1);
+    taylor2(t2, pr2, pi2);
+    const F2 one = mk(1.f, 1.f), mone = mk(-1.f, -1.f);
+    // direct: E = sin d / d - i (1 - cos d) / d ; Taylor: E = 1 + d^2 pr - i... (Im E = d pi)
+    const F2 E1xd = mul2(mk(s1a, s1b), inv1), E1yd = mul2(add2(mk(c1a, c1b), mone), inv1);
+    const F2 E2xd = mul2(mk(s2a, s2b), inv2), E2yd = mul2(add2(mk(c2a, c2b), mone), inv2);
+    const F2 E1xt = fma2(t1, pr1, one), E1yt = mul2(d1, pi1);
+    const F2 E2xt = fma2(t2, pr2, one), E2yt = mul2(d2, pi2);
+    g.E1x = sel2(m1a, m1b, E1xt, E1xd);
+    g.E1y = sel2(m1a, m1b, E1yt, E1yd);
+    g.E2x = sel2(m2a, m2b, E2xt, E2xd);
+    g.E2y = sel2(m2a, m2b, E2yt, E2yd);
+    if (ADJ) {
+        // q = (E - 1)/d (direct) ; Re q = d pr, Im q = pi (Taylor)
+        g.q1x = sel2(m1a, m1b, mul2(d1, pr1), mul2(add2(g.E1x, mone), inv1));
+        g.q1y = sel2(m1a, m1b, pi1, mul2(g.E1y, inv1));
+        g.q2x = sel2(m2a, m2b, mul2(d2, pr2), mul2(add2(g.E2x, mone), inv2));
+        g.q2y = sel2(m2a, m2b, pi2, mul2(g.E2y, inv2));
+    }
+}
+
+// ------------------------------------------------------------------------------------- forward
 template <int MODE, bool EXPLICIT>
 __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, FreqSrc fs,
                                                          float tpx, float tpy, float tpz,
@@ -38,25 +138,33 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
                                                          int* __restrict__ err) {
     __shared__ __align__(128) TriF32 tile[2][FWD_TILE];
     __shared__ __align__(8) uint64_t bar[2];
+    constexpr int PER_BLOCK = 2 * FWD_THREADS;
     const int tid = threadIdx.x;
     const int64_t M = fs.dM ? *fs.dM : fs.M;
-    if ((int64_t)blockIdx.x * FWD_THREADS >= M) return;  // whole block beyond the band (uniform)
-    const int64_t m = (int64_t)blockIdx.x * FWD_THREADS + tid;
-    const bool active = m < M;
+    if ((int64_t)blockIdx.x * PER_BLOCK >= M) return;  // whole block beyond the band (uniform)
+    const int64_t m0 = (int64_t)blockIdx.x * PER_BLOCK + 2 * tid;
+    const bool actA = m0 < M, actB = m0 + 1 < M;
 
-    int nx = 0, ny = 0, nz = 0;
-    if (active) {
-        if (EXPLICIT) {
-            nx = fs.nlist[3 * m];
-            ny = fs.nlist[3 * m + 1];
-            nz = fs.nlist[3 * m + 2];
-        } else {
-            const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
-            decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, nx, ny, nz);
+    int n[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+        const int64_t m = m0 + l;
+        if (m < M) {
+            if (EXPLICIT) {
+                n[l][0] = fs.nlist[3 * m];
+                n[l][1] = fs.nlist[3 * m + 1];
+                n[l][2] = fs.nlist[3 * m + 2];
+            } else {
+                const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
+                decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, n[l][0], n[l][1], n[l][2]);
+            }
         }
     }
-    const float xx = (float)nx * tpx, xy = (float)ny * tpy, xz = (float)nz * tpz;
-    const uint32_t unx = (uint32_t)nx, uny = (uint32_t)ny, unz = (uint32_t)nz;
+    const F2 X = mk((float)n[0][0] * tpx, (float)n[1][0] * tpx);
+    const F2 Y = mk((float)n[0][1] * tpy, (float)n[1][1] * tpy);
+    const F2 Z = mk((float)n[0][2] * tpz, (float)n[1][2] * tpz);
+    const uint32_t uA0 = (uint32_t)n[0][0], uA1 = (uint32_t)n[0][1], uA2 = (uint32_t)n[0][2];
+    const uint32_t uB0 = (uint32_t)n[1][0], uB1 = (uint32_t)n[1][1], uB2 = (uint32_t)n[1][2];
 
     constexpr uint32_t kTileBytes = FWD_TILE * sizeof(TriF32);
     if (tid == 0) {
@@ -70,7 +178,7 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
         bulk_g2s(&tile[0][0], tris, kTileBytes, &bar[0]);
     }
 
-    float accx = 0.f, accy = 0.f, cx = 0.f, cy = 0.f;
+    F2 SX = mk(0.f, 0.f), SY = mk(0.f, 0.f), CX = mk(0.f, 0.f), CY = mk(0.f, 0.f);
     for (int t = 0; t < n_tiles; ++t) {
         const int st = t & 1;
         if (tid == 0 && t + 1 < n_tiles) {
@@ -87,53 +195,94 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
             }
             return;
         }
-        float px = 0.f, py = 0.f;
-#pragma unroll 2
+        F2 PX = mk(0.f, 0.f), PY = mk(0.f, 0.f);
+#pragma unroll 1
         for (int j = 0; j < FWD_TILE; ++j) {
             const TriF32& T = tile[st][j];
-            const uint32_t P = unx * T.U[0] + uny * T.U[1] + unz * T.U[2];
-            const float ph = (float)(int32_t)P * kTwoPiOver2p32;
-            const float a = xx * T.e21x + xy * T.e21y + xz * T.e21z;
-            const float b = xx * T.e31x + xy * T.e31y + xz * T.e31z;
-            TriLocal<float, false> o;
-            tri_local<float, false>(a, b, o);
-            float sp, cp;
-            __sincosf(ph, &sp, &cp);
-            const Cx<float> r = cmul(Cx<float>{cp, -sp}, o.rho);
-            const Cx<float> f = cmul(r, o.f);
-            const float w = MODE == 0 ? T.w0 : xx * T.w0 + xy * T.w1 + xz * T.w2;
-            px += w * f.x;
-            py += w * f.y;
+            const uint32_t PA = uA0 * T.U[0] + uA1 * T.U[1] + uA2 * T.U[2];
+            const uint32_t PB = uB0 * T.U[0] + uB1 * T.U[1] + uB2 * T.U[2];
+            const F2 ph = mul2(mk((float)(int32_t)PA, (float)(int32_t)PB), mk(kTwoPiOver2p32, kTwoPiOver2p32));
+            const F2 a = fma2(Z, T.e21z, fma2(Y, T.e21y, mul2(X, T.e21x)));
+            const F2 b = fma2(Z, T.e31z, fma2(Y, T.e31y, mul2(X, T.e31x)));
+            const F2 w = MODE == 0 ? T.w0 : fma2(Z, T.w2, fma2(Y, T.w1, mul2(X, T.w0)));
+            const Order oA = order3(a.x, b.x), oB = order3(a.y, b.y);
+            const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
+            const F2 s = sub2(hi, lo);
+            if (s.x < TS || s.y < TS) {
+                // near-degenerate: evaluate each lane with the series branch (rare)
+                const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y}, ww[2] = {w.x, w.y};
+                float fx[2], fy[2];
+#pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    TriLocal<float, false> o;
+                    tri_local<float, false>(aa[l], bb[l], o);
+                    float sp, cp;
+                    __sincosf(pp[l], &sp, &cp);
+                    const Cx<float> f = cmul(cmul(Cx<float>{cp, -sp}, o.rho), o.f);
+                    fx[l] = ww[l] * f.x;
+                    fy[l] = ww[l] * f.y;
+                }
+                PX = add2(PX, mk(fx[0], fx[1]));
+                PY = add2(PY, mk(fy[0], fy[1]));
+                continue;
+            }
+            const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
+            const F2 phm = add2(ph, mid);
+            Gaps<false> g;
+            gaps2<false>(d1, d2, s, g);
+            float sma, cma, smb, cmb;
+            __sincosf(phm.x, &sma, &cma);
+            __sincosf(phm.y, &smb, &cmb);
+            const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
+            // f = (cm - i sm) (-gy + i gx) invs, gx = E2x - E1x, gy = E2y + E1y
+            const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
+            const F2 fx = fms2(sm, gx, mul2(cm, gy));
+            const F2 fy = fma2(cm, gx, mul2(sm, gy));
+            const F2 we = mul2(w, g.invs);
+            PX = fma2(we, fx, PX);
+            PY = fma2(we, fy, PY);
         }
-        kahan_add(accx, cx, px);
-        kahan_add(accy, cy, py);
+        kahan_add(SX.x, CX.x, PX.x);
+        kahan_add(SX.y, CX.y, PX.y);
+        kahan_add(SY.x, CY.x, PY.x);
+        kahan_add(SY.y, CY.y, PY.y);
         __syncthreads();
     }
-    if (!active) return;
+    float sx[2] = {SX.x, SX.y}, sy[2] = {SY.x, SY.y};
     if (MODE == 1) {
         // volume: S = (i / |xi|^2) sum_T (xi . n_T) f_T, and the enclosed volume at xi = 0
-        const float k2 = xx * xx + xy * xy + xz * xz;
-        if (nx == 0 && ny == 0 && nz == 0) {
-            accx = (float)*d_vol;
-            accy = 0.f;
-        } else {
-            const float ik2 = 1.0f / k2;
-            const float tx = -accy * ik2, ty = accx * ik2;
-            accx = tx;
-            accy = ty;
+        const float xs[2] = {X.x, X.y}, ys[2] = {Y.x, Y.y}, zs[2] = {Z.x, Z.y};
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            if (n[l][0] == 0 && n[l][1] == 0 && n[l][2] == 0) {
+                sx[l] = (float)*d_vol;
+                sy[l] = 0.f;
+            } else {
+                const float ik2 = 1.0f / (xs[l] * xs[l] + ys[l] * ys[l] + zs[l] * zs[l]);
+                const float tx = -sy[l] * ik2, ty = sx[l] * ik2;
+                sx[l] = tx;
+                sy[l] = ty;
+            }
         }
     }
-    S[m] = make_float2(accx, accy);
+    if (actA && actB && (reinterpret_cast<uintptr_t>(S + m0) & 15) == 0) {
+        *reinterpret_cast<float4*>(S + m0) = make_float4(sx[0], sy[0], sx[1], sy[1]);
+    } else {
+        if (actA) S[m0] = make_float2(sx[0], sy[0]);
+        if (actB) S[m0 + 1] = make_float2(sx[1], sy[1]);
+    }
 }
 
+// ------------------------------------------------------------------------------------- adjoint
 template <int MODE>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restrict__ tris, int64_t n_t,
-                                                         int64_t n_t_pad, const FreqF32* __restrict__ fr,
+                                                         int64_t n_t_pad, const FreqPairF32* __restrict__ fr,
                                                          const int64_t* __restrict__ dM, int64_t M_max,
                                                          int tiles_per_chunk, float* __restrict__ partial,
                                                          int* __restrict__ err) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
-    __shared__ __align__(128) FreqF32 tile[2][ADJ_FTILE];
+    constexpr int PAIRS = ADJ_FTILE / 2;
+    __shared__ __align__(128) FreqPairF32 tile[2][PAIRS];
     __shared__ __align__(8) uint64_t bar[2];
     const int tid = threadIdx.x;
     const int64_t t = (int64_t)blockIdx.x * ADJ_THREADS + tid;
@@ -148,7 +297,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     for (int k = 0; k < NACC; ++k) tot[k] = comp[k] = 0.f;
 
     if (f1 > f0) {
-        constexpr uint32_t kTileBytes = ADJ_FTILE * sizeof(FreqF32);
+        constexpr uint32_t kTileBytes = PAIRS * sizeof(FreqPairF32);
         if (tid == 0) {
             mbar_init(&bar[0], 1);
             mbar_init(&bar[1], 1);
@@ -157,7 +306,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
         __syncthreads();
         if (tid == 0) {
             mbar_arrive_expect_tx(&bar[0], kTileBytes);
-            bulk_g2s(&tile[0][0], fr + (int64_t)f0 * ADJ_FTILE, kTileBytes, &bar[0]);
+            bulk_g2s(&tile[0][0], fr + (int64_t)f0 * PAIRS, kTileBytes, &bar[0]);
         }
         for (int ft = f0; ft < f1; ++ft) {
             const int i = ft - f0;
@@ -165,7 +314,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
             if (tid == 0 && ft + 1 < f1) {
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&bar[st ^ 1], kTileBytes);
-                bulk_g2s(&tile[st ^ 1][0], fr + (int64_t)(ft + 1) * ADJ_FTILE, kTileBytes, &bar[st ^ 1]);
+                bulk_g2s(&tile[st ^ 1][0], fr + (int64_t)(ft + 1) * PAIRS, kTileBytes, &bar[st ^ 1]);
             }
             const bool ok = mbar_wait_bounded(&bar[st], (i >> 1) & 1, kWaitLimitNs);
             if (__syncthreads_or(!ok)) {
@@ -176,55 +325,104 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
                 }
                 return;
             }
-            float part[NACC];
+            F2 part[NACC];
 #pragma unroll
-            for (int k = 0; k < NACC; ++k) part[k] = 0.f;
+            for (int k = 0; k < NACC; ++k) part[k] = mk(0.f, 0.f);
 #pragma unroll 1
-            for (int j = 0; j < ADJ_FTILE; ++j) {
-                const FreqF32& Fq = tile[st][j];
-                const uint32_t P = (uint32_t)Fq.n[0] * T.U[0] + (uint32_t)Fq.n[1] * T.U[1] + (uint32_t)Fq.n[2] * T.U[2];
-                const float ph = (float)(int32_t)P * kTwoPiOver2p32;
-                const float xx = Fq.xi[0], xy = Fq.xi[1], xz = Fq.xi[2];
-                const float a = xx * T.e21x + xy * T.e21y + xz * T.e21z;
-                const float b = xx * T.e31x + xy * T.e31y + xz * T.e31z;
-                TriLocal<float, true> o;
-                tri_local<float, true>(a, b, o);
-                float sp, cp;
-                __sincosf(ph, &sp, &cp);
-                const Cx<float> r = cmul(Cx<float>{cp, -sp}, o.rho);
-                const Cx<float> H = cmul(Cx<float>{Fq.Gr, -Fq.Gi}, r);  // conj(Gw) exp(-i phi1) rho
-                const float rf = re_mul(H, o.f);
-                const float t0 = re_mul(H, o.D[0]), t1 = re_mul(H, o.D[1]), t2 = re_mul(H, o.D[2]);
-                const float tv1 = sel3(o.p1, t0, t1, t2);
-                const float tlo = sel3(o.plo, t0, t1, t2);
-                const float thi = sel3(o.phi, t0, t1, t2);
-                float tv2 = o.ab ? tlo : thi;
-                float tv3 = o.ab ? thi : tlo;
-                float tw1 = tv1;
-                if (MODE == 0) {
-                    part[0] += rf;
+            for (int j = 0; j < PAIRS; ++j) {
+                const FreqPairF32& R = tile[st][j];
+                const uint32_t PA = (uint32_t)R.nA[0] * T.U[0] + (uint32_t)R.nA[1] * T.U[1] + (uint32_t)R.nA[2] * T.U[2];
+                const uint32_t PB = (uint32_t)R.nB[0] * T.U[0] + (uint32_t)R.nB[1] * T.U[1] + (uint32_t)R.nB[2] * T.U[2];
+                const F2 ph = mul2(mk((float)(int32_t)PA, (float)(int32_t)PB), mk(kTwoPiOver2p32, kTwoPiOver2p32));
+                const F2 X = R.x, Y = R.y, Z = R.z;
+                const F2 a = fma2(Z, T.e21z, fma2(Y, T.e21y, mul2(X, T.e21x)));
+                const F2 b = fma2(Z, T.e31z, fma2(Y, T.e31y, mul2(X, T.e31x)));
+                const Order oA = order3(a.x, b.x), oB = order3(a.y, b.y);
+                const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
+                const F2 s = sub2(hi, lo);
+                F2 rf, tv1, tv2, tv3;
+                if (s.x < TS || s.y < TS) {
+                    // near-degenerate: each lane by the series branch in the vertex-1 frame (rare)
+                    const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y};
+                    const float gr[2] = {R.Gr.x, R.Gr.y}, gi[2] = {R.Gi.x, R.Gi.y};
+                    float o_rf[2], o1[2], o2[2], o3[2];
+#pragma unroll
+                    for (int l = 0; l < 2; ++l) {
+                        TriLocal<float, true> o;
+                        tri_local<float, true>(aa[l], bb[l], o);
+                        float sp, cp;
+                        __sincosf(pp[l], &sp, &cp);
+                        const Cx<float> H = cmul(Cx<float>{gr[l], -gi[l]}, cmul(Cx<float>{cp, -sp}, o.rho));
+                        o_rf[l] = re_mul(H, o.f);
+                        const float t0 = re_mul(H, o.D[0]), t1 = re_mul(H, o.D[1]), t2 = re_mul(H, o.D[2]);
+                        const float tlo = sel3(o.plo, t0, t1, t2), thi = sel3(o.phi, t0, t1, t2);
+                        o1[l] = sel3(o.p1, t0, t1, t2);
+                        o2[l] = o.ab ? tlo : thi;
+                        o3[l] = o.ab ? thi : tlo;
+                    }
+                    rf = mk(o_rf[0], o_rf[1]);
+                    tv1 = mk(o1[0], o1[1]);
+                    tv2 = mk(o2[0], o2[1]);
+                    tv3 = mk(o3[0], o3[1]);
                 } else {
-                    const float wn = xx * T.w0 + xy * T.w1 + xz * T.w2;  // xi . n_T
-                    part[0] += rf * xx;
-                    part[1] += rf * xy;
-                    part[2] += rf * xz;
-                    tw1 *= wn;
-                    tv2 *= wn;
-                    tv3 *= wn;
+                    const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
+                    const F2 phm = add2(ph, mid);
+                    Gaps<true> g;
+                    gaps2<true>(d1, d2, s, g);
+                    float sma, cma, smb, cmb;
+                    __sincosf(phm.x, &sma, &cma);
+                    __sincosf(phm.y, &smb, &cmb);
+                    const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
+                    // r = -i E - q = (Ey - qx, -Ex - qy)
+                    const F2 r1x = sub2(g.E1y, g.q1x), r1y = mk(-g.E1x.x - g.q1y.x, -g.E1x.y - g.q1y.y);
+                    const F2 r2x = sub2(g.E2y, g.q2x), r2y = mk(-g.E2x.x - g.q2y.x, -g.E2x.y - g.q2y.y);
+                    // f_m = i (E2 - conj E1) invs = (-gy, gx) invs
+                    const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
+                    const F2 mfx = mul2(gy, g.invs);  // -f_m.x
+                    const F2 fyv = mul2(gx, g.invs);  // f_m.y
+                    // unscaled derivatives (times s): D_lo = f + i conj r1, D_mid = i (q2 + conj q1), D_hi = i r2 - f
+                    const F2 Dlx = sub2(r1y, mfx), Dly = add2(fyv, r1x);
+                    const F2 Dmx = sub2(g.q1y, g.q2y), Dmy = add2(g.q2x, g.q1x);
+                    const F2 Dhx = sub2(mfx, r2y), Dhy = sub2(r2x, fyv);
+                    // conj(Gw) e^{-i phi_m} = h - i k with h = Gr cm - Gi sm, k = Gr sm + Gi cm;
+                    // Re((h - i k)(u + i v)) = h u + k v
+                    const F2 h = fms2(R.Gr, cm, mul2(R.Gi, sm));
+                    const F2 k = fma2(R.Gr, sm, mul2(R.Gi, cm));
+                    rf = fms2(k, fyv, mul2(h, mfx));  // h f.x + k f.y with f.x = -mfx
+                    const F2 hs = mul2(h, g.invs), ks = mul2(k, g.invs);
+                    const F2 tlo = fma2(hs, Dlx, mul2(ks, Dly));
+                    const F2 tmd = fma2(hs, Dmx, mul2(ks, Dmy));
+                    const F2 thi = fma2(hs, Dhx, mul2(ks, Dhy));
+                    // vertex 1 = 0, vertex 2 = a, vertex 3 = b
+                    const F2 tmn = sel2(oA.lo1, oB.lo1, tmd, tlo), tmx = sel2(oA.hi1, oB.hi1, tmd, thi);
+                    tv1 = sel2(oA.lo1, oB.lo1, tlo, sel2(oA.hi1, oB.hi1, thi, tmd));
+                    tv2 = sel2(oA.ab, oB.ab, tmn, tmx);
+                    tv3 = sel2(oA.ab, oB.ab, tmx, tmn);
                 }
                 constexpr int B = MODE == 0 ? 1 : 3;
-                part[B + 0] += tw1 * xx;
-                part[B + 1] += tw1 * xy;
-                part[B + 2] += tw1 * xz;
-                part[B + 3] += tv2 * xx;
-                part[B + 4] += tv2 * xy;
-                part[B + 5] += tv2 * xz;
-                part[B + 6] += tv3 * xx;
-                part[B + 7] += tv3 * xy;
-                part[B + 8] += tv3 * xz;
+                if (MODE == 0) {
+                    part[0] = add2(part[0], rf);
+                } else {
+                    const F2 wn = fma2(Z, T.w2, fma2(Y, T.w1, mul2(X, T.w0)));  // xi . n_T
+                    part[0] = fma2(rf, X, part[0]);
+                    part[1] = fma2(rf, Y, part[1]);
+                    part[2] = fma2(rf, Z, part[2]);
+                    tv1 = mul2(tv1, wn);
+                    tv2 = mul2(tv2, wn);
+                    tv3 = mul2(tv3, wn);
+                }
+                part[B + 0] = fma2(tv1, X, part[B + 0]);
+                part[B + 1] = fma2(tv1, Y, part[B + 1]);
+                part[B + 2] = fma2(tv1, Z, part[B + 2]);
+                part[B + 3] = fma2(tv2, X, part[B + 3]);
+                part[B + 4] = fma2(tv2, Y, part[B + 4]);
+                part[B + 5] = fma2(tv2, Z, part[B + 5]);
+                part[B + 6] = fma2(tv3, X, part[B + 6]);
+                part[B + 7] = fma2(tv3, Y, part[B + 7]);
+                part[B + 8] = fma2(tv3, Z, part[B + 8]);
             }
 #pragma unroll
-            for (int k = 0; k < NACC; ++k) kahan_add(tot[k], comp[k], part[k]);
+            for (int k = 0; k < NACC; ++k) kahan_add(tot[k], comp[k], part[k].x + part[k].y);
             __syncthreads();
         }
     }
@@ -242,7 +440,8 @@ cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const 
     const int n_tiles = (int)(n_t_pad / FWD_TILE);
     const float tpx = (float)(2.0 * M_PI / g.L[0]), tpy = (float)(2.0 * M_PI / g.L[1]),
                 tpz = (float)(2.0 * M_PI / g.L[2]);
-    const int64_t blocks = (fs.M + FWD_THREADS - 1) / FWD_THREADS;
+    const int64_t per_block = 2 * FWD_THREADS;
+    const int64_t blocks = (fs.M + per_block - 1) / per_block;
     if (blocks <= 0 || n_tiles <= 0) return cudaSuccess;
     const dim3 grid((unsigned)blocks);
     const bool ex = fs.nlist != nullptr;

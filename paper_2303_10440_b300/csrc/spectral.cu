@@ -30,15 +30,18 @@ __device__ __forceinline__ void fixed64(double u, uint64_t& U) {
 __device__ __forceinline__ void store_rec(TriF32& r, const double* v1, const double* e21, const double* e31,
                                           const double* w, const Geom& g) {
     for (int a = 0; a < 3; ++a) fixed32(v1[a] / g.L[a], r.U[a]);
-    r.e21x = (float)e21[0];
-    r.e21y = (float)e21[1];
-    r.e21z = (float)e21[2];
-    r.e31x = (float)e31[0];
-    r.e31y = (float)e31[1];
-    r.e31z = (float)e31[2];
-    r.w0 = (float)w[0];
-    r.w1 = (float)w[1];
-    r.w2 = (float)w[2];
+    r.pad = 0;
+    const auto dup = [](double v) { return make_float2((float)v, (float)v); };
+    r.e21x = dup(e21[0]);
+    r.e21y = dup(e21[1]);
+    r.e21z = dup(e21[2]);
+    r.e31x = dup(e31[0]);
+    r.e31y = dup(e31[1]);
+    r.e31z = dup(e31[2]);
+    r.w0 = dup(w[0]);
+    r.w1 = dup(w[1]);
+    r.w2 = dup(w[2]);
+    r.pad2 = make_float2(0.f, 0.f);
 }
 __device__ __forceinline__ void store_rec(TriF64& r, const double* v1, const double* e21, const double* e31,
                                           const double* w, const Geom& g) {
@@ -231,21 +234,24 @@ __global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* _
     if (threadIdx.x == 0) partial[blockIdx.x] = l;
 }
 
-template <class R>
-__device__ __forceinline__ void set_rec(FreqF32& r, int nx, int ny, int nz, double x, double y, double z, double gr,
-                                        double gi) {
-    r.n[0] = nx;
-    r.n[1] = ny;
-    r.n[2] = nz;
-    r.xi[0] = (float)x;
-    r.xi[1] = (float)y;
-    r.xi[2] = (float)z;
-    r.Gr = (float)gr;
-    r.Gi = (float)gi;
+// Adjoint record of frequency m: lane m % 2 of pair record m / 2 (FP32), or record m (FP64).
+__device__ __forceinline__ void set_rec(FreqPairF32* fr, int64_t m, int nx, int ny, int nz, double x, double y,
+                                        double z, double gr, double gi) {
+    FreqPairF32& r = fr[m >> 1];
+    int32_t* n = (m & 1) ? r.nB : r.nA;
+    n[0] = nx;
+    n[1] = ny;
+    n[2] = nz;
+    float* lane = reinterpret_cast<float*>(&r.x) + (m & 1);  // x, y, z, Gr, Gi are consecutive float2
+    lane[0] = (float)x;
+    lane[2] = (float)y;
+    lane[4] = (float)z;
+    lane[6] = (float)gr;
+    lane[8] = (float)gi;
 }
-template <class R>
-__device__ __forceinline__ void set_rec(FreqF64& r, int nx, int ny, int nz, double x, double y, double z, double gr,
-                                        double gi) {
+__device__ __forceinline__ void set_rec(FreqF64* fr, int64_t m, int nx, int ny, int nz, double x, double y, double z,
+                                        double gr, double gi) {
+    FreqF64& r = fr[m];
     r.n[0] = nx;
     r.n[1] = ny;
     r.n[2] = nz;
@@ -308,9 +314,9 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
             wr = Gui * ik2;
             wi = -Gur * ik2;
         }
-        set_rec<R>(fr[m], nx, ny, nz, x, y, z, wr, wi);
+        set_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
     } else if (m < M_pad) {
-        set_rec<R>(fr[m], 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
+        set_rec(fr, m, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
     }
     for (int k = 0; k < 7; ++k) {
         const double s = block_sum<NT>(part[k], scratch);
@@ -341,9 +347,9 @@ __global__ void __launch_bounds__(NT) k_prep_raw(int mode, const Cx<R>* __restri
                 wi = ti;
             }
         }
-        set_rec<R>(fr[m], nx, ny, nz, x, y, z, wr, wi);
+        set_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
     } else if (m < M_pad) {
-        set_rec<R>(fr[m], 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
+        set_rec(fr, m, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
     }
     const double s = block_sum<NT>(k0, scratch);
     if (threadIdx.x == 0) {
