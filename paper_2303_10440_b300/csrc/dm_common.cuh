@@ -64,6 +64,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -93,6 +97,66 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
+
+// ---------------------------------------------------------------- tile pipeline
+// Streams n_tiles tiles of TILE records from `src` through STAGES shared-memory stages.
+// full[s] completes when the bulk copy of a tile into stage s has landed; empty[s] collects
+// one arrival per warp when that warp is done with the stage; warp 0 then refills it. No
+// block-wide barrier per tile, so warps may run up to STAGES - 1 tiles apart. Every wait is
+// bounded; on expiry the thread sets ERR_TIMEOUT, stops, and thread 0 waits (bounded) for
+// the copies it issued. body(const Rec* tile) consumes one tile. Call with all threads of the
+// block after a __syncthreads; n_warps = blockDim.x / 32.
+template <int STAGES, int TILE, class Rec, class Body>
+__device__ __forceinline__ void run_tile_pipeline(const Rec* __restrict__ src, int n_tiles, Rec (*stage)[TILE],
+                                                  uint64_t* full, uint64_t* empty, int* err, Body&& body) {
+    constexpr uint32_t kBytes = TILE * sizeof(Rec);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], blockDim.x >> 5);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int issued = n_tiles < STAGES ? n_tiles : STAGES;
+    if (tid == 0)
+        for (int t = 0; t < issued; ++t) {
+            mbar_arrive_expect_tx(&full[t], kBytes);
+            bulk_g2s(stage[t], src + (int64_t)t * TILE, kBytes, &full[t]);
+        }
+    int t = 0;
+    bool ok = true;
+    for (; t < n_tiles; ++t) {
+        const int s = t % STAGES;
+        const uint32_t par = (uint32_t)(t / STAGES) & 1u;
+        if (!mbar_wait_bounded(&full[s], par, kWaitLimitNs)) {
+            ok = false;
+            break;
+        }
+        body(stage[s]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (warp == 0 && t + STAGES < n_tiles) {
+            if (!mbar_wait_bounded(&empty[s], par, kWaitLimitNs)) {
+                ok = false;
+                break;
+            }
+            if (lane == 0) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&full[s], kBytes);
+                bulk_g2s(stage[s], src + (int64_t)(t + STAGES) * TILE, kBytes, &full[s]);
+            }
+            issued = t + STAGES + 1;
+            __syncwarp();
+        }
+    }
+    if (!ok) {
+        atomicOr(err, ERR_TIMEOUT);
+        if (tid == 0)
+            for (int u = t; u < issued; ++u) mbar_wait_bounded(&full[u % STAGES], (uint32_t)(u / STAGES) & 1u, kWaitLimitNs);
+    }
+}
 
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {

@@ -36,6 +36,10 @@ constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;  // 2 pi / 2^32
 constexpr float TS = MathCfg<float>::TS;
 constexpr float TG = MathCfg<float>::TG;
 
+constexpr int kFwdStages = 4, kFwdTile = 64;  // forward: 4 stages x 64 triangle records (24 KB)
+constexpr int kAdjStages = 4;                 // adjoint: 4 stages x 128 frequency pairs (32 KB)
+static_assert(FWD_TILE % kFwdTile == 0, "triangle padding must cover whole forward tiles");
+
 typedef float2 F2;
 __device__ __forceinline__ F2 mk(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
@@ -47,18 +51,15 @@ __device__ __forceinline__ F2 sel2(bool ca, bool cb, F2 t, F2 f) { return mk(ca 
 
 // Taylor polynomials pr(t), pi(t) of meshft_math.cuh (t = d^2) for a pair of gaps.
 __device__ __forceinline__ void taylor2(F2 t, F2& pr, F2& pi) {
-    pr = mk((float)inv_fact(9), (float)inv_fact(9));
-    pr = fma2(pr, t, mk(-(float)inv_fact(7), -(float)inv_fact(7)));
-    pr = fma2(pr, t, mk((float)inv_fact(5), (float)inv_fact(5)));
+    const F2 nt = mk(-t.x, -t.y);
+    pr = fma2(mk((float)inv_fact(7), (float)inv_fact(7)), nt, mk((float)inv_fact(5), (float)inv_fact(5)));
     pr = fma2(pr, t, mk(-(float)inv_fact(3), -(float)inv_fact(3)));
-    pi = mk((float)inv_fact(10), (float)inv_fact(10));
-    pi = fma2(pi, t, mk(-(float)inv_fact(8), -(float)inv_fact(8)));
-    pi = fma2(pi, t, mk((float)inv_fact(6), (float)inv_fact(6)));
-    pi = fma2(pi, t, mk(-(float)inv_fact(4), -(float)inv_fact(4)));
-    pi = fma2(pi, t, mk((float)inv_fact(2), (float)inv_fact(2)));
+    pi = fma2(mk((float)inv_fact(8), (float)inv_fact(8)), nt, mk((float)inv_fact(6), (float)inv_fact(6)));
+    pi = fma2(pi, nt, mk((float)inv_fact(4), (float)inv_fact(4)));
+    pi = fma2(pi, nt, mk((float)inv_fact(2), (float)inv_fact(2)));
     pi = mk(-pi.x, -pi.y);
 }
-static_assert(MathCfg<float>::NPR == 4 && MathCfg<float>::NPI == 5, "taylor2 is written for these orders");
+static_assert(MathCfg<float>::NPR == 3 && MathCfg<float>::NPI == 4, "taylor2 is written for these orders");
 
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
     const float y = v - c;
@@ -85,6 +86,9 @@ __device__ __forceinline__ Order order3(float a, float b) {
 }
 
 // Gap functions for both lanes of both gaps: E(d1), E(d2) and (adjoint) q(d1), q(d2).
+// Since s = d1 + d2 >= TS >= 2 TG here, at most one gap per lane is below TG, so a single
+// Taylor evaluation on min(d1, d2) serves whichever gap needs it.
+static_assert(MathCfg<float>::TS >= 2.0f * MathCfg<float>::TG, "one Taylor evaluation per term needs TS >= 2 TG");
 template <bool ADJ>
 struct Gaps {
     F2 E1x, E1y, E2x, E2y;
@@ -99,34 +103,30 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
     __sincosf(d2.x, &s2a, &c2a);
     __sincosf(d2.y, &s2b, &c2b);
     const bool m1a = d1.x < TG, m1b = d1.y < TG, m2a = d2.x < TG, m2b = d2.y < TG;
-    const F2 d1c = mk(m1a ? 1.f : d1.x, m1b ? 1.f : d1.y);
-    const F2 d2c = mk(m2a ? 1.f : d2.x, m2b ? 1.f : d2.y);
-    const F2 t12 = mul2(d1c, d2c);
-    const F2 prod = mul2(t12, s);
-    const F2 r = mk(__fdividef(1.f, prod.x), __fdividef(1.f, prod.y));
-    const F2 rs = mul2(r, s);
-    const F2 inv1 = mul2(rs, d2c), inv2 = mul2(rs, d1c);
-    g.invs = mul2(r, t12);
-    const F2 t1 = mul2(d1, d1), t2 = mul2(d2, d2);
-    F2 pr1, pi1, pr2, pi2;
-    taylor2(t1, pr1, pi1);
-    taylor2(t2, pr2, pi2);
-    const F2 one = mk(1.f, 1.f), mone = mk(-1.f, -1.f);
-    // direct: E = sin d / d - i (1 - cos d) / d ; Taylor: E = 1 + d^2 pr - i... (Im E = d pi)
+    // reciprocals on the MUFU pipe (the FP32 pipe is the busier one); 1/d only used for d >= TG
+    const F2 inv1 = mk(__fdividef(1.f, fmaxf(d1.x, TG)), __fdividef(1.f, fmaxf(d1.y, TG)));
+    const F2 inv2 = mk(__fdividef(1.f, fmaxf(d2.x, TG)), __fdividef(1.f, fmaxf(d2.y, TG)));
+    g.invs = mk(__fdividef(1.f, s.x), __fdividef(1.f, s.y));
+    const F2 dm = mk(fminf(d1.x, d2.x), fminf(d1.y, d2.y));
+    const F2 tm = mul2(dm, dm);
+    F2 pr, pi;
+    taylor2(tm, pr, pi);
+    const F2 mone = mk(-1.f, -1.f);
+    // Taylor: Re E = 1 + d^2 pr, Im E = d pi ; direct: E = sin d / d - i (1 - cos d) / d
+    const F2 Etx = fma2(tm, pr, mk(1.f, 1.f)), Ety = mul2(dm, pi);
     const F2 E1xd = mul2(mk(s1a, s1b), inv1), E1yd = mul2(add2(mk(c1a, c1b), mone), inv1);
     const F2 E2xd = mul2(mk(s2a, s2b), inv2), E2yd = mul2(add2(mk(c2a, c2b), mone), inv2);
-    const F2 E1xt = fma2(t1, pr1, one), E1yt = mul2(d1, pi1);
-    const F2 E2xt = fma2(t2, pr2, one), E2yt = mul2(d2, pi2);
-    g.E1x = sel2(m1a, m1b, E1xt, E1xd);
-    g.E1y = sel2(m1a, m1b, E1yt, E1yd);
-    g.E2x = sel2(m2a, m2b, E2xt, E2xd);
-    g.E2y = sel2(m2a, m2b, E2yt, E2yd);
+    g.E1x = sel2(m1a, m1b, Etx, E1xd);
+    g.E1y = sel2(m1a, m1b, Ety, E1yd);
+    g.E2x = sel2(m2a, m2b, Etx, E2xd);
+    g.E2y = sel2(m2a, m2b, Ety, E2yd);
     if (ADJ) {
-        // q = (E - 1)/d (direct) ; Re q = d pr, Im q = pi (Taylor)
-        g.q1x = sel2(m1a, m1b, mul2(d1, pr1), mul2(add2(g.E1x, mone), inv1));
-        g.q1y = sel2(m1a, m1b, pi1, mul2(g.E1y, inv1));
-        g.q2x = sel2(m2a, m2b, mul2(d2, pr2), mul2(add2(g.E2x, mone), inv2));
-        g.q2y = sel2(m2a, m2b, pi2, mul2(g.E2y, inv2));
+        // Taylor: Re q = d pr, Im q = pi ; direct: q = (E - 1)/d
+        const F2 qtx = mul2(dm, pr);
+        g.q1x = sel2(m1a, m1b, qtx, mul2(add2(E1xd, mone), inv1));
+        g.q1y = sel2(m1a, m1b, pi, mul2(E1yd, inv1));
+        g.q2x = sel2(m2a, m2b, qtx, mul2(add2(E2xd, mone), inv2));
+        g.q2y = sel2(m2a, m2b, pi, mul2(E2yd, inv2));
     }
 }
 
@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
                                                          float tpx, float tpy, float tpz,
                                                          const double* __restrict__ d_vol, float2* __restrict__ S,
                                                          int* __restrict__ err) {
-    __shared__ __align__(128) TriF32 tile[2][FWD_TILE];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
+    __shared__ __align__(8) uint64_t full[kFwdStages], empty[kFwdStages];
     constexpr int PER_BLOCK = 2 * FWD_THREADS;
     const int tid = threadIdx.x;
     const int64_t M = fs.dM ? *fs.dM : fs.M;
@@ -166,39 +166,12 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
     const uint32_t uA0 = (uint32_t)n[0][0], uA1 = (uint32_t)n[0][1], uA2 = (uint32_t)n[0][2];
     const uint32_t uB0 = (uint32_t)n[1][0], uB1 = (uint32_t)n[1][1], uB2 = (uint32_t)n[1][2];
 
-    constexpr uint32_t kTileBytes = FWD_TILE * sizeof(TriF32);
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bar[0], kTileBytes);
-        bulk_g2s(&tile[0][0], tris, kTileBytes, &bar[0]);
-    }
-
     F2 SX = mk(0.f, 0.f), SY = mk(0.f, 0.f), CX = mk(0.f, 0.f), CY = mk(0.f, 0.f);
-    for (int t = 0; t < n_tiles; ++t) {
-        const int st = t & 1;
-        if (tid == 0 && t + 1 < n_tiles) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar[st ^ 1], kTileBytes);
-            bulk_g2s(&tile[st ^ 1][0], tris + (int64_t)(t + 1) * FWD_TILE, kTileBytes, &bar[st ^ 1]);
-        }
-        const bool ok = mbar_wait_bounded(&bar[st], (t >> 1) & 1, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(err, ERR_TIMEOUT);
-                mbar_wait_bounded(&bar[st], (t >> 1) & 1, kWaitLimitNs);
-                if (t + 1 < n_tiles) mbar_wait_bounded(&bar[st ^ 1], ((t + 1) >> 1) & 1, kWaitLimitNs);
-            }
-            return;
-        }
+    const auto consume = [&](const TriF32* tile) {
         F2 PX = mk(0.f, 0.f), PY = mk(0.f, 0.f);
-#pragma unroll 1
-        for (int j = 0; j < FWD_TILE; ++j) {
-            const TriF32& T = tile[st][j];
+        #pragma unroll 1
+        for (int j = 0; j < kFwdTile; ++j) {
+            const TriF32& T = tile[j];
             const uint32_t PA = uA0 * T.U[0] + uA1 * T.U[1] + uA2 * T.U[2];
             const uint32_t PB = uB0 * T.U[0] + uB1 * T.U[1] + uB2 * T.U[2];
             const F2 ph = mul2(mk((float)(int32_t)PA, (float)(int32_t)PB), mk(kTwoPiOver2p32, kTwoPiOver2p32));
@@ -212,7 +185,7 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
                 // near-degenerate: evaluate each lane with the series branch (rare)
                 const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y}, ww[2] = {w.x, w.y};
                 float fx[2], fy[2];
-#pragma unroll
+        #pragma unroll
                 for (int l = 0; l < 2; ++l) {
                     TriLocal<float, false> o;
                     tri_local<float, false>(aa[l], bb[l], o);
@@ -246,8 +219,8 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
         kahan_add(SX.y, CX.y, PX.y);
         kahan_add(SY.x, CY.x, PY.x);
         kahan_add(SY.y, CY.y, PY.y);
-        __syncthreads();
-    }
+    };
+    run_tile_pipeline<kFwdStages, kFwdTile>(tris, n_tiles, stage, full, empty, err, consume);
     float sx[2] = {SX.x, SX.y}, sy[2] = {SY.x, SY.y};
     if (MODE == 1) {
         // volume: S = (i / |xi|^2) sum_T (xi . n_T) f_T, and the enclosed volume at xi = 0
@@ -282,8 +255,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
                                                          int* __restrict__ err) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
     constexpr int PAIRS = ADJ_FTILE / 2;
-    __shared__ __align__(128) FreqPairF32 tile[2][PAIRS];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(128) FreqPairF32 stage[kAdjStages][PAIRS];
+    __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
     const int tid = threadIdx.x;
     const int64_t t = (int64_t)blockIdx.x * ADJ_THREADS + tid;
     const int64_t M = dM ? *dM : M_max;
@@ -297,134 +270,107 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     for (int k = 0; k < NACC; ++k) tot[k] = comp[k] = 0.f;
 
     if (f1 > f0) {
-        constexpr uint32_t kTileBytes = PAIRS * sizeof(FreqPairF32);
-        if (tid == 0) {
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
-            mbar_fence_init();
-        }
-        __syncthreads();
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&bar[0], kTileBytes);
-            bulk_g2s(&tile[0][0], fr + (int64_t)f0 * PAIRS, kTileBytes, &bar[0]);
-        }
-        for (int ft = f0; ft < f1; ++ft) {
-            const int i = ft - f0;
-            const int st = i & 1;
-            if (tid == 0 && ft + 1 < f1) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(&bar[st ^ 1], kTileBytes);
-                bulk_g2s(&tile[st ^ 1][0], fr + (int64_t)(ft + 1) * PAIRS, kTileBytes, &bar[st ^ 1]);
-            }
-            const bool ok = mbar_wait_bounded(&bar[st], (i >> 1) & 1, kWaitLimitNs);
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0) {
-                    atomicOr(err, ERR_TIMEOUT);
-                    mbar_wait_bounded(&bar[st], (i >> 1) & 1, kWaitLimitNs);
-                    if (ft + 1 < f1) mbar_wait_bounded(&bar[st ^ 1], ((i + 1) >> 1) & 1, kWaitLimitNs);
-                }
-                return;
-            }
+        const auto consume = [&](const FreqPairF32* tile) {
             F2 part[NACC];
-#pragma unroll
+            #pragma unroll
             for (int k = 0; k < NACC; ++k) part[k] = mk(0.f, 0.f);
-#pragma unroll 1
+            #pragma unroll 1
             for (int j = 0; j < PAIRS; ++j) {
-                const FreqPairF32& R = tile[st][j];
-                const uint32_t PA = (uint32_t)R.nA[0] * T.U[0] + (uint32_t)R.nA[1] * T.U[1] + (uint32_t)R.nA[2] * T.U[2];
-                const uint32_t PB = (uint32_t)R.nB[0] * T.U[0] + (uint32_t)R.nB[1] * T.U[1] + (uint32_t)R.nB[2] * T.U[2];
-                const F2 ph = mul2(mk((float)(int32_t)PA, (float)(int32_t)PB), mk(kTwoPiOver2p32, kTwoPiOver2p32));
-                const F2 X = R.x, Y = R.y, Z = R.z;
-                const F2 a = fma2(Z, T.e21z, fma2(Y, T.e21y, mul2(X, T.e21x)));
-                const F2 b = fma2(Z, T.e31z, fma2(Y, T.e31y, mul2(X, T.e31x)));
-                const Order oA = order3(a.x, b.x), oB = order3(a.y, b.y);
-                const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
-                const F2 s = sub2(hi, lo);
-                F2 rf, tv1, tv2, tv3;
-                if (s.x < TS || s.y < TS) {
-                    // near-degenerate: each lane by the series branch in the vertex-1 frame (rare)
-                    const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y};
-                    const float gr[2] = {R.Gr.x, R.Gr.y}, gi[2] = {R.Gi.x, R.Gi.y};
-                    float o_rf[2], o1[2], o2[2], o3[2];
-#pragma unroll
-                    for (int l = 0; l < 2; ++l) {
-                        TriLocal<float, true> o;
-                        tri_local<float, true>(aa[l], bb[l], o);
-                        float sp, cp;
-                        __sincosf(pp[l], &sp, &cp);
-                        const Cx<float> H = cmul(Cx<float>{gr[l], -gi[l]}, cmul(Cx<float>{cp, -sp}, o.rho));
-                        o_rf[l] = re_mul(H, o.f);
-                        const float t0 = re_mul(H, o.D[0]), t1 = re_mul(H, o.D[1]), t2 = re_mul(H, o.D[2]);
-                        const float tlo = sel3(o.plo, t0, t1, t2), thi = sel3(o.phi, t0, t1, t2);
-                        o1[l] = sel3(o.p1, t0, t1, t2);
-                        o2[l] = o.ab ? tlo : thi;
-                        o3[l] = o.ab ? thi : tlo;
-                    }
-                    rf = mk(o_rf[0], o_rf[1]);
-                    tv1 = mk(o1[0], o1[1]);
-                    tv2 = mk(o2[0], o2[1]);
-                    tv3 = mk(o3[0], o3[1]);
-                } else {
-                    const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
-                    const F2 phm = add2(ph, mid);
-                    Gaps<true> g;
-                    gaps2<true>(d1, d2, s, g);
-                    float sma, cma, smb, cmb;
-                    __sincosf(phm.x, &sma, &cma);
-                    __sincosf(phm.y, &smb, &cmb);
-                    const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
-                    // r = -i E - q = (Ey - qx, -Ex - qy)
-                    const F2 r1x = sub2(g.E1y, g.q1x), r1y = mk(-g.E1x.x - g.q1y.x, -g.E1x.y - g.q1y.y);
-                    const F2 r2x = sub2(g.E2y, g.q2x), r2y = mk(-g.E2x.x - g.q2y.x, -g.E2x.y - g.q2y.y);
-                    // f_m = i (E2 - conj E1) invs = (-gy, gx) invs
-                    const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
-                    const F2 mfx = mul2(gy, g.invs);  // -f_m.x
-                    const F2 fyv = mul2(gx, g.invs);  // f_m.y
-                    // unscaled derivatives (times s): D_lo = f + i conj r1, D_mid = i (q2 + conj q1), D_hi = i r2 - f
-                    const F2 Dlx = sub2(r1y, mfx), Dly = add2(fyv, r1x);
-                    const F2 Dmx = sub2(g.q1y, g.q2y), Dmy = add2(g.q2x, g.q1x);
-                    const F2 Dhx = sub2(mfx, r2y), Dhy = sub2(r2x, fyv);
-                    // conj(Gw) e^{-i phi_m} = h - i k with h = Gr cm - Gi sm, k = Gr sm + Gi cm;
-                    // Re((h - i k)(u + i v)) = h u + k v
-                    const F2 h = fms2(R.Gr, cm, mul2(R.Gi, sm));
-                    const F2 k = fma2(R.Gr, sm, mul2(R.Gi, cm));
-                    rf = fms2(k, fyv, mul2(h, mfx));  // h f.x + k f.y with f.x = -mfx
-                    const F2 hs = mul2(h, g.invs), ks = mul2(k, g.invs);
-                    const F2 tlo = fma2(hs, Dlx, mul2(ks, Dly));
-                    const F2 tmd = fma2(hs, Dmx, mul2(ks, Dmy));
-                    const F2 thi = fma2(hs, Dhx, mul2(ks, Dhy));
-                    // vertex 1 = 0, vertex 2 = a, vertex 3 = b
-                    const F2 tmn = sel2(oA.lo1, oB.lo1, tmd, tlo), tmx = sel2(oA.hi1, oB.hi1, tmd, thi);
-                    tv1 = sel2(oA.lo1, oB.lo1, tlo, sel2(oA.hi1, oB.hi1, thi, tmd));
-                    tv2 = sel2(oA.ab, oB.ab, tmn, tmx);
-                    tv3 = sel2(oA.ab, oB.ab, tmx, tmn);
+            const FreqPairF32& R = tile[j];
+            const uint32_t PA = (uint32_t)R.nA[0] * T.U[0] + (uint32_t)R.nA[1] * T.U[1] + (uint32_t)R.nA[2] * T.U[2];
+            const uint32_t PB = (uint32_t)R.nB[0] * T.U[0] + (uint32_t)R.nB[1] * T.U[1] + (uint32_t)R.nB[2] * T.U[2];
+            const F2 ph = mul2(mk((float)(int32_t)PA, (float)(int32_t)PB), mk(kTwoPiOver2p32, kTwoPiOver2p32));
+            const F2 X = R.x, Y = R.y, Z = R.z;
+            const F2 a = fma2(Z, T.e21z, fma2(Y, T.e21y, mul2(X, T.e21x)));
+            const F2 b = fma2(Z, T.e31z, fma2(Y, T.e31y, mul2(X, T.e31x)));
+            const Order oA = order3(a.x, b.x), oB = order3(a.y, b.y);
+            const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
+            const F2 s = sub2(hi, lo);
+            F2 rf, tv1, tv2, tv3;
+            if (s.x < TS || s.y < TS) {
+                // near-degenerate: each lane by the series branch in the vertex-1 frame (rare)
+                const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y};
+                const float gr[2] = {R.Gr.x, R.Gr.y}, gi[2] = {R.Gi.x, R.Gi.y};
+                float o_rf[2], o1[2], o2[2], o3[2];
+            #pragma unroll
+                for (int l = 0; l < 2; ++l) {
+                    TriLocal<float, true> o;
+                    tri_local<float, true>(aa[l], bb[l], o);
+                    float sp, cp;
+                    __sincosf(pp[l], &sp, &cp);
+                    const Cx<float> H = cmul(Cx<float>{gr[l], -gi[l]}, cmul(Cx<float>{cp, -sp}, o.rho));
+                    o_rf[l] = re_mul(H, o.f);
+                    const float t0 = re_mul(H, o.D[0]), t1 = re_mul(H, o.D[1]), t2 = re_mul(H, o.D[2]);
+                    const float tlo = sel3(o.plo, t0, t1, t2), thi = sel3(o.phi, t0, t1, t2);
+                    o1[l] = sel3(o.p1, t0, t1, t2);
+                    o2[l] = o.ab ? tlo : thi;
+                    o3[l] = o.ab ? thi : tlo;
                 }
-                constexpr int B = MODE == 0 ? 1 : 3;
-                if (MODE == 0) {
-                    part[0] = add2(part[0], rf);
-                } else {
-                    const F2 wn = fma2(Z, T.w2, fma2(Y, T.w1, mul2(X, T.w0)));  // xi . n_T
-                    part[0] = fma2(rf, X, part[0]);
-                    part[1] = fma2(rf, Y, part[1]);
-                    part[2] = fma2(rf, Z, part[2]);
-                    tv1 = mul2(tv1, wn);
-                    tv2 = mul2(tv2, wn);
-                    tv3 = mul2(tv3, wn);
-                }
-                part[B + 0] = fma2(tv1, X, part[B + 0]);
-                part[B + 1] = fma2(tv1, Y, part[B + 1]);
-                part[B + 2] = fma2(tv1, Z, part[B + 2]);
-                part[B + 3] = fma2(tv2, X, part[B + 3]);
-                part[B + 4] = fma2(tv2, Y, part[B + 4]);
-                part[B + 5] = fma2(tv2, Z, part[B + 5]);
-                part[B + 6] = fma2(tv3, X, part[B + 6]);
-                part[B + 7] = fma2(tv3, Y, part[B + 7]);
-                part[B + 8] = fma2(tv3, Z, part[B + 8]);
+                rf = mk(o_rf[0], o_rf[1]);
+                tv1 = mk(o1[0], o1[1]);
+                tv2 = mk(o2[0], o2[1]);
+                tv3 = mk(o3[0], o3[1]);
+            } else {
+                const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
+                const F2 phm = add2(ph, mid);
+                Gaps<true> g;
+                gaps2<true>(d1, d2, s, g);
+                float sma, cma, smb, cmb;
+                __sincosf(phm.x, &sma, &cma);
+                __sincosf(phm.y, &smb, &cmb);
+                const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
+                // r = -i E - q = (Ey - qx, -Ex - qy)
+                const F2 r1x = sub2(g.E1y, g.q1x), r1y = mk(-g.E1x.x - g.q1y.x, -g.E1x.y - g.q1y.y);
+                const F2 r2x = sub2(g.E2y, g.q2x), r2y = mk(-g.E2x.x - g.q2y.x, -g.E2x.y - g.q2y.y);
+                // f_m = i (E2 - conj E1) invs = (-gy, gx) invs
+                const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
+                const F2 mfx = mul2(gy, g.invs);  // -f_m.x
+                const F2 fyv = mul2(gx, g.invs);  // f_m.y
+                // unscaled derivatives (times s): D_lo = f + i conj r1, D_mid = i (q2 + conj q1), D_hi = i r2 - f
+                const F2 Dlx = sub2(r1y, mfx), Dly = add2(fyv, r1x);
+                const F2 Dmx = sub2(g.q1y, g.q2y), Dmy = add2(g.q2x, g.q1x);
+                const F2 Dhx = sub2(mfx, r2y), Dhy = sub2(r2x, fyv);
+                // conj(Gw) e^{-i phi_m} = h - i k with h = Gr cm - Gi sm, k = Gr sm + Gi cm;
+                // Re((h - i k)(u + i v)) = h u + k v
+                const F2 h = fms2(R.Gr, cm, mul2(R.Gi, sm));
+                const F2 k = fma2(R.Gr, sm, mul2(R.Gi, cm));
+                rf = fms2(k, fyv, mul2(h, mfx));  // h f.x + k f.y with f.x = -mfx
+                const F2 hs = mul2(h, g.invs), ks = mul2(k, g.invs);
+                const F2 tlo = fma2(hs, Dlx, mul2(ks, Dly));
+                const F2 tmd = fma2(hs, Dmx, mul2(ks, Dmy));
+                const F2 thi = fma2(hs, Dhx, mul2(ks, Dhy));
+                // vertex 1 = 0, vertex 2 = a, vertex 3 = b
+                const F2 tmn = sel2(oA.lo1, oB.lo1, tmd, tlo), tmx = sel2(oA.hi1, oB.hi1, tmd, thi);
+                tv1 = sel2(oA.lo1, oB.lo1, tlo, sel2(oA.hi1, oB.hi1, thi, tmd));
+                tv2 = sel2(oA.ab, oB.ab, tmn, tmx);
+                tv3 = sel2(oA.ab, oB.ab, tmx, tmn);
             }
-#pragma unroll
+            constexpr int B = MODE == 0 ? 1 : 3;
+            if (MODE == 0) {
+                part[0] = add2(part[0], rf);
+            } else {
+                const F2 wn = fma2(Z, T.w2, fma2(Y, T.w1, mul2(X, T.w0)));  // xi . n_T
+                part[0] = fma2(rf, X, part[0]);
+                part[1] = fma2(rf, Y, part[1]);
+                part[2] = fma2(rf, Z, part[2]);
+                tv1 = mul2(tv1, wn);
+                tv2 = mul2(tv2, wn);
+                tv3 = mul2(tv3, wn);
+            }
+            part[B + 0] = fma2(tv1, X, part[B + 0]);
+            part[B + 1] = fma2(tv1, Y, part[B + 1]);
+            part[B + 2] = fma2(tv1, Z, part[B + 2]);
+            part[B + 3] = fma2(tv2, X, part[B + 3]);
+            part[B + 4] = fma2(tv2, Y, part[B + 4]);
+            part[B + 5] = fma2(tv2, Z, part[B + 5]);
+            part[B + 6] = fma2(tv3, X, part[B + 6]);
+            part[B + 7] = fma2(tv3, Y, part[B + 7]);
+            part[B + 8] = fma2(tv3, Z, part[B + 8]);
+            }
+            #pragma unroll
             for (int k = 0; k < NACC; ++k) kahan_add(tot[k], comp[k], part[k].x + part[k].y);
-            __syncthreads();
-        }
+        };
+        run_tile_pipeline<kAdjStages, PAIRS>(fr + (int64_t)f0 * PAIRS, f1 - f0, stage, full, empty, err, consume);
     }
     if (t < n_t_pad) {
         float* out = partial + (int64_t)blockIdx.y * NACC * n_t_pad + t;
@@ -437,7 +383,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
 
 cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, float2* S, int* d_err, cudaStream_t st) {
-    const int n_tiles = (int)(n_t_pad / FWD_TILE);
+    const int n_tiles = (int)(n_t_pad / kFwdTile);
     const float tpx = (float)(2.0 * M_PI / g.L[0]), tpy = (float)(2.0 * M_PI / g.L[1]),
                 tpz = (float)(2.0 * M_PI / g.L[2]);
     const int64_t per_block = 2 * FWD_THREADS;

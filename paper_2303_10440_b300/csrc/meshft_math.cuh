@@ -34,11 +34,11 @@ template <class R>
 struct MathCfg;
 template <>
 struct MathCfg<float> {
-    static constexpr float TS = 0.5f;  // spread threshold for the series branch
-    static constexpr float TG = 0.5f;  // gap threshold for the Taylor forms of E, q
-    static constexpr int K = 8;        // series terms (truncation < 1e-7 relative at s = TS)
-    static constexpr int NPR = 4;      // Taylor coefficients of pr(t) (t = d^2)
-    static constexpr int NPI = 5;      // Taylor coefficients of pi(t)
+    static constexpr float TS = 0.5f;   // spread threshold for the series branch (>= 2 TG: at most one small gap)
+    static constexpr float TG = 0.25f;  // gap threshold for the Taylor forms of E, q
+    static constexpr int K = 8;         // series terms (truncation < 1e-8 relative at s = TS)
+    static constexpr int NPR = 3;       // Taylor coefficients of pr(t) (t = d^2; truncation < 1e-9 at d = TG)
+    static constexpr int NPI = 4;       // Taylor coefficients of pi(t)
 };
 template <>
 struct MathCfg<double> {

@@ -1,0 +1,110 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py times.
+
+* 128^3 single cell (5120 triangles, band = 1,064,960 frequencies): the FP32 path against the
+  FP64 GPU path (itself held to 1e-10 of the oracle at small sizes) over the whole image, loss
+  and gradients; and both paths against the oracle on sampled frequencies, which the oracle can
+  evaluate one by one (spectrum and mesh adjoint at the full mesh size).
+* 256x256x128 cell (20480 triangles): sampled spectrum against the oracle, and properties that
+  hold at any size (unit total intensity, repeat determinism).
+
+Errors are printed (run with -s to see them).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def renderers():
+    from paper_2303_10440_b300 import Renderer
+
+    r32, r64 = Renderer("fp32"), Renderer("fp64")
+    yield r32, r64
+    r32.close()
+    r64.close()
+
+
+def _dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def test_c2_fp32_matches_fp64_over_the_whole_image(renderers):
+    r32, r64 = renderers
+    case = synth.config_c2()
+    Fd = _dev(case.F)
+    T64 = r64.render(_dev(case.V_true), Fd, case.grid, case.psf)
+    L64, dV64, dp64, I64 = r64.loss_and_grad(_dev(case.V_init), Fd, case.grid, case.psf, T64, "mse", want_image=True)
+    L32, dV32, dp32, I32 = r32.loss_and_grad(_dev(case.V_init), Fd, case.grid, case.psf, T64.float(), "mse",
+                                             want_image=True)
+    e_img = rel(I32.double().cpu(), I64.cpu())
+    e_L = abs(L32 - L64) / L64
+    e_dV = rel(dV32.cpu(), dV64.cpu())
+    e_dp = rel(dp32, dp64)
+    print(f"\n[c2 128^3] FP32 vs FP64: image {e_img:.2e}  loss {e_L:.2e}  dV {e_dV:.2e}  dsigma {e_dp:.2e}")
+    assert e_img < 1e-4 and e_L < 2e-4 and e_dV < 1e-3 and e_dp < 1e-3
+    # unit total intensity (Eq. 3): the band is the whole half spectrum here
+    assert abs(float(I32.double().sum()) * np.prod(case.grid.h) - 1.0) < 1e-5
+    assert abs(float(I64.sum()) * np.prod(case.grid.h) - 1.0) < 1e-12
+
+
+def _sample_band(case, n, seed):
+    nvec, _ = oracle.half_spectrum(case.grid.n)
+    band = oracle.band_mask(oracle.otf(oracle.wavevectors(nvec, case.grid), case.psf), case.psf.band_tau)
+    idx = np.nonzero(band)[0]
+    rng = np.random.default_rng(seed)
+    sel = np.concatenate([[idx[0]], rng.choice(idx, size=n - 1, replace=False)])
+    return nvec[sel].astype(np.int32)
+
+
+@pytest.mark.parametrize("which", ["c2", "c3"])
+def test_full_mesh_spectrum_on_sampled_frequencies(which, renderers):
+    r32, r64 = renderers
+    case = synth.config_c2() if which == "c2" else synth.config_c3()
+    fn = _sample_band(case, 512, seed=5)
+    ref = oracle.mesh_ft(case.V_true - np.asarray(case.grid.origin), case.F, oracle.wavevectors(fn, case.grid))
+    S32 = r32.meshft(_dev(case.V_true), _dev(case.F), case.grid, _dev(fn)).cpu().numpy()
+    S64 = r64.meshft(_dev(case.V_true), _dev(case.F), case.grid, _dev(fn)).cpu().numpy()
+    e32, e64 = rel(S32, ref), rel(S64, ref)
+    print(f"\n[{which} sampled spectrum] FP32 {e32:.2e}  FP64 {e64:.2e}  (n_t = {case.F.shape[0]})")
+    assert e64 < 1e-11 and e32 < 1e-5
+
+
+def test_c2_mesh_adjoint_on_sampled_frequencies(renderers):
+    r32, r64 = renderers
+    case = synth.config_c2()
+    fn = _sample_band(case, 256, seed=6)
+    rng = np.random.default_rng(7)
+    G = (rng.normal(size=len(fn)) + 1j * rng.normal(size=len(fn))) / len(fn)
+    ref = oracle.mesh_ft_adjoint(case.V_init - np.asarray(case.grid.origin), case.F,
+                                 oracle.wavevectors(fn, case.grid), G)
+    d32 = r32.meshft_adjoint(_dev(case.V_init), _dev(case.F), case.grid, _dev(fn), _dev(G)).cpu().numpy()
+    d64 = r64.meshft_adjoint(_dev(case.V_init), _dev(case.F), case.grid, _dev(fn), _dev(G)).cpu().numpy()
+    e32, e64 = rel(d32, ref), rel(d64, ref)
+    print(f"\n[c2 sampled adjoint] FP32 {e32:.2e}  FP64 {e64:.2e}")
+    assert e64 < 1e-10 and e32 < 1e-4
+
+
+def test_c3_properties_and_determinism(renderers):
+    r32, _ = renderers
+    case = synth.config_c3()
+    Vd, Fd = _dev(case.V_true), _dev(case.F)
+    img = r32.render(Vd, Fd, case.grid, case.psf)
+    total = float(img.double().sum()) * np.prod(case.grid.h)
+    print(f"\n[c3 256x256x128] total intensity - 1 = {total - 1:.2e}")
+    assert abs(total - 1.0) < 1e-5
+    T = torch.zeros_like(img)
+    a = r32.loss_and_grad(Vd, Fd, case.grid, case.psf, T, "mse")
+    b = r32.loss_and_grad(Vd, Fd, case.grid, case.psf, T, "mse")
+    assert a[0] == b[0] and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
