@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--workload", choices=["c2", "c3", "c1", "c2s"], default="c2",
                    help="c2: 128^3 single cell (default); c3: 256x256x128, 20480 triangles; c1: 32^3 icosphere; "
                    "c2s: the c2 cell on a 64^3 grid of doubled voxels (small profiling case)")
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                   help="fp32: the FP32 mixed path (headline); fp64: the plain FP64 path (comparator)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -243,7 +245,7 @@ def run_ours(args):
 
     case = make_case(args.workload)
     grid, psf = case.grid, case.psf
-    r = Renderer("fp32", device=local)
+    r = Renderer(args.precision, device=local)
     M = len(r.band(grid, psf))
     n_t = case.F.shape[0]
     terms_step = 2.0 * M * n_t
@@ -306,6 +308,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (event-timed inside the library on this stream)
     dom = max(("fwd", "adj"), key=lambda s: stages[s][0])
+    kern = {"fwd": "k_fwd_f32", "adj": "k_adj_f32"} if args.precision == "fp32" else {"fwd": "k_fwd_f64", "adj": "k_adj_f64"}
     dom_ms = stages[dom][0] / max(stages[dom][1], 1)
     terms_launch = M * n_t
     f_mhz = clk.get("sm_mhz") or 1920.0
@@ -314,7 +317,7 @@ def run_ours(args):
     achieved = terms_launch * OPS_PER_TERM[dom] / (dom_ms / 1e3) / 1e12
     roofline = {
         "bound": "alu",
-        "kernel": "k_adj_f32" if dom == "adj" else "k_fwd_f32",
+        "kernel": kern[dom],
         "achieved": achieved,
         "peak": peak,
         "unit": "Tops/s",
@@ -341,7 +344,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic",
         "config": workload_config(case, M, "flushed (256 MB write) between timed steps, outside the events"),
         "roofline": roofline,

@@ -247,14 +247,18 @@ class Renderer:
         return idx[: M.value].clone()
 
     # ------------------------------------------------------------------ optimisation
-    def adam(self, param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    def adam(self, param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-20, stream=None):
         st = self.lib.dm_adam(self.ctx, param.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), param.numel(),
                               lr, beta1, beta2, eps, int(step), _stream(stream, param.device))
         self._check(st, "dm_adam")
 
     def fit(self, V, F, grid, psf, target, steps, lr_vertex, lr_psf=0.0, loss="mse", label="surface", weights=None,
-            beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
-        """Adam fit on the device. Returns (V_fitted, sigma_fitted, loss_history)."""
+            beta1=0.9, beta2=0.999, eps=1e-20, stream=None):
+        """Adam fit on the device. Returns (V_fitted, sigma_fitted, loss_history).
+
+        eps defaults to 1e-20: rendered images have unit total intensity, so MSE gradients are
+        ~1e-10 and the usual 1e-8 would dominate sqrt(v) and shrink every step.
+        """
         dev = self._dev(V)
         Vw = _as_tensor(V, torch.float64, dev).clone()
         m, keep = self._mesh(Vw, F, label, weights, dev)
