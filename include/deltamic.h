@@ -231,6 +231,80 @@ typedef struct {
 dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
                  const void* target, const dm_fit_options* opt, double* loss_history, void* stream);
 
+/* ---------------------------------------------------------------- fit server
+ * Continuous batching of many shape fits on one GPU (FP32 mixed path). Jobs are copied at
+ * submit into a queue; an engine thread admits them first-in first-out whenever a slot
+ * (max_jobs) and room in the server's device arena (memory_bytes) are free, keeps each
+ * admitted job's mesh, Adam state, band and target on the device, and runs iterations in
+ * which every active job advances by one Adam step: the forward and adjoint mesh-transform
+ * sums of all active jobs run as one persistent launch each, over a work list of
+ * (job, frequency block) and (job, triangle block, frequency chunk) units. A job's results do
+ * not depend on which other jobs share its iterations. Finished jobs leave at the end of an
+ * iteration and queued jobs join at the start of the next. */
+typedef struct dm_server dm_server;
+
+typedef struct {
+    int32_t device;        /* CUDA device ordinal */
+    int32_t max_jobs;      /* jobs advanced concurrently (batch slots), >= 1 */
+    size_t memory_bytes;   /* device arena for job state (0: half of the free device memory) */
+    int32_t chunk_tiles;   /* adjoint frequency tiles (256 frequencies) per work unit (0: 16) */
+    int32_t reserved;
+} dm_server_options;
+
+typedef struct {
+    const double* V;       /* host [n_v][3] initial vertices (copied at submit) */
+    int64_t n_v;
+    const int32_t* F;      /* host [n_t][3] (copied at submit) */
+    int64_t n_t;
+    const float* target;   /* host [Nx][Ny][Nz] target image (copied at submit) */
+    dm_grid grid;
+    dm_psf psf;            /* DM_PSF_DIAG; sigma is the initial value when fit.lr_psf > 0 */
+    dm_fit_options fit;    /* steps, loss, learning rates, Adam constants */
+    int32_t label;         /* DM_SURFACE or DM_VOLUME */
+    int32_t reserved;
+} dm_job;
+
+#define DM_JOB_QUEUED 0
+#define DM_JOB_RUNNING 1
+#define DM_JOB_DONE 2
+#define DM_JOB_FAILED 3
+
+typedef struct {
+    int32_t state;         /* DM_JOB_* */
+    int32_t steps_done;
+    double t_submit;       /* seconds on the server clock */
+    double t_start;        /* admission */
+    double t_end;          /* completion */
+    double last_loss;      /* loss before the last completed step */
+} dm_job_status;
+
+typedef struct {
+    int64_t iterations;    /* engine iterations run */
+    int64_t jobs_done;
+    int64_t job_steps;     /* Adam steps summed over jobs */
+    int64_t peak_active;   /* largest batch */
+    double busy_s;         /* engine time spent in iterations */
+    size_t bytes_in_use;   /* arena bytes held by admitted jobs */
+    size_t bytes_peak;
+    size_t bytes_total;
+} dm_server_stats;
+
+/* Create a server and start its engine thread. */
+dm_status dm_server_create(dm_server** srv, const dm_server_options* opt);
+/* Validate and enqueue a job (all inputs copied). DM_ERR_OOM if it can never fit the arena. */
+dm_status dm_server_submit(dm_server* srv, const dm_job* job, int64_t* job_id);
+dm_status dm_server_status(dm_server* srv, int64_t job_id, dm_job_status* out);
+/* Block until the job is done (or failed); DM_ERR_TIMEOUT after timeout_s seconds (< 0: forever). */
+dm_status dm_server_wait(dm_server* srv, int64_t job_id, double timeout_s);
+/* Copy a finished job's results (host buffers, each nullable): V_out [n_v][3], sigma_out [3],
+ * loss_history [steps]; then forget the job. */
+dm_status dm_server_result(dm_server* srv, int64_t job_id, double* V_out, double* sigma_out, double* loss_history);
+dm_status dm_server_get_stats(dm_server* srv, dm_server_stats* out);
+/* Seconds since the server was created (the clock of dm_job_status). */
+double dm_server_clock(const dm_server* srv);
+/* Stop the engine after its current iteration and release every resource. */
+dm_status dm_server_shutdown(dm_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

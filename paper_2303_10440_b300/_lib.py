@@ -66,6 +66,39 @@ class dm_fit_options(ctypes.Structure):
     ]
 
 
+class dm_server_options(ctypes.Structure):
+    _fields_ = [("device", c_i32), ("max_jobs", c_i32), ("memory_bytes", ctypes.c_size_t), ("chunk_tiles", c_i32),
+                ("reserved", c_i32)]
+
+
+class dm_job(ctypes.Structure):
+    _fields_ = [
+        ("V", c_p),
+        ("n_v", c_i64),
+        ("F", c_p),
+        ("n_t", c_i64),
+        ("target", c_p),
+        ("grid", dm_grid),
+        ("psf", dm_psf),
+        ("fit", dm_fit_options),
+        ("label", c_i32),
+        ("reserved", c_i32),
+    ]
+
+
+class dm_job_status(ctypes.Structure):
+    _fields_ = [("state", c_i32), ("steps_done", c_i32), ("t_submit", c_f64), ("t_start", c_f64), ("t_end", c_f64),
+                ("last_loss", c_f64)]
+
+
+class dm_server_stats(ctypes.Structure):
+    _fields_ = [("iterations", c_i64), ("jobs_done", c_i64), ("job_steps", c_i64), ("peak_active", c_i64),
+                ("busy_s", c_f64), ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
+                ("bytes_total", ctypes.c_size_t)]
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
 _SIGS = {
     "dm_create": (c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(dm_options)]),
     "dm_destroy": (c_i32, [c_p]),
@@ -92,6 +125,14 @@ _SIGS = {
         [c_p, ctypes.POINTER(dm_mesh), ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p, c_p, c_p, c_p],
     ),
     "dm_adam": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i64, c_f64, c_f64, c_f64, c_f64, c_i64, c_p]),
+    "dm_server_create": (c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(dm_server_options)]),
+    "dm_server_submit": (c_i32, [c_p, ctypes.POINTER(dm_job), ctypes.POINTER(c_i64)]),
+    "dm_server_status": (c_i32, [c_p, c_i64, ctypes.POINTER(dm_job_status)]),
+    "dm_server_wait": (c_i32, [c_p, c_i64, c_f64]),
+    "dm_server_result": (c_i32, [c_p, c_i64, c_p, c_p, c_p]),
+    "dm_server_get_stats": (c_i32, [c_p, ctypes.POINTER(dm_server_stats)]),
+    "dm_server_clock": (c_f64, [c_p]),
+    "dm_server_shutdown": (c_i32, [c_p]),
     "dm_fit": (
         c_i32,
         [c_p, ctypes.POINTER(dm_mesh), c_p, ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p,

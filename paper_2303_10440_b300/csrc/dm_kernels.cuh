@@ -90,6 +90,41 @@ cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_
                            const int64_t* dM, int64_t M_max, float* partial, int n_chunks, int* d_err, cudaStream_t st);
 int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count);
 
+// Batched (multi-job) persistent launches of the FP32 sums.
+struct BatchFwdJob {
+    const TriF32* tris;
+    int n_tiles;  // 64-record tiles
+    int mode;
+    FreqSrc fs;
+    float tp[3];
+    const double* d_vol;
+    float2* S;
+};
+struct BatchAdjJob {
+    const TriF32* tris;
+    int64_t n_t, n_t_pad;
+    const FreqPairF32* fr;
+    const int64_t* dM;
+    int64_t M_max;
+    int mode;
+    int chunk_tiles;  // frequency tiles per unit (fixed per job: results do not depend on the batch)
+    float* partial;   // [chunks][10|12][n_t_pad]
+};
+struct BatchUnit {
+    int job;
+    int a;  // forward: frequency block; adjoint: triangle block
+    int b;  // adjoint: frequency chunk
+    int pad;
+};
+cudaError_t launch_fwd_batch_f32(const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
+                                 int* d_err, cudaStream_t st);
+cudaError_t launch_adj_batch_f32(const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
+                                 int* d_err, cudaStream_t st);
+int batch_blocks_per_sm_fwd();
+int batch_blocks_per_sm_adj();
+constexpr int FWD_BLOCK_FREQS = 2 * FWD_THREADS;  // band frequencies per forward block
+constexpr int FWD_REC_TILE = 64;                  // triangle records per forward pipeline stage
+
 // Mesh transform (FP64 plain path).
 cudaError_t launch_fwd_f64(int mode, const TriF64* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, double2* S, cudaStream_t st);

@@ -131,18 +131,18 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
 }
 
 // ------------------------------------------------------------------------------------- forward
+// One forward block: band frequencies [bidx * 512, bidx * 512 + 512) against all triangles.
+// Returns false (without touching the barriers) when the block lies beyond the band.
 template <int MODE, bool EXPLICIT>
-__global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, FreqSrc fs,
-                                                         float tpx, float tpy, float tpz,
-                                                         const double* __restrict__ d_vol, float2* __restrict__ S,
-                                                         int* __restrict__ err) {
-    __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
-    __shared__ __align__(8) uint64_t full[kFwdStages], empty[kFwdStages];
+__device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n_tiles, const FreqSrc& fs, float tpx,
+                                          float tpy, float tpz, const double* __restrict__ d_vol,
+                                          float2* __restrict__ S, int* __restrict__ err, int64_t bidx,
+                                          TriF32 (*stage)[kFwdTile], uint64_t* full, uint64_t* empty) {
     constexpr int PER_BLOCK = 2 * FWD_THREADS;
     const int tid = threadIdx.x;
     const int64_t M = fs.dM ? *fs.dM : fs.M;
-    if ((int64_t)blockIdx.x * PER_BLOCK >= M) return;  // whole block beyond the band (uniform)
-    const int64_t m0 = (int64_t)blockIdx.x * PER_BLOCK + 2 * tid;
+    if (bidx * PER_BLOCK >= M) return false;  // whole block beyond the band (uniform)
+    const int64_t m0 = bidx * PER_BLOCK + 2 * tid;
     const bool actA = m0 < M, actB = m0 + 1 < M;
 
     int n[2][3] = {{0, 0, 0}, {0, 0, 0}};
@@ -244,25 +244,33 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restric
         if (actA) S[m0] = make_float2(sx[0], sy[0]);
         if (actB) S[m0 + 1] = make_float2(sx[1], sy[1]);
     }
+    return true;
+}
+
+template <int MODE, bool EXPLICIT>
+__global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, FreqSrc fs,
+                                                         float tpx, float tpy, float tpz,
+                                                         const double* __restrict__ d_vol, float2* __restrict__ S,
+                                                         int* __restrict__ err) {
+    __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
+    __shared__ __align__(8) uint64_t full[kFwdStages], empty[kFwdStages];
+    fwd_block<MODE, EXPLICIT>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, err, blockIdx.x, stage, full, empty);
 }
 
 // ------------------------------------------------------------------------------------- adjoint
+constexpr int kAdjPairs = ADJ_FTILE / 2;
+
+// One adjoint block: triangles [tblock * 128, tblock * 128 + 128) against frequency tiles [f0, f1);
+// writes the block's sums to out[k * n_t_pad + t] (k < 10 or 12). Returns whether the barriers were used.
 template <int MODE>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restrict__ tris, int64_t n_t,
-                                                         int64_t n_t_pad, const FreqPairF32* __restrict__ fr,
-                                                         const int64_t* __restrict__ dM, int64_t M_max,
-                                                         int tiles_per_chunk, float* __restrict__ partial,
-                                                         int* __restrict__ err) {
+__device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64_t n_t, int64_t n_t_pad,
+                                          const FreqPairF32* __restrict__ fr, int f0, int f1, int64_t tblock,
+                                          float* __restrict__ out_chunk, int* __restrict__ err,
+                                          FreqPairF32 (*stage)[kAdjPairs], uint64_t* full, uint64_t* empty) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
-    constexpr int PAIRS = ADJ_FTILE / 2;
-    __shared__ __align__(128) FreqPairF32 stage[kAdjStages][PAIRS];
-    __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
+    constexpr int PAIRS = kAdjPairs;
     const int tid = threadIdx.x;
-    const int64_t t = (int64_t)blockIdx.x * ADJ_THREADS + tid;
-    const int64_t M = dM ? *dM : M_max;
-    const int n_ftiles = (int)((M + ADJ_FTILE - 1) / ADJ_FTILE);
-    const int f0 = blockIdx.y * tiles_per_chunk;
-    const int f1 = min(f0 + tiles_per_chunk, n_ftiles);
+    const int64_t t = tblock * ADJ_THREADS + tid;
 
     const TriF32 T = tris[t < n_t_pad ? t : 0];
     float tot[NACC], comp[NACC];
@@ -370,12 +378,100 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
             #pragma unroll
             for (int k = 0; k < NACC; ++k) kahan_add(tot[k], comp[k], part[k].x + part[k].y);
         };
-        run_tile_pipeline<kAdjStages, PAIRS>(fr + (int64_t)f0 * PAIRS, f1 - f0, stage, full, empty, err, consume);
+        run_tile_pipeline<kAdjStages, kAdjPairs>(fr + (int64_t)f0 * PAIRS, f1 - f0, stage, full, empty, err, consume);
     }
     if (t < n_t_pad) {
-        float* out = partial + (int64_t)blockIdx.y * NACC * n_t_pad + t;
+        float* out = out_chunk + t;
 #pragma unroll
         for (int k = 0; k < NACC; ++k) out[(int64_t)k * n_t_pad] = t < n_t ? tot[k] : 0.f;
+    }
+    return f1 > f0;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restrict__ tris, int64_t n_t,
+                                                         int64_t n_t_pad, const FreqPairF32* __restrict__ fr,
+                                                         const int64_t* __restrict__ dM, int64_t M_max,
+                                                         int tiles_per_chunk, float* __restrict__ partial,
+                                                         int* __restrict__ err) {
+    constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
+    __shared__ __align__(128) FreqPairF32 stage[kAdjStages][kAdjPairs];
+    __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
+    const int64_t M = dM ? *dM : M_max;
+    const int n_ftiles = (int)((M + ADJ_FTILE - 1) / ADJ_FTILE);
+    const int f0 = blockIdx.y * tiles_per_chunk;
+    const int f1 = min(f0 + tiles_per_chunk, n_ftiles);
+    adj_block<MODE>(tris, n_t, n_t_pad, fr, f0, f1, blockIdx.x, partial + (int64_t)blockIdx.y * NACC * n_t_pad, err,
+                    stage, full, empty);
+}
+
+// ------------------------------------------------------------------------------------- batched
+__device__ __forceinline__ void inval_barriers(uint64_t* full, uint64_t* empty, int n) {
+    for (int s = 0; s < n; ++s) {
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+}
+
+// Persistent forward over the units of several jobs: each block repeatedly takes the next
+// unit (job, frequency block) from an atomic counter. A unit's result does not depend on
+// which block runs it or on the other jobs in the batch.
+__global__ void __launch_bounds__(FWD_THREADS) k_fwd_batch_f32(const BatchFwdJob* __restrict__ jobs,
+                                                               const BatchUnit* __restrict__ units, int n_units,
+                                                               int* __restrict__ counter, int* __restrict__ err) {
+    __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
+    __shared__ __align__(8) uint64_t full[kFwdStages], empty[kFwdStages];
+    __shared__ int s_u;
+    while (true) {
+        if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_u;
+        __syncthreads();
+        if (u >= n_units) break;
+        const BatchUnit U = units[u];
+        const BatchFwdJob& J = jobs[U.job];
+        bool used;
+        if (J.mode == 0)
+            used = fwd_block<0, false>(J.tris, J.n_tiles, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
+                                       stage, full, empty);
+        else
+            used = fwd_block<1, false>(J.tris, J.n_tiles, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
+                                       stage, full, empty);
+        __syncthreads();
+        if (used && threadIdx.x == 0) inval_barriers(full, empty, kFwdStages);
+        __syncthreads();
+    }
+}
+
+// Persistent adjoint over units (job, triangle block, frequency chunk of chunk_tiles tiles).
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_batch_f32(const BatchAdjJob* __restrict__ jobs,
+                                                               const BatchUnit* __restrict__ units, int n_units,
+                                                               int* __restrict__ counter, int* __restrict__ err) {
+    __shared__ __align__(128) FreqPairF32 stage[kAdjStages][kAdjPairs];
+    __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
+    __shared__ int s_u;
+    while (true) {
+        if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_u;
+        __syncthreads();
+        if (u >= n_units) break;
+        const BatchUnit U = units[u];
+        const BatchAdjJob& J = jobs[U.job];
+        const int64_t M = J.dM ? *J.dM : J.M_max;
+        const int n_ftiles = (int)((M + ADJ_FTILE - 1) / ADJ_FTILE);
+        const int f0 = U.b * J.chunk_tiles;
+        const int f1 = min(f0 + J.chunk_tiles, n_ftiles);
+        const int nacc = J.mode == 0 ? NACC_SURF : NACC_VOL;
+        float* out = J.partial + (int64_t)U.b * nacc * J.n_t_pad;
+        bool used;
+        if (J.mode == 0)
+            used = adj_block<0>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty);
+        else
+            used = adj_block<1>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty);
+        __syncthreads();
+        if (used && threadIdx.x == 0) inval_barriers(full, empty, kAdjStages);
+        __syncthreads();
     }
 }
 
@@ -418,6 +514,35 @@ cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_
         k_adj_f32<0><<<grid, ADJ_THREADS, 0, st>>>(tris, n_t, n_t_pad, fr, dM, M_max, tpc, partial, d_err);
     else
         k_adj_f32<1><<<grid, ADJ_THREADS, 0, st>>>(tris, n_t, n_t_pad, fr, dM, M_max, tpc, partial, d_err);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm_fwd() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fwd_batch_f32, FWD_THREADS, 0);
+    return n > 0 ? n : 1;
+}
+int batch_blocks_per_sm_adj() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adj_batch_f32, ADJ_THREADS, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_fwd_batch_f32(const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
+                                 int* d_err, cudaStream_t st) {
+    if (n_units <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_fwd_batch_f32<<<grid, FWD_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_batch_f32(const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
+                                 int* d_err, cudaStream_t st) {
+    if (n_units <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_adj_batch_f32<<<grid, ADJ_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
     return cudaGetLastError();
 }
 

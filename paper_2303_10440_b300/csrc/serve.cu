@@ -1,0 +1,633 @@
+// Continuous-batching fit server (include/deltamic.h, "fit server").
+//
+// Engine thread, per iteration:
+//   admit   queued jobs move in (FIFO) while a batch slot and arena room are free; their
+//           mesh, target, PSF parameters, Adam state, vertex star and band live on the device;
+//   step    every active job advances by one Adam step: per-job stage kernels on one stream,
+//           and the two mesh-transform sums of all active jobs as one persistent batched
+//           launch each (work lists of equal-cost units pulled from an atomic counter);
+//   retire  jobs that reached their step count copy their results to the host and release
+//           their arena block.
+// Arrivals therefore join at the next iteration while earlier jobs are still running, and
+// their work overlaps on the device inside the same launches.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "api_internal.cuh"
+
+namespace {
+
+// First-fit allocator over one device allocation (256-byte granules).
+class DeviceArena {
+  public:
+    char* base = nullptr;
+    size_t total = 0, in_use = 0, peak = 0;
+
+    bool init(size_t bytes) {
+        bytes &= ~(size_t)255;
+        if (cudaMalloc(&base, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            base = nullptr;
+            return false;
+        }
+        total = bytes;
+        free_[0] = bytes;
+        return true;
+    }
+    void release() {
+        if (base) cudaFree(base);
+        base = nullptr;
+        free_.clear();
+    }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                in_use += bytes;
+                peak = std::max(peak, in_use);
+                return true;
+            }
+        }
+        return false;
+    }
+    void release_block(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        in_use -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+  private:
+    std::map<size_t, size_t> free_;
+};
+
+struct SJob {
+    int64_t id = 0;
+    std::vector<double> V;
+    std::vector<int32_t> F;
+    std::vector<float> T;
+    dm_grid grid;
+    dm_psf psf;
+    dm_fit_options fit;
+    int label = DM_SURFACE;
+    int state = DM_JOB_QUEUED;
+    int steps_done = 0;
+    double t_submit = 0, t_start = 0, t_end = 0, last_loss = NAN;
+    // device state
+    size_t off = 0, bytes = 0;
+    Sizes z;
+    Bufs b;
+    double *mV = nullptr, *vV = nullptr, *ms = nullptr, *vs = nullptr, *hist = nullptr;
+    FFTAxis ax[3];
+    // results
+    std::vector<double> V_out, hist_out;
+    double sigma_out[3] = {0, 0, 0};
+};
+
+size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, double** mom, double** hist) {
+    layout(z, A, b, true, true, false, true, false);
+    *mom = A.take<double>(6 * n_v + 8);
+    *hist = A.take<double>(steps);
+    return A.off + 256;
+}
+
+}  // namespace
+
+struct dm_server {
+    dm_ctx* ctx = nullptr;
+    cudaStream_t st = nullptr;
+    DeviceArena arena;
+    int device = 0, max_jobs = 1, chunk_tiles = 32;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<SJob*> pending;
+    std::vector<SJob*> active;
+    std::unordered_map<int64_t, SJob*> jobs;
+    int64_t next_id = 1;
+    bool stop = false;
+    std::thread engine;
+    std::chrono::steady_clock::time_point t0;
+    dm_server_stats stats;
+    // unit lists (rebuilt when the active set changes) and their staging
+    bool dirty = true;
+    std::vector<BatchFwdJob> fj;
+    std::vector<BatchAdjJob> aj;
+    std::vector<BatchUnit> uf, ua;
+    BatchFwdJob* d_fj = nullptr;
+    BatchAdjJob* d_aj = nullptr;
+    BatchUnit *d_uf = nullptr, *d_ua = nullptr;
+    size_t cap_fj = 0, cap_aj = 0, cap_uf = 0, cap_ua = 0;
+    int* d_counter = nullptr;
+    double* h_loss = nullptr;  // pinned, one per batch slot
+    int grid_fwd = 0, grid_adj = 0;
+
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+namespace {
+
+bool grow(void** p, size_t* cap, size_t need, size_t elem) {
+    if (need <= *cap) return true;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    size_t n = std::max(need, *cap * 2 + 16);
+    if (cudaMalloc(p, n * elem) != cudaSuccess) {
+        cudaGetLastError();
+        *cap = 0;
+        return false;
+    }
+    *cap = n;
+    return true;
+}
+
+// Device state of an admitted job; returns false (nothing held) if the arena has no room.
+bool setup_job(dm_server* S, SJob* J) {
+    dm_ctx* ctx = S->ctx;
+    Sizes z = make_sizes(ctx, &J->grid, (int64_t)J->V.size() / 3, (int64_t)J->F.size() / 3, J->psf.band_tau > 0,
+                         J->label);
+    const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
+    z.n_chunks = (int)((ftiles + S->chunk_tiles - 1) / S->chunk_tiles);  // fixed per job
+    Arena A;
+    Bufs b;
+    double *mom, *hist;
+    const size_t bytes = job_layout(z, J->fit.steps, z.n_v, A, b, &mom, &hist);
+    size_t off;
+    if (!S->arena.alloc(bytes, &off)) return false;
+    A.base = S->arena.base + off;
+    A.off = 0;
+    job_layout(z, J->fit.steps, z.n_v, A, b, &mom, &hist);
+    J->off = off;
+    J->bytes = bytes;
+    J->z = z;
+    J->b = b;
+    J->mV = mom;
+    J->vV = mom + 3 * z.n_v;
+    J->ms = mom + 6 * z.n_v;
+    J->vs = J->ms + 4;
+    J->hist = hist;
+    cudaStream_t st = S->st;
+    bool ok = cudaMemcpyAsync(b.V, J->V.data(), J->V.size() * sizeof(double), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(b.F, J->F.data(), J->F.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(b.target, J->T.data(), J->T.size() * sizeof(float), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemsetAsync(mom, 0, (6 * z.n_v + 8) * sizeof(double), st) == cudaSuccess &&
+              launch_set_params(b.d_params, psf_params(&J->psf), 9, st) == cudaSuccess &&
+              launch_csr(b.F, z.n_t, z.n_v, b.cnt, b.ptr, b.ent, ctx->d_err, st) == cudaSuccess &&
+              fft_axes(ctx, J->grid.n, J->ax) == DM_OK;
+    g_launches += 5;
+    // host vectors stay until the uploads have run (synchronised at the end of the iteration)
+    if (!ok) {
+        cudaGetLastError();
+        S->arena.release_block(off, bytes);
+        return false;
+    }
+    return true;
+}
+
+bool rebuild_units(dm_server* S) {
+    const size_t nj = S->active.size();
+    S->fj.resize(nj);
+    S->aj.resize(nj);
+    S->uf.clear();
+    S->ua.clear();
+    std::vector<int> order(nj);
+    for (size_t j = 0; j < nj; ++j) {
+        SJob* J = S->active[j];
+        const Sizes& z = J->z;
+        const Bufs& b = J->b;
+        const Geom G = make_geom(&J->grid);
+        BatchFwdJob& f = S->fj[j];
+        f.tris = (const TriF32*)b.tris;
+        f.n_tiles = (int)(z.n_t_pad / FWD_REC_TILE);
+        f.mode = J->label;
+        f.fs.nlist = nullptr;
+        f.fs.idx = z.band ? b.band_idx : nullptr;
+        f.fs.dM = z.band ? b.dM : nullptr;
+        f.fs.M = z.nH;
+        f.fs.Nx = J->grid.n[0];
+        f.fs.Ny = J->grid.n[1];
+        f.fs.Nz = J->grid.n[2];
+        f.fs.Nzh = J->grid.n[2] / 2 + 1;
+        for (int a = 0; a < 3; ++a) f.tp[a] = (float)(2.0 * M_PI / G.L[a]);
+        f.d_vol = b.d_params + 16;
+        f.S = (float2*)b.S;
+        BatchAdjJob& a = S->aj[j];
+        a.tris = (const TriF32*)b.tris;
+        a.n_t = z.n_t;
+        a.n_t_pad = z.n_t_pad;
+        a.fr = (const FreqPairF32*)b.fr;
+        a.dM = z.band ? b.dM : nullptr;
+        a.M_max = z.M_max;
+        a.mode = J->label;
+        a.chunk_tiles = S->chunk_tiles;
+        a.partial = (float*)b.adjp;
+        order[j] = (int)j;
+    }
+    // largest triangle counts first: their forward units cost the most
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return S->active[x]->z.n_t > S->active[y]->z.n_t; });
+    for (int j : order) {
+        const int64_t nb = (S->active[j]->z.nH + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
+        for (int64_t k = 0; k < nb; ++k) S->uf.push_back({j, (int)k, 0, 0});
+    }
+    for (int j : order) {
+        const Sizes& z = S->active[j]->z;
+        const int64_t tb = z.n_t_pad / ADJ_THREADS;
+        for (int c = 0; c < z.n_chunks; ++c)
+            for (int64_t t = 0; t < tb; ++t) S->ua.push_back({j, (int)t, c, 0});
+    }
+    bool ok = grow((void**)&S->d_fj, &S->cap_fj, nj, sizeof(BatchFwdJob)) &&
+              grow((void**)&S->d_aj, &S->cap_aj, nj, sizeof(BatchAdjJob)) &&
+              grow((void**)&S->d_uf, &S->cap_uf, S->uf.size(), sizeof(BatchUnit)) &&
+              grow((void**)&S->d_ua, &S->cap_ua, S->ua.size(), sizeof(BatchUnit));
+    S->dirty = !ok;
+    return ok;
+}
+
+// One Adam step of every active job. Returns false on a device fault.
+bool iterate(dm_server* S) {
+    dm_ctx* ctx = S->ctx;
+    cudaStream_t st = S->st;
+    if (S->dirty && !rebuild_units(S)) return false;
+    const size_t nj = S->active.size();
+    BatchFwdJob* d_fj = S->d_fj;
+    BatchAdjJob* d_aj = S->d_aj;
+    bool ok = true;
+    ok &= cudaMemcpyAsync(d_fj, S->fj.data(), nj * sizeof(BatchFwdJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok &= cudaMemcpyAsync(d_aj, S->aj.data(), nj * sizeof(BatchAdjJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok &= cudaMemcpyAsync(S->d_uf, S->uf.data(), S->uf.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
+          cudaSuccess;
+    ok &= cudaMemcpyAsync(S->d_ua, S->ua.data(), S->ua.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
+          cudaSuccess;
+    // triangle records, normalisers, bands
+    for (SJob* J : S->active) {
+        const Geom G = make_geom(&J->grid);
+        const Bufs& b = J->b;
+        int nb = 0;
+        ok &= launch_tri_prep<TriF32>(J->label, b.V, J->z.n_v, b.F, J->z.n_t, nullptr, G, (TriF32*)b.tris,
+                                      J->z.n_t_pad, b.partial, &nb, ctx->d_err, st) == cudaSuccess;
+        ok &= launch_sum(b.partial, nb, 1, 1, b.d_params + 16, st) == cudaSuccess;
+        g_launches += 2;
+        if (J->z.band) {
+            ok &= launch_band(b.d_params, J->psf.kind, J->psf.band_tau, J->grid.n[0], J->grid.n[1], J->grid.n[2], G,
+                              b.band_idx, b.dM, b.band_counts, st) == cudaSuccess;
+            g_launches += 3;
+        }
+    }
+    ok &= launch_fwd_batch_f32(d_fj, S->d_uf, (int)S->uf.size(), S->d_counter, S->grid_fwd, ctx->d_err, st) ==
+          cudaSuccess;
+    g_launches += 1;
+    // image, loss, adjoint records
+    for (SJob* J : S->active) {
+        const Geom G = make_geom(&J->grid);
+        const Bufs& b = J->b;
+        const Sizes& z = J->z;
+        FreqSrc fs;
+        fs.nlist = nullptr;
+        fs.idx = z.band ? b.band_idx : nullptr;
+        fs.dM = z.band ? b.dM : nullptr;
+        fs.M = z.nH;
+        fs.Nx = J->grid.n[0];
+        fs.Ny = J->grid.n[1];
+        fs.Nz = J->grid.n[2];
+        fs.Nzh = J->grid.n[2] / 2 + 1;
+        const int* n = J->grid.n;
+        int nl = 0, ng = 0;
+        ok &= launch_scatter<float>((const Cx<float>*)b.S, fs, b.d_params, J->psf.kind, b.d_params + 16, G,
+                                    (Cx<float>*)b.spec, z.band, st) == cudaSuccess;
+        ok &= launch_c2r<float>((const Cx<float>*)b.spec, (Cx<float>*)b.spec, (float*)b.image, n[0], n[1], n[2], J->ax,
+                                st) == cudaSuccess;
+        ok &= launch_loss<float>((const float*)b.image, (const float*)b.target, z.N, J->fit.loss, (float*)b.resid,
+                                 b.partial, &nl, st) == cudaSuccess;
+        ok &= launch_sum(b.partial, nl, 1, 1, b.d_params + 17, st) == cudaSuccess;
+        ok &= launch_r2c<float>((const float*)b.resid, (Cx<float>*)b.spec, n[0], n[1], n[2], J->ax, st) == cudaSuccess;
+        ok &= launch_gather<float, FreqF32>(J->label, (const Cx<float>*)b.spec, (const Cx<float>*)b.S, fs, b.d_params,
+                                            J->psf.kind, b.d_params + 16, G, (FreqF32*)b.fr, z.M_pad, b.partial, &ng,
+                                            st) == cudaSuccess;
+        ok &= launch_sum(b.partial, ng, 8, 8, b.d_params + 24, st) == cudaSuccess;
+        g_launches += 12;
+    }
+    ok &= launch_adj_batch_f32(d_aj, S->d_ua, (int)S->ua.size(), S->d_counter, S->grid_adj, ctx->d_err, st) ==
+          cudaSuccess;
+    g_launches += 1;
+    // per-vertex gradients and Adam
+    for (size_t j = 0; j < nj; ++j) {
+        SJob* J = S->active[j];
+        const Geom G = make_geom(&J->grid);
+        const Bufs& b = J->b;
+        const Sizes& z = J->z;
+        ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, st) ==
+              cudaSuccess;
+        ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, nullptr, G, b.acc, b.d_params + 30, b.contrib, st) ==
+              cudaSuccess;
+        ok &= launch_vertex_gather(b.ptr, b.ent, b.contrib, z.n_v, b.dV, st) == cudaSuccess;
+        ok &= cudaMemcpyAsync(J->hist + J->steps_done, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToDevice,
+                              st) == cudaSuccess;
+        ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, st) ==
+              cudaSuccess;
+        const dm_fit_options& o = J->fit;
+        ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps, J->steps_done + 1,
+                          st) == cudaSuccess;
+        g_launches += 4;
+        if (o.lr_psf > 0) {
+            ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
+                              J->steps_done + 1, st) == cudaSuccess;
+            g_launches += 1;
+        }
+    }
+    ok &= cudaStreamSynchronize(st) == cudaSuccess;
+    int h = 0;
+    ok &= cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (h) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        ok = false;
+    }
+    if (!ok) cudaGetLastError();
+    for (size_t j = 0; j < nj; ++j) {
+        S->active[j]->steps_done += 1;
+        S->active[j]->last_loss = S->h_loss[j];
+    }
+    return ok;
+}
+
+void finish_job(dm_server* S, SJob* J, int state) {
+    if (state == DM_JOB_DONE) {
+        const int64_t nV = 3 * J->z.n_v;
+        J->V_out.resize(nV);
+        J->hist_out.resize(J->fit.steps);
+        cudaMemcpy(J->V_out.data(), J->b.V, nV * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->sigma_out, J->b.d_params, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->hist_out.data(), J->hist, J->fit.steps * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    S->arena.release_block(J->off, J->bytes);
+    std::vector<double>().swap(J->V);
+    std::vector<int32_t>().swap(J->F);
+    std::vector<float>().swap(J->T);
+    std::lock_guard<std::mutex> lk(S->mu);
+    J->state = state;
+    J->t_end = S->now();
+    if (state == DM_JOB_DONE) S->stats.jobs_done += 1;
+}
+
+void engine_main(dm_server* S) {
+    cudaSetDevice(S->device);
+    while (true) {
+        // admission (FIFO; a job that does not fit yet blocks the ones behind it)
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
+            if (S->stop) break;
+        }
+        while ((int)S->active.size() < S->max_jobs) {
+            SJob* J = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                if (S->pending.empty()) break;
+                J = S->pending.front();
+            }
+            if (!setup_job(S, J)) break;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->pending.pop_front();
+                J->state = DM_JOB_RUNNING;
+                J->t_start = S->now();
+            }
+            S->active.push_back(J);
+            S->dirty = true;
+        }
+        if (S->active.empty()) continue;
+        S->stats.peak_active = std::max<int64_t>(S->stats.peak_active, (int64_t)S->active.size());
+        const double t_it = S->now();
+        const bool ok = iterate(S);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stats.iterations += 1;
+            S->stats.job_steps += (int64_t)S->active.size();
+            S->stats.busy_s += S->now() - t_it;
+        }
+        // retire
+        std::vector<SJob*> keep;
+        for (SJob* J : S->active) {
+            if (!ok)
+                finish_job(S, J, DM_JOB_FAILED);
+            else if (J->steps_done >= J->fit.steps)
+                finish_job(S, J, DM_JOB_DONE);
+            else
+                keep.push_back(J);
+        }
+        if (keep.size() != S->active.size()) S->dirty = true;
+        S->active.swap(keep);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stats.bytes_in_use = S->arena.in_use;
+            S->stats.bytes_peak = S->arena.peak;
+        }
+        S->cv.notify_all();
+    }
+    // shutdown: release whatever is still admitted
+    for (SJob* J : S->active) finish_job(S, J, DM_JOB_FAILED);
+    S->active.clear();
+    S->cv.notify_all();
+}
+
+dm_status validate_job(const dm_job* j) {
+    if (!j || !j->V || !j->F || !j->target || j->n_v < 3 || j->n_t < 1) return DM_ERR_ARG;
+    if (j->fit.steps < 1 || j->fit.loss < 0 || j->fit.loss > 2) return DM_ERR_ARG;
+    if (j->psf.kind != DM_PSF_DIAG) return DM_ERR_UNSUPPORTED;
+    if (j->label != DM_SURFACE && j->label != DM_VOLUME) return DM_ERR_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (!(j->psf.sigma[a] > 0) || !(j->grid.h[a] > 0) || j->grid.n[a] < 1) return DM_ERR_ARG;
+        FFTAxis ax;
+        if (!fft_factor(j->grid.n[a], ax)) return DM_ERR_UNSUPPORTED;
+    }
+    for (int64_t i = 0; i < 3 * j->n_t; ++i)
+        if (j->F[i] < 0 || j->F[i] >= j->n_v) return DM_ERR_ARG;
+    for (int64_t i = 0; i < 3 * j->n_v; ++i)
+        if (!std::isfinite(j->V[i])) return DM_ERR_ARG;
+    return DM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
+    if (!out || !opt || opt->max_jobs < 1) return DM_ERR_ARG;
+    *out = nullptr;
+    dm_options o{DM_FP32_MIXED, opt->device, 1, 0};
+    dm_ctx* ctx = nullptr;
+    dm_status s = dm_create(&ctx, &o);
+    if (s != DM_OK) return s;
+    dm_server* S = new dm_server();
+    S->ctx = ctx;
+    S->device = opt->device;
+    S->max_jobs = opt->max_jobs;
+    S->chunk_tiles = opt->chunk_tiles > 0 ? opt->chunk_tiles : 32;
+    S->t0 = std::chrono::steady_clock::now();
+    memset(&S->stats, 0, sizeof(S->stats));
+    DeviceGuard dg(opt->device);
+    size_t bytes = opt->memory_bytes;
+    if (bytes == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        bytes = fr / 2;
+    }
+    bool ok = S->arena.init(bytes) && cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&S->d_counter, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost(&S->h_loss, sizeof(double) * (size_t)S->max_jobs) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        S->arena.release();
+        if (S->st) cudaStreamDestroy(S->st);
+        if (S->d_counter) cudaFree(S->d_counter);
+        dm_destroy(ctx);
+        delete S;
+        return DM_ERR_OOM;
+    }
+    S->stats.bytes_total = S->arena.total;
+    const int sms = ctx->sm_count;
+    S->grid_fwd = sms * batch_blocks_per_sm_fwd();
+    S->grid_adj = sms * batch_blocks_per_sm_adj();
+    S->engine = std::thread(engine_main, S);
+    *out = S;
+    return DM_OK;
+}
+
+dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
+    if (!S || !job_id) return DM_ERR_ARG;
+    dm_status s = validate_job(job);
+    if (s != DM_OK) return s;
+    SJob* J = new SJob();
+    J->V.assign(job->V, job->V + 3 * job->n_v);
+    J->F.assign(job->F, job->F + 3 * job->n_t);
+    const int64_t N = (int64_t)job->grid.n[0] * job->grid.n[1] * job->grid.n[2];
+    J->T.assign(job->target, job->target + N);
+    J->grid = job->grid;
+    J->psf = job->psf;
+    J->fit = job->fit;
+    J->label = job->label;
+    // a job whose state can never fit the arena is refused now rather than queued forever
+    Sizes z = make_sizes(S->ctx, &job->grid, job->n_v, job->n_t, job->psf.band_tau > 0, job->label);
+    const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
+    z.n_chunks = (int)((ftiles + S->chunk_tiles - 1) / S->chunk_tiles);
+    Arena A;
+    Bufs b;
+    double *mom, *hist;
+    if (job_layout(z, job->fit.steps, job->n_v, A, b, &mom, &hist) > S->arena.total) {
+        delete J;
+        return DM_ERR_OOM;
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        J->id = S->next_id++;
+        J->t_submit = S->now();
+        S->jobs[J->id] = J;
+        S->pending.push_back(J);
+        *job_id = J->id;
+    }
+    S->cv.notify_all();
+    return DM_OK;
+}
+
+dm_status dm_server_status(dm_server* S, int64_t id, dm_job_status* out) {
+    if (!S || !out) return DM_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(id);
+    if (it == S->jobs.end()) return DM_ERR_ARG;
+    const SJob* J = it->second;
+    out->state = J->state;
+    out->steps_done = J->steps_done;
+    out->t_submit = J->t_submit;
+    out->t_start = J->t_start;
+    out->t_end = J->t_end;
+    out->last_loss = J->last_loss;
+    return DM_OK;
+}
+
+dm_status dm_server_wait(dm_server* S, int64_t id, double timeout_s) {
+    if (!S) return DM_ERR_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->jobs.find(id);
+    if (it == S->jobs.end()) return DM_ERR_ARG;
+    SJob* J = it->second;
+    auto done = [&] { return J->state == DM_JOB_DONE || J->state == DM_JOB_FAILED || S->stop; };
+    if (timeout_s < 0)
+        S->cv.wait(lk, done);
+    else if (!S->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), done))
+        return DM_ERR_TIMEOUT;
+    return J->state == DM_JOB_DONE ? DM_OK : DM_ERR_CUDA;
+}
+
+dm_status dm_server_result(dm_server* S, int64_t id, double* V_out, double* sigma_out, double* loss_history) {
+    if (!S) return DM_ERR_ARG;
+    SJob* J = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->jobs.find(id);
+        if (it == S->jobs.end()) return DM_ERR_ARG;
+        J = it->second;
+        if (J->state != DM_JOB_DONE) return J->state == DM_JOB_FAILED ? DM_ERR_CUDA : DM_ERR_ARG;
+        S->jobs.erase(it);
+    }
+    if (V_out) memcpy(V_out, J->V_out.data(), J->V_out.size() * sizeof(double));
+    if (sigma_out) memcpy(sigma_out, J->sigma_out, 3 * sizeof(double));
+    if (loss_history) memcpy(loss_history, J->hist_out.data(), J->hist_out.size() * sizeof(double));
+    delete J;
+    return DM_OK;
+}
+
+dm_status dm_server_get_stats(dm_server* S, dm_server_stats* out) {
+    if (!S || !out) return DM_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    return DM_OK;
+}
+
+double dm_server_clock(const dm_server* S) { return S ? S->now() : 0.0; }
+
+dm_status dm_server_shutdown(dm_server* S) {
+    if (!S) return DM_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->engine.joinable()) S->engine.join();
+    DeviceGuard dg(S->device);
+    cudaStreamSynchronize(S->st);
+    for (auto& kv : S->jobs) delete kv.second;  // queued, finished and unclaimed jobs
+    S->arena.release();
+    cudaFree(S->d_fj);
+    cudaFree(S->d_aj);
+    cudaFree(S->d_uf);
+    cudaFree(S->d_ua);
+    cudaFree(S->d_counter);
+    cudaFreeHost(S->h_loss);
+    cudaStreamDestroy(S->st);
+    dm_destroy(S->ctx);
+    delete S;
+    return DM_OK;
+}
+
+}  // extern "C"

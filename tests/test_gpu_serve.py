@@ -1,0 +1,158 @@
+"""Continuous-batching fit server: a job's result is the same alone and in a mix, late
+arrivals join running batches, admission waits for device memory, invalid jobs are refused."""
+
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 6
+
+
+def _jobs(r32):
+    """Five uneven jobs: grids 32^3-64^3, icosphere levels 2-3, targets rendered from SH-deformed cells."""
+    specs = [((64, 64, 64), 3, 7.0), ((32, 32, 32), 2, 4.0), ((48, 48, 48), 3, 5.0), ((64, 64, 32), 2, 6.0),
+             ((40, 40, 40), 3, 4.5)]
+    jobs = []
+    for k, (n, lev, R) in enumerate(specs):
+        grid = synth.Grid(n=n, h=(0.5, 0.5, 1.0) if n[2] == n[0] else (0.5, 0.5, 2.0))
+        R = min(R, 0.3 * float(min(grid.L)))
+        V_t, F = synth.sh_deformed_sphere(lev, R, grid.center, lmax=4, coef_sigma=0.04 * R, seed=40 + k)
+        V0, _ = synth.sphere_mesh(lev, R, grid.center)
+        psf = synth.Psf(sigma=(0.4, 0.4, 0.9), band_tau=1e-3)
+        T = r32.render(torch.as_tensor(V_t).cuda(), torch.as_tensor(F).cuda(), grid, psf).cpu().numpy()
+        jobs.append(dict(V=V0, F=F, target=T, grid=grid, psf=psf, steps=STEPS, lr_vertex=0.02))
+    return jobs
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2303_10440_b300 import Renderer
+
+    r32 = Renderer("fp32")
+    jobs = _jobs(r32)
+    yield r32, jobs
+    r32.close()
+
+
+def _run(server, jobs, order, late=()):
+    ids = {}
+    for k in order:
+        ids[k] = server.submit(**jobs[k])
+    if late:
+        # wait until the batch is running, then add more jobs
+        first = ids[order[0]]
+        t_end = time.time() + 60
+        while server.status(first)["steps_done"] < 1 and time.time() < t_end:
+            time.sleep(0.001)
+        for k in late:
+            ids[k] = server.submit(**jobs[k])
+    out = {}
+    for k, i in ids.items():
+        assert server.wait(i, timeout=300)
+        out[k] = server.result(i)
+    return out
+
+
+def test_result_is_the_same_alone_and_in_the_mix(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    s1 = FitServer(max_jobs=8)
+    alone = _run(s1, jobs, [0])[0]
+    s1.shutdown()
+    s2 = FitServer(max_jobs=8)
+    mix = _run(s2, jobs, [1, 2, 0], late=[3, 4])
+    st = s2.stats()
+    s2.shutdown()
+    assert st["peak_active"] >= 3
+    assert np.array_equal(alone.V, mix[0].V)
+    assert np.array_equal(alone.loss_history, mix[0].loss_history)
+    print(f"\n[serve] alone == in mix (bitwise); peak batch {st['peak_active']}, iterations {st['iterations']}")
+
+
+def test_served_fit_matches_the_standalone_fit(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    s = FitServer(max_jobs=4)
+    res = _run(s, jobs, [0, 1])
+    s.shutdown()
+    for k in (0, 1):
+        j = jobs[k]
+        Vf, sig, hist = r32.fit(torch.as_tensor(j["V"]).cuda(), torch.as_tensor(j["F"]).cuda(), j["grid"], j["psf"],
+                                torch.as_tensor(j["target"]).cuda(), steps=STEPS, lr_vertex=j["lr_vertex"])
+        Vf = Vf.cpu().numpy()
+        moved = np.linalg.norm(Vf - j["V"])
+        assert moved > 0
+        assert np.linalg.norm(res[k].V - Vf) < 1e-3 * moved
+        assert np.allclose(res[k].loss_history, hist.numpy(), rtol=1e-4)
+
+
+def test_late_arrivals_join_running_batches(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    long_job = dict(jobs[0], steps=60)
+    s = FitServer(max_jobs=8)
+    a = s.submit(**long_job)
+    deadline = time.time() + 120
+    while s.status(a)["steps_done"] < 2 and time.time() < deadline:
+        time.sleep(0.001)
+    b = s.submit(**jobs[1])
+    c = s.submit(**jobs[2])
+    for i in (a, b, c):
+        assert s.wait(i, timeout=300)
+    ra, rb, rc = s.result(a), s.result(b), s.result(c)
+    s.shutdown()
+    # b and c were admitted and finished while a was still running
+    assert rb.t_start < ra.t_end and rc.t_start < ra.t_end
+    assert rb.t_end < ra.t_end
+
+
+def test_admission_waits_for_device_memory(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    j = jobs[1]  # 32^3 job
+    probe = FitServer(max_jobs=1)
+    i = probe.submit(**j)
+    assert probe.wait(i, timeout=300)
+    one_job = probe.stats()["bytes_peak"]  # arena bytes one such job holds
+    probe.shutdown()
+    s = FitServer(max_jobs=8, memory_bytes=int(one_job * 1.5))
+    ids = [s.submit(**j) for _ in range(3)]
+    res = [None] * 3
+    for k, i in enumerate(ids):
+        assert s.wait(i, timeout=300)
+        res[k] = s.result(i)
+    st = s.stats()
+    with pytest.raises(RuntimeError, match="DM_ERR_OOM"):
+        s.submit(**jobs[0])  # a 64^3 job can never fit this arena
+    s.shutdown()
+    assert st["peak_active"] == 1
+    for k in (1, 2):
+        assert res[k].t_start >= res[k - 1].t_end
+    assert np.array_equal(res[0].V, res[1].V) and np.array_equal(res[1].V, res[2].V)
+
+
+def test_invalid_jobs_are_refused(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    s = FitServer(max_jobs=2)
+    bad = dict(jobs[1])
+    F = bad["F"].copy()
+    F[0, 0] = 10**6
+    bad["F"] = F
+    with pytest.raises(RuntimeError, match="DM_ERR_ARG"):
+        s.submit(**bad)
+    bad = dict(jobs[1], grid=synth.Grid(n=(14, 14, 14), h=(1, 1, 1)))
+    with pytest.raises(RuntimeError, match="DM_ERR_UNSUPPORTED"):
+        s.submit(**bad)
+    s.shutdown()
