@@ -52,6 +52,7 @@ def parse():
                    help="fp32: the FP32 mixed path (headline); fp64: the plain FP64 path (comparator)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     return p.parse_args()
 
 
@@ -230,6 +231,132 @@ def workload_config(case, M, l2):
     }
 
 
+# ----------------------------------------------------------------------------- serving
+def serving_jobs(r32, n_jobs, seed, levels, sides, steps):
+    """Fit requests drawn like the serving workload (random icosphere level, grid side and
+    anisotropic sigma; target = render of an SH-deformed cell), restricted to `levels`/`sides`."""
+    import torch
+
+    import synth
+
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for k in range(n_jobs):
+        lev = int(rng.choice(levels))
+        side = int(rng.choice(sides))
+        grid = synth.Grid(n=(side, side, side), h=(0.5, 0.5, 1.0))
+        sxy, sz = float(rng.uniform(0.15, 0.3)), float(rng.uniform(0.4, 0.9))
+        R = 0.3 * float(min(grid.L))
+        V_t, F = synth.sh_deformed_sphere(lev, R, grid.center, lmax=6, coef_sigma=0.03 * R, seed=10_000 + k)
+        V0, _ = synth.sphere_mesh(lev, R, grid.center)
+        psf = synth.Psf(sigma=(sxy, sxy, sz), band_tau=1e-3)
+        T = r32.render(torch.as_tensor(V_t).cuda(), torch.as_tensor(F).cuda(), grid, psf).cpu().numpy()
+        jobs.append(dict(V=V0, F=F, target=T, grid=grid, psf=psf, steps=steps, lr_vertex=1e-2 * min(grid.h)))
+    return jobs
+
+
+def _queue_latencies(arrivals, durations):
+    """One job at a time in arrival order: completion = max(arrival, previous completion) + duration."""
+    t, lat = 0.0, []
+    for a, d in zip(arrivals, durations):
+        t = max(t, a) + d
+        lat.append(t - a)
+    return np.array(lat), t - arrivals[0]
+
+
+def _stats(lat, span, n):
+    return {"fits_per_s": n / span, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "span_s": span}
+
+
+def _served_run(jobs, arrivals, dev):
+    import threading
+
+    from paper_2303_10440_b300.serve import FitServer
+
+    srv = FitServer(device=dev.index or 0, max_jobs=32)
+    ids = [None] * len(jobs)
+    t0 = srv.clock()
+
+    def feeder():
+        for k, j in enumerate(jobs):
+            delay = t0 + arrivals[k] - srv.clock()
+            if delay > 0:
+                time.sleep(delay)
+            ids[k] = srv.submit(**j)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    res = []
+    for i in ids:
+        srv.wait(i, timeout=600)
+        res.append(srv.result(i))
+    st = srv.stats()
+    srv.shutdown()
+    lat = np.array([r.latency for r in res])
+    span = max(r.t_end for r in res) - min(r.t_submit for r in res)
+    return dict(_stats(lat, span, len(jobs)), peak_batch=int(st["peak_active"]), iterations=int(st["iterations"]))
+
+
+def serving_leg(args, dev, n_jobs=16, rates=(10.0, 50.0, 500.0), steps=10, levels=(2, 3), sides=(32, 48, 64),
+                with_fp64=True):
+    """Served fits/s and p50/p99 latency vs one-job-at-a-time FP32 and plain FP64 at each arrival rate.
+
+    The one-at-a-time durations are measured once per job; their latencies at each rate follow
+    from the same arrival times (completion = max(arrival, previous completion) + duration)."""
+    import torch
+
+    from paper_2303_10440_b300 import Renderer
+
+    r32 = Renderer("fp32", device=dev.index or 0)
+    jobs = serving_jobs(r32, n_jobs, 5, levels, sides, steps)
+    legs = [("sequential_fp32", r32)]
+    if with_fp64:
+        legs.append(("plain_fp64", Renderer("fp64", device=dev.index or 0)))
+    durations = {}
+    for name, r in legs:
+        durs = []
+        for j in jobs:
+            Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
+            Td = torch.as_tensor(j["target"]).to(dev)
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter()
+            r.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=steps, lr_vertex=j["lr_vertex"])
+            torch.cuda.synchronize(dev)
+            durs.append(time.perf_counter() - t)
+        durations[name] = durs
+    out = {
+        "workload": f"{n_jobs} fit requests, icosphere levels {list(levels)}, cubic grids {list(sides)} of "
+        f"(0.5, 0.5, 1) um, sigma_xy~U(0.15,0.3) um, sigma_z~U(0.4,0.9) um, {steps} Adam steps each, "
+        f"open-loop Poisson arrivals",
+        "one_at_a_time_note": "sequential_fp32 / plain_fp64: each job alone through dm_fit (FP32 / FP64 context), "
+        "durations measured once, queued in arrival order",
+        "rates": {},
+    }
+    for rate in rates:
+        rng = np.random.default_rng(6)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
+        arrivals -= arrivals[0]
+        entry = {"served_fp32": _served_run(jobs, arrivals, dev)}
+        for name, durs in durations.items():
+            lat, span = _queue_latencies(arrivals, durs)
+            entry[name] = _stats(lat, span, n_jobs)
+        out["rates"][f"{rate:g}/s"] = entry
+    if with_fp64:
+        r64 = legs[-1][1]
+        errs = []
+        for j in jobs:
+            Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
+            a = r32.render(Vd, Fd, j["grid"], j["psf"]).double()
+            b = r64.render(Vd, Fd, j["grid"], j["psf"])
+            errs.append(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)))
+        out["max_render_rel_err_fp32_vs_fp64"] = max(errs)
+        r64.close()
+    r32.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -354,6 +481,8 @@ def run_ours(args):
 
     if not args.no_e2e:
         out["e2e"] = e2e_through_host_buffers(r, case, grid, psf, T, terms_step, args, dev, world)
+    if not args.no_serve:
+        out["serving"] = serving_leg(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(case)
     if rank == 0:

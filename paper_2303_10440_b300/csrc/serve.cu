@@ -98,10 +98,26 @@ struct SJob {
     Bufs b;
     double *mV = nullptr, *vV = nullptr, *ms = nullptr, *vs = nullptr, *hist = nullptr;
     FFTAxis ax[3];
+    int chunk_tiles = 1;
+    cudaStream_t stream = nullptr;  // the job's stream for its own stage kernels (held while admitted)
+    cudaEvent_t ev = nullptr;       // marks the end of the job's stage work within an iteration
     // results
     std::vector<double> V_out, hist_out;
     double sigma_out[3] = {0, 0, 0};
 };
+
+// Adjoint frequency tiles per work unit for a job: small enough that the job alone yields about
+// 8 units per SM, at most max_tiles. It depends only on the job's own sizes, so a job's results
+// do not depend on the other jobs in its iterations.
+int job_chunk_tiles(const Sizes& z, int max_tiles, int sm_count) {
+    const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
+    const int64_t tblocks = z.n_t_pad / ADJ_THREADS;
+    const int64_t target = 8 * (int64_t)sm_count;
+    int64_t c = (ftiles * tblocks + target - 1) / target;
+    if (c < 1) c = 1;
+    if (c > max_tiles) c = max_tiles;
+    return (int)c;
+}
 
 size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, double** mom, double** hist) {
     layout(z, A, b, true, true, false, true, false);
@@ -139,6 +155,9 @@ struct dm_server {
     int* d_counter = nullptr;
     double* h_loss = nullptr;  // pinned, one per batch slot
     int grid_fwd = 0, grid_adj = 0;
+    std::vector<std::pair<cudaStream_t, cudaEvent_t>> free_streams;  // job streams not in use
+    cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr;                  // after each batched launch
+    int64_t since_sync = 0;
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
@@ -165,7 +184,8 @@ bool setup_job(dm_server* S, SJob* J) {
     Sizes z = make_sizes(ctx, &J->grid, (int64_t)J->V.size() / 3, (int64_t)J->F.size() / 3, J->psf.band_tau > 0,
                          J->label);
     const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
-    z.n_chunks = (int)((ftiles + S->chunk_tiles - 1) / S->chunk_tiles);  // fixed per job
+    J->chunk_tiles = job_chunk_tiles(z, S->chunk_tiles, ctx->sm_count);
+    z.n_chunks = (int)((ftiles + J->chunk_tiles - 1) / J->chunk_tiles);  // fixed per job
     Arena A;
     Bufs b;
     double *mom, *hist;
@@ -184,7 +204,21 @@ bool setup_job(dm_server* S, SJob* J) {
     J->ms = mom + 6 * z.n_v;
     J->vs = J->ms + 4;
     J->hist = hist;
-    cudaStream_t st = S->st;
+    if (S->free_streams.empty()) {
+        cudaStream_t js;
+        cudaEvent_t je;
+        if (cudaStreamCreateWithFlags(&js, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&je, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            S->arena.release_block(off, bytes);
+            return false;
+        }
+        S->free_streams.push_back({js, je});
+    }
+    J->stream = S->free_streams.back().first;
+    J->ev = S->free_streams.back().second;
+    S->free_streams.pop_back();
+    cudaStream_t st = J->stream;
     bool ok = cudaMemcpyAsync(b.V, J->V.data(), J->V.size() * sizeof(double), cudaMemcpyHostToDevice, st) ==
                   cudaSuccess &&
               cudaMemcpyAsync(b.F, J->F.data(), J->F.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st) ==
@@ -200,6 +234,7 @@ bool setup_job(dm_server* S, SJob* J) {
     if (!ok) {
         cudaGetLastError();
         S->arena.release_block(off, bytes);
+        S->free_streams.push_back({J->stream, J->ev});
         return false;
     }
     return true;
@@ -240,7 +275,7 @@ bool rebuild_units(dm_server* S) {
         a.dM = z.band ? b.dM : nullptr;
         a.M_max = z.M_max;
         a.mode = J->label;
-        a.chunk_tiles = S->chunk_tiles;
+        a.chunk_tiles = J->chunk_tiles;
         a.partial = (float*)b.adjp;
         order[j] = (int)j;
     }
@@ -265,41 +300,47 @@ bool rebuild_units(dm_server* S) {
     return ok;
 }
 
-// One Adam step of every active job. Returns false on a device fault.
-bool iterate(dm_server* S) {
+// Enqueue one Adam step of every active job. Each job's own stage kernels run on its stream;
+// the two batched launches run on the server stream after every job's preceding stage (events).
+// Synchronises only when `sync` is set; returns false on a device fault seen at a sync.
+bool iterate(dm_server* S, bool sync) {
     dm_ctx* ctx = S->ctx;
     cudaStream_t st = S->st;
     if (S->dirty && !rebuild_units(S)) return false;
     const size_t nj = S->active.size();
-    BatchFwdJob* d_fj = S->d_fj;
-    BatchAdjJob* d_aj = S->d_aj;
     bool ok = true;
-    ok &= cudaMemcpyAsync(d_fj, S->fj.data(), nj * sizeof(BatchFwdJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
-    ok &= cudaMemcpyAsync(d_aj, S->aj.data(), nj * sizeof(BatchAdjJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok &= cudaMemcpyAsync(S->d_fj, S->fj.data(), nj * sizeof(BatchFwdJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok &= cudaMemcpyAsync(S->d_aj, S->aj.data(), nj * sizeof(BatchAdjJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
     ok &= cudaMemcpyAsync(S->d_uf, S->uf.data(), S->uf.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
           cudaSuccess;
     ok &= cudaMemcpyAsync(S->d_ua, S->ua.data(), S->ua.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
           cudaSuccess;
     // triangle records, normalisers, bands
     for (SJob* J : S->active) {
+        cudaStream_t js = J->stream;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         int nb = 0;
         ok &= launch_tri_prep<TriF32>(J->label, b.V, J->z.n_v, b.F, J->z.n_t, nullptr, G, (TriF32*)b.tris,
-                                      J->z.n_t_pad, b.partial, &nb, ctx->d_err, st) == cudaSuccess;
-        ok &= launch_sum(b.partial, nb, 1, 1, b.d_params + 16, st) == cudaSuccess;
+                                      J->z.n_t_pad, b.partial, &nb, ctx->d_err, js) == cudaSuccess;
+        ok &= launch_sum(b.partial, nb, 1, 1, b.d_params + 16, js) == cudaSuccess;
         g_launches += 2;
         if (J->z.band) {
             ok &= launch_band(b.d_params, J->psf.kind, J->psf.band_tau, J->grid.n[0], J->grid.n[1], J->grid.n[2], G,
-                              b.band_idx, b.dM, b.band_counts, st) == cudaSuccess;
+                              b.band_idx, b.dM, b.band_counts, js) == cudaSuccess;
             g_launches += 3;
         }
+        ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
+        ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
     }
-    ok &= launch_fwd_batch_f32(d_fj, S->d_uf, (int)S->uf.size(), S->d_counter, S->grid_fwd, ctx->d_err, st) ==
+    ok &= launch_fwd_batch_f32(S->d_fj, S->d_uf, (int)S->uf.size(), S->d_counter, S->grid_fwd, ctx->d_err, st) ==
           cudaSuccess;
+    ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
     g_launches += 1;
     // image, loss, adjoint records
     for (SJob* J : S->active) {
+        cudaStream_t js = J->stream;
+        ok &= cudaStreamWaitEvent(js, S->ev_fwd, 0) == cudaSuccess;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         const Sizes& z = J->z;
@@ -315,59 +356,68 @@ bool iterate(dm_server* S) {
         const int* n = J->grid.n;
         int nl = 0, ng = 0;
         ok &= launch_scatter<float>((const Cx<float>*)b.S, fs, b.d_params, J->psf.kind, b.d_params + 16, G,
-                                    (Cx<float>*)b.spec, z.band, st) == cudaSuccess;
+                                    (Cx<float>*)b.spec, z.band, js) == cudaSuccess;
         ok &= launch_c2r<float>((const Cx<float>*)b.spec, (Cx<float>*)b.spec, (float*)b.image, n[0], n[1], n[2], J->ax,
-                                st) == cudaSuccess;
+                                js) == cudaSuccess;
         ok &= launch_loss<float>((const float*)b.image, (const float*)b.target, z.N, J->fit.loss, (float*)b.resid,
-                                 b.partial, &nl, st) == cudaSuccess;
-        ok &= launch_sum(b.partial, nl, 1, 1, b.d_params + 17, st) == cudaSuccess;
-        ok &= launch_r2c<float>((const float*)b.resid, (Cx<float>*)b.spec, n[0], n[1], n[2], J->ax, st) == cudaSuccess;
+                                 b.partial, &nl, js) == cudaSuccess;
+        ok &= launch_sum(b.partial, nl, 1, 1, b.d_params + 17, js) == cudaSuccess;
+        ok &= launch_r2c<float>((const float*)b.resid, (Cx<float>*)b.spec, n[0], n[1], n[2], J->ax, js) == cudaSuccess;
         ok &= launch_gather<float, FreqF32>(J->label, (const Cx<float>*)b.spec, (const Cx<float>*)b.S, fs, b.d_params,
                                             J->psf.kind, b.d_params + 16, G, (FreqF32*)b.fr, z.M_pad, b.partial, &ng,
-                                            st) == cudaSuccess;
-        ok &= launch_sum(b.partial, ng, 8, 8, b.d_params + 24, st) == cudaSuccess;
+                                            js) == cudaSuccess;
+        ok &= launch_sum(b.partial, ng, 8, 8, b.d_params + 24, js) == cudaSuccess;
         g_launches += 12;
+        ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
+        ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
     }
-    ok &= launch_adj_batch_f32(d_aj, S->d_ua, (int)S->ua.size(), S->d_counter, S->grid_adj, ctx->d_err, st) ==
+    ok &= launch_adj_batch_f32(S->d_aj, S->d_ua, (int)S->ua.size(), S->d_counter, S->grid_adj, ctx->d_err, st) ==
           cudaSuccess;
+    ok &= cudaEventRecord(S->ev_adj, st) == cudaSuccess;
     g_launches += 1;
     // per-vertex gradients and Adam
     for (size_t j = 0; j < nj; ++j) {
         SJob* J = S->active[j];
+        cudaStream_t js = J->stream;
+        ok &= cudaStreamWaitEvent(js, S->ev_adj, 0) == cudaSuccess;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         const Sizes& z = J->z;
-        ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, st) ==
+        ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, js) ==
               cudaSuccess;
-        ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, nullptr, G, b.acc, b.d_params + 30, b.contrib, st) ==
+        ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, nullptr, G, b.acc, b.d_params + 30, b.contrib, js) ==
               cudaSuccess;
-        ok &= launch_vertex_gather(b.ptr, b.ent, b.contrib, z.n_v, b.dV, st) == cudaSuccess;
+        ok &= launch_vertex_gather(b.ptr, b.ent, b.contrib, z.n_v, b.dV, js) == cudaSuccess;
         ok &= cudaMemcpyAsync(J->hist + J->steps_done, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToDevice,
-                              st) == cudaSuccess;
-        ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, st) ==
+                              js) == cudaSuccess;
+        ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, js) ==
               cudaSuccess;
         const dm_fit_options& o = J->fit;
         ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps, J->steps_done + 1,
-                          st) == cudaSuccess;
+                          js) == cudaSuccess;
         g_launches += 4;
         if (o.lr_psf > 0) {
             ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
-                              J->steps_done + 1, st) == cudaSuccess;
+                              J->steps_done + 1, js) == cudaSuccess;
             g_launches += 1;
         }
+        // the next iteration's batched launches on the server stream also follow this job's Adam
+        ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
+        ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
     }
-    ok &= cudaStreamSynchronize(st) == cudaSuccess;
-    int h = 0;
-    ok &= cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
-    if (h) {
-        cudaMemset(ctx->d_err, 0, sizeof(int));
-        ok = false;
+    for (size_t j = 0; j < nj; ++j) S->active[j]->steps_done += 1;
+    if (sync) {
+        ok &= cudaStreamSynchronize(st) == cudaSuccess;
+        for (SJob* J : S->active) ok &= cudaStreamSynchronize(J->stream) == cudaSuccess;
+        int h = 0;
+        ok &= cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+        if (h) {
+            cudaMemset(ctx->d_err, 0, sizeof(int));
+            ok = false;
+        }
+        for (size_t j = 0; j < nj; ++j) S->active[j]->last_loss = S->h_loss[j];
     }
     if (!ok) cudaGetLastError();
-    for (size_t j = 0; j < nj; ++j) {
-        S->active[j]->steps_done += 1;
-        S->active[j]->last_loss = S->h_loss[j];
-    }
     return ok;
 }
 
@@ -381,6 +431,8 @@ void finish_job(dm_server* S, SJob* J, int state) {
         cudaMemcpy(J->hist_out.data(), J->hist, J->fit.steps * sizeof(double), cudaMemcpyDeviceToHost);
     }
     S->arena.release_block(J->off, J->bytes);
+    if (J->stream) S->free_streams.push_back({J->stream, J->ev});
+    J->stream = nullptr;
     std::vector<double>().swap(J->V);
     std::vector<int32_t>().swap(J->F);
     std::vector<float>().swap(J->T);
@@ -419,7 +471,10 @@ void engine_main(dm_server* S) {
         if (S->active.empty()) continue;
         S->stats.peak_active = std::max<int64_t>(S->stats.peak_active, (int64_t)S->active.size());
         const double t_it = S->now();
-        const bool ok = iterate(S);
+        bool sync = ++S->since_sync >= 16;
+        for (SJob* J : S->active) sync = sync || J->steps_done + 1 >= J->fit.steps;
+        if (sync) S->since_sync = 0;
+        const bool ok = iterate(S, sync);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->stats.iterations += 1;
@@ -495,7 +550,9 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     }
     bool ok = S->arena.init(bytes) && cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) == cudaSuccess &&
               cudaMalloc(&S->d_counter, sizeof(int)) == cudaSuccess &&
-              cudaMallocHost(&S->h_loss, sizeof(double) * (size_t)S->max_jobs) == cudaSuccess;
+              cudaMallocHost(&S->h_loss, sizeof(double) * (size_t)S->max_jobs) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S->ev_fwd, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S->ev_adj, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         S->arena.release();
@@ -530,7 +587,8 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     // a job whose state can never fit the arena is refused now rather than queued forever
     Sizes z = make_sizes(S->ctx, &job->grid, job->n_v, job->n_t, job->psf.band_tau > 0, job->label);
     const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
-    z.n_chunks = (int)((ftiles + S->chunk_tiles - 1) / S->chunk_tiles);
+    const int ct = job_chunk_tiles(z, S->chunk_tiles, S->ctx->sm_count);
+    z.n_chunks = (int)((ftiles + ct - 1) / ct);
     Arena A;
     Bufs b;
     double *mom, *hist;
@@ -624,6 +682,12 @@ dm_status dm_server_shutdown(dm_server* S) {
     cudaFree(S->d_ua);
     cudaFree(S->d_counter);
     cudaFreeHost(S->h_loss);
+    for (auto& p : S->free_streams) {
+        cudaStreamDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    if (S->ev_fwd) cudaEventDestroy(S->ev_fwd);
+    if (S->ev_adj) cudaEventDestroy(S->ev_adj);
     cudaStreamDestroy(S->st);
     dm_destroy(S->ctx);
     delete S;
