@@ -53,6 +53,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5"], default="step",
+                   help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
+                   "serve-c5: Poisson stream of serving requests")
+    p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 10)")
+    p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
     return p.parse_args()
 
 
@@ -69,6 +74,20 @@ def make_case(name):
         c.name = "c2s_cell_sh6_64cube_profile"
         return c
     return synth.config_c1()
+
+
+def whole_job_value(t_ms_local: float, terms_per_rank: float, world: int, device=None):
+    """Max of the ranks' timed-region durations (ms) and the whole-job rate: every rank processes
+    terms_per_rank terms in the timed region (weak scaling: independent fits, no data exchange)."""
+    import torch
+
+    t = torch.tensor([t_ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return world * terms_per_rank / (t_max / 1e3), t_max
 
 
 def dist_env():
@@ -427,11 +446,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = world * terms_step * args.steps / (t_max / 1e3)
+    value, t_max = whole_job_value(t_ms, terms_step * args.steps, world, dev)
 
     # roofline of the dominant kernel (event-timed inside the library on this stream)
     dom = max(("fwd", "adj"), key=lambda s: stages[s][0])
@@ -526,8 +541,112 @@ def e2e_through_host_buffers(r, case, grid, psf, T_dev, terms_step, args, dev, w
     }
 
 
+def _job_terms(j):
+    n = j["grid"].n
+    return 2.0 * n[0] * n[1] * (n[2] // 2 + 1) * j["F"].shape[0] * j["steps"]
+
+
+def _one_at_a_time(r, jobs, dev):
+    import torch
+
+    durs = []
+    for j in jobs:
+        Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
+        Td = torch.as_tensor(j["target"]).to(dev)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        r.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=j["steps"], lr_vertex=j["lr_vertex"])
+        torch.cuda.synchronize(dev)
+        durs.append(time.perf_counter() - t)
+    return durs
+
+
+def _fp64_rate(jobs, dev):
+    """Plain FP64 terms/s measured on one step of the smallest job (the FP64 path is ~100x slower)."""
+    import torch
+
+    from paper_2303_10440_b300 import Renderer
+
+    j = min(jobs, key=_job_terms)
+    r64 = Renderer("fp64", device=dev.index or 0)
+    Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
+    Td = torch.as_tensor(j["target"]).to(dev)
+    r64.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=1, lr_vertex=j["lr_vertex"])
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    r64.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=2, lr_vertex=j["lr_vertex"])
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t
+    r64.close()
+    return _job_terms(dict(j, steps=2)) / dt
+
+
+def run_serve_mode(args):
+    import torch
+
+    import synth
+    from paper_2303_10440_b300 import Renderer
+
+    dev = torch.device("cuda", 0)
+    r32 = Renderer("fp32")
+    if args.mode == "serve-c4":
+        steps = args.fit_steps or 20
+        _, cells = synth.config_c4_cells()
+        jobs = []
+        for k, c in enumerate(cells):
+            T = r32.render(torch.as_tensor(c["V_true"]).to(dev), torch.as_tensor(c["F"]).to(dev), c["grid"],
+                           c["psf"]).cpu().numpy()
+            noisy, scale = synth.add_poisson_gaussian_noise(T, 200.0, 2.0, seed=500 + k)
+            jobs.append(dict(V=c["V_init"], F=c["F"], target=noisy / scale, grid=c["grid"], psf=c["psf"], steps=steps,
+                             lr_vertex=1e-2 * min(c["grid"].h)))
+        arrivals = np.zeros(len(jobs))
+        workload = (f"32 SH-deformed cells packed in a 256^3 tissue (levels 3-5, radii 8-20 um), one fit per cell "
+                    f"on its 64^3-128^3 crop, Poisson(peak 200) + N(0, 2^2) noise, {steps} Adam steps, all jobs "
+                    f"submitted together (one persistent batched launch per iteration)")
+        rates = {"batch": arrivals}
+    else:
+        steps = args.fit_steps or 10
+        rng = np.random.default_rng(55)
+        jobs = []
+        for k in range(args.jobs):
+            c = synth.config_c5_job(rng, k)
+            T = r32.render(torch.as_tensor(c["V_true"]).to(dev), torch.as_tensor(c["F"]).to(dev), c["grid"],
+                           c["psf"]).cpu().numpy()
+            jobs.append(dict(V=c["V_init"], F=c["F"], target=T, grid=c["grid"], psf=c["psf"], steps=steps,
+                             lr_vertex=1e-2 * min(c["grid"].h)))
+        workload = (f"{len(jobs)} serving requests (levels 2-6 = 320-81920 triangles, cubic grids 64-256 of "
+                    f"(0.5, 0.5, 1) um, random anisotropic sigma), {steps} Adam steps each (reduced from 100 to bound "
+                    f"the run), open-loop Poisson arrivals")
+        rates = {}
+        for rate in (10.0, 100.0, 500.0):
+            r = np.random.default_rng(7)
+            a = np.cumsum(r.exponential(1.0 / rate, size=len(jobs)))
+            rates[f"{rate:g}/s"] = a - a[0]
+    total_terms = sum(_job_terms(j) for j in jobs)
+    durs = _one_at_a_time(r32, jobs, dev)
+    fp64 = _fp64_rate(jobs, dev)
+    out = {"metric": "served fits/s and p50/p99 latency vs one-at-a-time FP32 and plain FP64", "mode": args.mode,
+           "workload": workload, "n_jobs": len(jobs), "total_terms": total_terms, "results": {}}
+    fp64_durs = [_job_terms(j) / fp64 for j in jobs]
+    for name, arr in rates.items():
+        served = _served_run(jobs, arr, dev)
+        served["terms_per_s"] = total_terms / served["span_s"]
+        lat, span = _queue_latencies(arr, durs)
+        lat64, span64 = _queue_latencies(arr, fp64_durs)
+        out["results"][name] = {
+            "served_fp32": served,
+            "sequential_fp32": dict(_stats(lat, span, len(jobs)), terms_per_s=total_terms / span),
+            "plain_fp64_from_measured_rate": dict(_stats(lat64, span64, len(jobs)), terms_per_s=fp64),
+        }
+    out["plain_fp64_terms_per_s_measured"] = fp64
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode != "step":
+        run_serve_mode(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

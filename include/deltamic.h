@@ -247,8 +247,8 @@ typedef struct {
     int32_t device;        /* CUDA device ordinal */
     int32_t max_jobs;      /* jobs advanced concurrently (batch slots), >= 1 */
     size_t memory_bytes;   /* device arena for job state (0: half of the free device memory) */
-    int32_t chunk_tiles;   /* most adjoint frequency tiles (256 frequencies) per work unit (0: 32); small
-                              jobs use fewer so that each job alone yields ~8 units per SM */
+    int32_t chunk_tiles;   /* most adjoint frequency tiles (256 frequencies) per work unit (0: 1024); each
+                              job uses fewer so that it alone yields ~8 units per SM */
     int32_t reserved;
 } dm_server_options;
 

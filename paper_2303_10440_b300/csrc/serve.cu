@@ -538,7 +538,7 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     S->ctx = ctx;
     S->device = opt->device;
     S->max_jobs = opt->max_jobs;
-    S->chunk_tiles = opt->chunk_tiles > 0 ? opt->chunk_tiles : 32;
+    S->chunk_tiles = opt->chunk_tiles > 0 ? opt->chunk_tiles : 1024;
     S->t0 = std::chrono::steady_clock::now();
     memset(&S->stats, 0, sizeof(S->stats));
     DeviceGuard dg(opt->device);
