@@ -210,12 +210,13 @@ void oracle_tri_grad(const double* v1, const double* v2, const double* v3, const
 }
 
 /*
- * Mesh spectrum S(xi_m) = sum_T u_T(xi_m) (mode 0, surface; Eq. 5 numerator) or
+ * Mesh spectrum S(xi_m) = sum_T rho_T u_T(xi_m) (mode 0, surface; Eq. 5 numerator with the
+ * per-triangle fluorophore density rho_T of Section 3.3, wts == NULL meaning 1) or
  * sum_T of the signed tetrahedra (mode 1, volume), at M wavevectors xi[M][3].
  * V[n_v][3], F[n_t][3] (0-based), c0 the tetrahedra apex. Output S[M][2].
  */
 void oracle_mesh_ft(int mode, const double* V, int64_t n_v, const int32_t* F, int64_t n_t,
-                    const double* xi, int64_t M, const double* c0, double* S) {
+                    const double* xi, int64_t M, const double* c0, const double* wts, double* S) {
     (void)n_v;
     tri_geom* G = (tri_geom*)malloc(sizeof(tri_geom) * (size_t)(n_t > 0 ? n_t : 1));
     for (int64_t t = 0; t < n_t; ++t)
@@ -224,7 +225,8 @@ void oracle_mesh_ft(int mode, const double* V, int64_t n_v, const int32_t* F, in
     for (int64_t m = 0; m < M; ++m) {
         cplx acc = 0.0;
         for (int64_t t = 0; t < n_t; ++t)
-            acc += mode == 0 ? tri_ft_surface(&G[t], xi + 3 * m) : tet_ft(c0, &G[t], xi + 3 * m, NULL);
+            acc += mode == 0 ? (wts ? wts[t] : 1.0) * tri_ft_surface(&G[t], xi + 3 * m)
+                             : tet_ft(c0, &G[t], xi + 3 * m, NULL);
         S[2 * m] = creal(acc);
         S[2 * m + 1] = cimag(acc);
     }
@@ -238,7 +240,8 @@ void oracle_mesh_ft(int mode, const double* V, int64_t n_v, const int32_t* F, in
  * result is independent of the thread count.
  */
 void oracle_mesh_ft_adjoint(int mode, const double* V, int64_t n_v, const int32_t* F, int64_t n_t,
-                            const double* xi, int64_t M, const double* Gs, const double* c0, double* dV) {
+                            const double* xi, int64_t M, const double* Gs, const double* c0, const double* wts,
+                            double* dV) {
     double* acc = (double*)calloc((size_t)(n_t > 0 ? n_t : 1) * 9, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < n_t; ++t) {
@@ -279,7 +282,8 @@ void oracle_mesh_ft_adjoint(int mode, const double* V, int64_t n_v, const int32_
                 }
             }
         }
-        memcpy(acc + 9 * t, loc, sizeof(loc));
+        const double rho = (mode == 0 && wts) ? wts[t] : 1.0;
+        for (int k = 0; k < 9; ++k) acc[9 * t + k] = rho * loc[k];
     }
     memset(dV, 0, sizeof(double) * (size_t)n_v * 3);
     for (int64_t t = 0; t < n_t; ++t)

@@ -55,9 +55,9 @@ def lib():
         L.oracle_dd.argtypes = [d, ctypes.c_int, d, d]
         L.oracle_tri_ft.argtypes = [d, d, d, d, d, d]
         L.oracle_tri_grad.argtypes = [d, d, d, d, d]
-        L.oracle_mesh_ft.argtypes = [ctypes.c_int, d, ctypes.c_int64, i32, ctypes.c_int64, d, ctypes.c_int64, d, d]
+        L.oracle_mesh_ft.argtypes = [ctypes.c_int, d, ctypes.c_int64, i32, ctypes.c_int64, d, ctypes.c_int64, d, d, d]
         L.oracle_mesh_ft_adjoint.argtypes = [
-            ctypes.c_int, d, ctypes.c_int64, i32, ctypes.c_int64, d, ctypes.c_int64, d, d, d,
+            ctypes.c_int, d, ctypes.c_int64, i32, ctypes.c_int64, d, ctypes.c_int64, d, d, d, d,
         ]
         L.oracle_num_threads.restype = ctypes.c_int
         _LIB = L
@@ -110,47 +110,60 @@ def tri_grad(v1, v2, v3, xi) -> np.ndarray:
 _MODES = {"surface": 0, "volume": 1}
 
 
-def mesh_ft(V, F, xi, mode: str = "surface", c0=None) -> np.ndarray:
-    """S(xi_m) = sum over triangles (surface) or signed tetrahedra about c0 (volume)."""
+def _wp(weights, n_t):
+    if weights is None:
+        return None, None
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    assert w.shape == (n_t,)
+    return w, _dp(w)
+
+
+def mesh_ft(V, F, xi, mode: str = "surface", c0=None, weights=None) -> np.ndarray:
+    """S(xi_m) = sum over triangles rho_T u_T (surface; rho = weights or 1) or signed tetrahedra about c0 (volume)."""
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
     xi = np.ascontiguousarray(np.atleast_2d(xi), dtype=np.float64)
     c0 = np.ascontiguousarray(np.zeros(3) if c0 is None else c0, dtype=np.float64)
+    w, wp = _wp(weights, F.shape[0])
     out = np.zeros((xi.shape[0], 2), dtype=np.float64)
-    lib().oracle_mesh_ft(_MODES[mode], _dp(V), V.shape[0], _ip(F), F.shape[0], _dp(xi), xi.shape[0], _dp(c0), _dp(out))
+    lib().oracle_mesh_ft(_MODES[mode], _dp(V), V.shape[0], _ip(F), F.shape[0], _dp(xi), xi.shape[0], _dp(c0), wp,
+                         _dp(out))
     return out[:, 0] + 1j * out[:, 1]
 
 
-def mesh_ft_adjoint(V, F, xi, Gs, mode: str = "surface", c0=None) -> np.ndarray:
+def mesh_ft_adjoint(V, F, xi, Gs, mode: str = "surface", c0=None, weights=None) -> np.ndarray:
     """dV[v] = sum_m Re(conj(Gs_m) dS(xi_m)/dv)."""
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
     xi = np.ascontiguousarray(np.atleast_2d(xi), dtype=np.float64)
     G = np.ascontiguousarray(np.stack([np.real(Gs), np.imag(Gs)], axis=1), dtype=np.float64)
     c0 = np.ascontiguousarray(np.zeros(3) if c0 is None else c0, dtype=np.float64)
+    w, wp = _wp(weights, F.shape[0])
     out = np.zeros((V.shape[0], 3), dtype=np.float64)
     lib().oracle_mesh_ft_adjoint(
-        _MODES[mode], _dp(V), V.shape[0], _ip(F), F.shape[0], _dp(xi), xi.shape[0], _dp(G), _dp(c0), _dp(out)
+        _MODES[mode], _dp(V), V.shape[0], _ip(F), F.shape[0], _dp(xi), xi.shape[0], _dp(G), _dp(c0), wp, _dp(out)
     )
     return out
 
 
-def surface_area(V, F) -> float:
-    """|Lambda| = sum_T A_T, A_T = |e3 x e1| / 2 (Section 4.1.2)."""
+def surface_area(V, F, weights=None) -> float:
+    """|Lambda| = sum_T rho_T A_T, A_T = |e3 x e1| / 2 (Section 4.1.2; rho = weights or 1)."""
     a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
-    return 0.5 * float(np.linalg.norm(np.cross(b - a, c - a), axis=1).sum())
+    A = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    return float(np.sum(A if weights is None else np.asarray(weights) * A))
 
 
-def surface_area_grad(V, F) -> np.ndarray:
-    """d|Lambda|/dv = sum over incident triangles of -w_p / 2 = (N x e_p) / 2."""
+def surface_area_grad(V, F, weights=None) -> np.ndarray:
+    """d|Lambda|/dv = sum over incident triangles of rho_T (-w_p / 2) = rho_T (N x e_p) / 2."""
     v = [V[F[:, k]] for k in range(3)]
     e = [v[2] - v[1], v[0] - v[2], v[1] - v[0]]  # e1, e2, e3
     n = np.cross(e[2], e[0])
     nn = np.linalg.norm(n, axis=1, keepdims=True)
     N = np.divide(n, nn, out=np.zeros_like(n), where=nn > 0)
+    rho = np.ones((F.shape[0], 1)) if weights is None else np.asarray(weights, dtype=np.float64)[:, None]
     out = np.zeros_like(V)
     for p in range(3):
-        np.add.at(out, F[:, p], 0.5 * np.cross(N, e[p]))
+        np.add.at(out, F[:, p], 0.5 * rho * np.cross(N, e[p]))
     return out
 
 
@@ -239,14 +252,17 @@ def image_adjoint(R, nvec, c, grid) -> np.ndarray:
 # ----------------------------------------------------------------------------- render / loss / grad
 
 
-def _normaliser(Vs, F, mode):
-    return surface_area(Vs, F) if mode == "surface" else enclosed_volume(Vs, F)
+def _normaliser(Vs, F, mode, weights=None):
+    return surface_area(Vs, F, weights) if mode == "surface" else enclosed_volume(Vs, F)
 
 
 def render(V, F, grid, psf, mode: str = "surface", method: str = "fft", weights=None):
-    """Image of the mesh under the PSF; returns a dict with the image and intermediates."""
-    if weights is not None:
-        raise NotImplementedError("per-triangle weights are not part of the oracle yet")
+    """Image of the mesh under the PSF; returns a dict with the image and intermediates.
+
+    weights: optional per-triangle fluorophore density rho_T (surface mode; Section 3.3 — cell-cell
+    interfaces carry density 2); the density is normalised by sum_T rho_T A_T."""
+    if weights is not None and mode != "surface":
+        raise ValueError("weights apply to the surface-labelled mode")
     Vs = np.asarray(V, dtype=np.float64) - np.asarray(grid.origin, dtype=np.float64)[None, :]
     nvec, c = half_spectrum(grid.n)
     xi_all = wavevectors(nvec, grid)
@@ -254,12 +270,13 @@ def render(V, F, grid, psf, mode: str = "surface", method: str = "fft", weights=
     B = band_mask(h_all, psf.band_tau)
     nvec, c, xi, h = nvec[B], c[B], xi_all[B], h_all[B]
     c0 = 0.5 * grid.L
-    S = mesh_ft(Vs, F, xi, mode, c0)
-    norm = _normaliser(Vs, F, mode)
+    S = mesh_ft(Vs, F, xi, mode, c0, weights)
+    norm = _normaliser(Vs, F, mode, weights)
     u = S / norm
     X = u * h
     img = spectrum_to_image(X, nvec, c, grid, method)
-    return dict(image=img, S=S, u=u, X=X, nvec=nvec, c=c, xi=xi, h=h, norm=norm, band=B, c0=c0, Vs=Vs)
+    return dict(image=img, S=S, u=u, X=X, nvec=nvec, c=c, xi=xi, h=h, norm=norm, band=B, c0=c0, Vs=Vs,
+                weights=weights)
 
 
 _LOSS = {"l2": 0, "mse": 1, "weighted": 2}
@@ -277,9 +294,9 @@ def loss_value(I, T, kind: str) -> tuple[float, np.ndarray]:
     raise ValueError(kind)
 
 
-def render_adjoint(V, F, grid, psf, dL_dI, mode: str = "surface", fwd=None):
+def render_adjoint(V, F, grid, psf, dL_dI, mode: str = "surface", fwd=None, weights=None):
     """Given dL/dI, return (dL/dV, dL/dsigma [3] or dL/dcov [6]) through the whole chain."""
-    r = fwd if fwd is not None else render(V, F, grid, psf, mode)
+    r = fwd if fwd is not None else render(V, F, grid, psf, mode, weights=weights)
     Vs, nvec, c, xi, h, S, u, X, norm, c0 = (r[k] for k in ("Vs", "nvec", "c", "xi", "h", "S", "u", "X", "norm", "c0"))
     G = image_adjoint(dL_dI, nvec, c, grid)  # dL/dX on the band
     # PSF: X = u h_hat, d h_hat / d Sigma_ab = -1/2 xi_a xi_b h_hat
@@ -292,15 +309,16 @@ def render_adjoint(V, F, grid, psf, dL_dI, mode: str = "surface", fwd=None):
         dpsf = np.array([np.sum(gx * (-s[a] * xi[:, a] ** 2)) for a in range(3)])
     # mesh: u = S / norm (Eq. 6 quotient rule)
     Gu = G * h  # dL/du
-    dV_S = mesh_ft_adjoint(Vs, F, xi, Gu / norm, mode, c0)
+    w = r.get("weights")
+    dV_S = mesh_ft_adjoint(Vs, F, xi, Gu / norm, mode, c0, w)
     cq = float(np.sum(np.real(np.conj(Gu) * S))) / norm**2
-    dnorm = surface_area_grad(Vs, F) if mode == "surface" else enclosed_volume_grad(Vs, F)
+    dnorm = surface_area_grad(Vs, F, w) if mode == "surface" else enclosed_volume_grad(Vs, F)
     dV = dV_S - cq * dnorm
     return dV, dpsf
 
 
-def loss_and_grad(V, F, grid, psf, target, kind: str = "mse", mode: str = "surface"):
-    r = render(V, F, grid, psf, mode)
+def loss_and_grad(V, F, grid, psf, target, kind: str = "mse", mode: str = "surface", weights=None):
+    r = render(V, F, grid, psf, mode, weights=weights)
     L, dI = loss_value(r["image"], target, kind)
     dV, dpsf = render_adjoint(V, F, grid, psf, dI, mode, fwd=r)
     return L, dV, dpsf, r

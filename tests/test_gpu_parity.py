@@ -238,3 +238,45 @@ def test_argument_errors_are_reported(r32):
     # the context stays usable afterwards
     img = r32.render(_cuda(V), _cuda(F), grid, psf)
     assert torch.isfinite(img).all()
+
+
+@pytest.mark.parametrize("wkind", ["interface", "random"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_weighted_density_matches_oracle(wkind, prec, r64, r32):
+    """Per-triangle fluorophore density (Section 3.3): image, loss and gradients vs the oracle."""
+    grid, psf, V, F, T = _case_small()
+    if wkind == "interface":
+        cen = V[F].mean(axis=1)
+        w = np.where(cen[:, 0] > grid.center[0], 2.0, 1.0).astype(np.float32)
+    else:
+        w = np.random.default_rng(21).uniform(0.25, 3.0, len(F)).astype(np.float32)
+    w64 = w.astype(np.float64)
+    r = r64 if prec == "fp64" else r32
+    ref = oracle.render(V, F, grid, psf, weights=w64)["image"]
+    img = r.render(_cuda(V), _cuda(F), grid, psf, weights=_cuda(w)).cpu().numpy()
+    assert rel(img, ref) < (1e-10 if prec == "fp64" else 1e-4)
+    L0, dV0, dpsf0, _ = oracle.loss_and_grad(V, F, grid, psf, T, "mse", weights=w64)
+    L, dV, dpsf, _ = r.loss_and_grad(_cuda(V), _cuda(F), grid, psf, _cuda(T), "mse", weights=_cuda(w))
+    tl, tg = (1e-10, 1e-9) if prec == "fp64" else (2e-4, 1e-3)
+    assert abs(L - L0) <= tl * abs(L0)
+    assert rel(dV.cpu().numpy(), dV0) < tg
+    assert rel(dpsf.numpy(), dpsf0) < tg
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_weighted_meshft_and_adjoint_match_oracle(prec, r64, r32):
+    V, F = _meshes()["sh_sphere"]
+    w = np.random.default_rng(22).uniform(0.5, 2.0, len(F)).astype(np.float32)
+    w64 = w.astype(np.float64)
+    fn = _freqs(5)
+    xi = oracle.wavevectors(fn, GRID)
+    Vo = V - np.asarray(GRID.origin)
+    r = r64 if prec == "fp64" else r32
+    S0 = oracle.mesh_ft(Vo, F, xi, weights=w64)
+    S = r.meshft(_cuda(V), _cuda(F), GRID, _cuda(fn), weights=_cuda(w)).cpu().numpy()
+    assert rel(S, S0) < (1e-11 if prec == "fp64" else 2e-6)
+    rng = np.random.default_rng(6)
+    G = (rng.normal(size=len(fn)) + 1j * rng.normal(size=len(fn))) / np.sqrt(len(fn))
+    dV0 = oracle.mesh_ft_adjoint(Vo, F, xi, G, weights=w64)
+    dV = r.meshft_adjoint(_cuda(V), _cuda(F), GRID, _cuda(fn), _cuda(G), weights=_cuda(w)).cpu().numpy()
+    assert rel(dV, dV0) < (1e-10 if prec == "fp64" else 1e-4)

@@ -118,3 +118,64 @@ def test_full_covariance_gradient_matches_finite_differences():
         Lp = oracle.loss_value(oracle.render(V, F, grid, synth.Psf(sigma=(1, 1, 1), cov=tuple(cp)))["image"], T, "l2")[0]
         Lm = oracle.loss_value(oracle.render(V, F, grid, synth.Psf(sigma=(1, 1, 1), cov=tuple(cm)))["image"], T, "l2")[0]
         assert abs(dcov[k] - (Lp - Lm) / (2 * h)) <= 1e-6 * np.abs(dcov).sum()
+
+
+def _interface_case(seed=11):
+    """A cell whose triangles on one side carry two membranes (Section 3.3: a cell-cell interface
+    has twice the fluorophore density of a free membrane)."""
+    grid, psf, V, F = _small_case(n=(10, 9, 8), level=1, seed=seed)
+    cen = V[F].mean(axis=1)
+    shared = cen[:, 0] > grid.center[0] + 0.3
+    w = np.where(shared, 2.0, 1.0)
+    return grid, psf, V, F, shared, w
+
+
+def test_density_two_equals_a_doubled_sheet():
+    """rho_T = 2 is the same surface density as two coincident copies of the triangle."""
+    grid, psf, V, F, shared, w = _interface_case()
+    F2 = np.concatenate([F, F[shared]])
+    a = oracle.render(V, F, grid, psf, weights=w)
+    b = oracle.render(V, F2, grid, psf)
+    assert abs(a["norm"] - b["norm"]) < 1e-13 * b["norm"]
+    assert np.max(np.abs(a["image"] - b["image"])) < 1e-12 * np.max(np.abs(b["image"]))
+    T = synth.add_gaussian_noise(oracle.render(V * 1.02, F2, grid, psf)["image"], 0.05, seed=1)
+    La, dVa, dpa, _ = oracle.loss_and_grad(V, F, grid, psf, T, "l2", weights=w)
+    Lb, dVb, dpb, _ = oracle.loss_and_grad(V, F2, grid, psf, T, "l2")
+    assert abs(La - Lb) < 1e-12 * Lb
+    assert np.linalg.norm(dVa - dVb) < 1e-11 * np.linalg.norm(dVb)
+    assert np.linalg.norm(dpa - dpb) < 1e-11 * np.linalg.norm(dpb)
+    # and the interface is visible: the weighted image differs from the unweighted one
+    c = oracle.render(V, F, grid, psf)
+    assert np.linalg.norm(a["image"] - c["image"]) > 1e-2 * np.linalg.norm(c["image"])
+
+
+def test_uniform_density_leaves_the_image_unchanged():
+    """The image is normalised by sum_T rho_T A_T (Eq. 3 unit mass), so a constant rho cancels."""
+    grid, psf, V, F, _, _ = _interface_case()
+    a = oracle.render(V, F, grid, psf, weights=np.full(len(F), 3.0))["image"]
+    b = oracle.render(V, F, grid, psf)["image"]
+    assert np.max(np.abs(a - b)) < 1e-13 * np.max(np.abs(b))
+    assert abs(a.sum() * np.prod(grid.h) - 1.0) < 1e-12
+
+
+def test_weighted_loss_gradient_matches_finite_differences():
+    grid, psf, V, F, _, _ = _interface_case()
+    w = np.random.default_rng(5).uniform(0.5, 2.5, len(F))
+    T = synth.add_gaussian_noise(oracle.render(V * 1.03 + 0.05, F, grid, psf)["image"], 0.05, seed=3)
+    L, dV, dpsf, _ = oracle.loss_and_grad(V, F, grid, psf, T, "mse", weights=w)
+    rng = np.random.default_rng(9)
+    h = 1e-6
+
+    def Lof(W, p):
+        return oracle.loss_value(oracle.render(W, F, grid, p, weights=w)["image"], T, "mse")[0]
+
+    for _ in range(4):
+        d = rng.normal(size=V.shape)
+        fd = (Lof(V + h * d, psf) - Lof(V - h * d, psf)) / (2 * h)
+        assert abs(np.sum(dV * d) - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(dV).sum())
+    sp = list(psf.sigma)
+    sm = list(psf.sigma)
+    sp[2] += h
+    sm[2] -= h
+    fd = (Lof(V, synth.Psf(sigma=tuple(sp))) - Lof(V, synth.Psf(sigma=tuple(sm)))) / (2 * h)
+    assert abs(dpsf[2] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(dpsf).sum())
