@@ -142,7 +142,8 @@ int64_t dm_kernel_launches(const dm_ctx* ctx);
 #define DM_STAGE_REDUCE 10  /* per-chunk sums                               */
 #define DM_STAGE_ASSEMBLE 11 /* per-vertex gradient (Eq. 6)                 */
 #define DM_STAGE_ADAM 12    /* optimiser update                             */
-#define DM_NUM_STAGES 13
+#define DM_STAGE_SMOOTH 13  /* large-steps smoothing solves (Sec. 5.1)      */
+#define DM_NUM_STAGES 14
 dm_status dm_profile_enable(dm_ctx* ctx, int32_t enable);
 /* ms, calls: arrays of DM_NUM_STAGES (either may be NULL). */
 dm_status dm_profile_read(dm_ctx* ctx, double* ms, int64_t* calls);
@@ -230,6 +231,66 @@ typedef struct {
  * (host struct). loss_history (nullable): [steps] doubles, the loss before each step. */
 dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
                  const void* target, const dm_fit_options* opt, double* loss_history, void* stream);
+
+/* ---------------------------------------------------------------- staggered fit
+ * Section 5.1 ("A staggered optimization scheme") and Section 5.2 ("PSF optimization step"):
+ * rounds of (a) shape steps on the narrow band of the current PSF, PSF held, then (b) PSF
+ * steps on every frequency of the half spectrum, shape held. The shape optimiser of the paper
+ * is the large-steps update v <- v - eta (1 + lambda L)^-2 dL/dv with uniform Adam (lambda = 50,
+ * after Nicolet et al. 2021); the PSF optimiser is Adam on the covariance. */
+#define DM_OPT_ADAM 0        /* plain Adam on the vertex positions */
+#define DM_OPT_LARGE_STEPS 1 /* uniform Adam on u = (1 + lambda L) v */
+
+/* Smoothing solve of the large-steps update: X = (1 + lambda L)^-1 B, L the combinatorial
+ * Laplacian of the mesh edges (degree minus adjacency over the unique undirected edges of F).
+ * F: [n_t][3] int32 (host or device). B, X: DEVICE [n_v][3] doubles; X holds the starting
+ * guess on entry (zeros are fine) and the solution on return. Jacobi-preconditioned conjugate
+ * gradients in the context's precision, one CTA per coordinate, until ||r|| <= tol ||b||
+ * (tol <= 0: 1e-6 for DM_FP32_MIXED, 1e-12 for DM_FP64) or max_iter iterations (<= 0: 2000).
+ * iters (nullable, host int64[3]): total iterations of the 3 columns, the most in one column,
+ * and the number of columns that stopped at max_iter. Synchronises the stream when iters is
+ * given. DM_ERR_ARG: NULL or host B / X, lambda < 0, indices out of range. */
+dm_status dm_smooth_solve(dm_ctx* ctx, const int32_t* F, int64_t n_t, int64_t n_v, double lambda, const double* B,
+                          double* X, double tol, int32_t max_iter, int64_t* iters, void* stream);
+
+/* One uniform-Adam step (Nicolet et al. 2021) on n DEVICE doubles: m, v (zero before step 1)
+ * are updated in place and delta[i] = lr m_hat[i] / (sqrt(max_j v_hat[j]) + eps); the caller
+ * moves the parameter by -delta. */
+dm_status dm_adam_uniform(dm_ctx* ctx, const double* grad, double* m, double* v, double* delta, int64_t n, double lr,
+                          double beta1, double beta2, double eps, int64_t step, void* stream);
+
+typedef struct {
+    int32_t rounds;       /* staggered rounds */
+    int32_t shape_steps;  /* (a) steps per round: narrow band (psf band_tau), PSF held */
+    int32_t psf_steps;    /* (b) steps per round: whole half spectrum, shape held */
+    int32_t shape_loss;   /* DM_LOSS_*; the paper's shape loss is DM_LOSS_WEIGHTED */
+    int32_t psf_loss;     /* DM_LOSS_*; the paper's PSF loss is DM_LOSS_L2 */
+    int32_t optimizer;    /* DM_OPT_LARGE_STEPS (the paper's) or DM_OPT_ADAM */
+    double lr_vertex;     /* step size of the vertex optimiser */
+    double lr_psf;        /* Adam step size on the Cholesky factor of Sigma */
+    double lambda;        /* smoothing weight of the large-steps update (the paper: 50) */
+    double beta1, beta2, eps;
+    double cg_tol;        /* smoothing-solve tolerance (<= 0: the dm_smooth_solve default) */
+    int32_t cg_max_iter;  /* smoothing-solve iteration limit (<= 0: 2000) */
+    int32_t reserved;
+} dm_stagger_options;
+
+typedef struct {
+    int64_t cg_iterations;   /* over all smoothing solves and columns */
+    int64_t cg_max;          /* most iterations of one column */
+    int64_t cg_unconverged;  /* columns that stopped at cg_max_iter */
+} dm_stagger_stats;
+
+/* The staggered fit, entirely on the device. The covariance is parameterised as
+ * Sigma = C C^T, C lower triangular (6 numbers), and Adam acts on C; a DIAG psf_io starts from
+ * C = diag(sigma). On return psf_io is DM_PSF_FULL with the fitted cov (and sigma = the square
+ * roots of its diagonal); band_tau is kept. V_io: [n_v][3] host or device, fitted positions
+ * out. shape_loss (nullable): [rounds * shape_steps] doubles, psf_loss (nullable):
+ * [rounds * psf_steps] doubles, each the loss before its step. stats nullable.
+ * DM_ERR_ARG: a covariance that is not positive definite, bad options. */
+dm_status dm_fit_staggered(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
+                           const void* target, const dm_stagger_options* opt, double* shape_loss, double* psf_loss,
+                           dm_stagger_stats* stats, void* stream);
 
 /* ---------------------------------------------------------------- fit server
  * Continuous batching of many shape fits on one GPU (FP32 mixed path). Jobs are copied at

@@ -27,7 +27,8 @@ LOSSES = {"l2": 0, "mse": 1, "weighted": 2}
 DM_PSF_DIAG, DM_PSF_FULL = 0, 1
 DM_NOALLOC_MAX_TRIANGLES = 65536
 STAGES = ("params", "prep", "band", "fwd", "scatter", "c2r", "loss", "r2c", "gather", "adj", "reduce", "assemble",
-          "adam")
+          "adam", "smooth")
+OPTIMIZERS = {"adam": 0, "large_steps": 1}
 
 
 class dm_options(ctypes.Structure):
@@ -64,6 +65,30 @@ class dm_fit_options(ctypes.Structure):
         ("beta2", c_f64),
         ("eps", c_f64),
     ]
+
+
+class dm_stagger_options(ctypes.Structure):
+    _fields_ = [
+        ("rounds", c_i32),
+        ("shape_steps", c_i32),
+        ("psf_steps", c_i32),
+        ("shape_loss", c_i32),
+        ("psf_loss", c_i32),
+        ("optimizer", c_i32),
+        ("lr_vertex", c_f64),
+        ("lr_psf", c_f64),
+        ("lam", c_f64),
+        ("beta1", c_f64),
+        ("beta2", c_f64),
+        ("eps", c_f64),
+        ("cg_tol", c_f64),
+        ("cg_max_iter", c_i32),
+        ("reserved", c_i32),
+    ]
+
+
+class dm_stagger_stats(ctypes.Structure):
+    _fields_ = [("cg_iterations", c_i64), ("cg_max", c_i64), ("cg_unconverged", c_i64)]
 
 
 class dm_server_options(ctypes.Structure):
@@ -133,6 +158,13 @@ _SIGS = {
     "dm_server_get_stats": (c_i32, [c_p, ctypes.POINTER(dm_server_stats)]),
     "dm_server_clock": (c_f64, [c_p]),
     "dm_server_shutdown": (c_i32, [c_p]),
+    "dm_smooth_solve": (c_i32, [c_p, c_p, c_i64, c_i64, c_f64, c_p, c_p, c_f64, c_i32, c_p, c_p]),
+    "dm_adam_uniform": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i64, c_f64, c_f64, c_f64, c_f64, c_i64, c_p]),
+    "dm_fit_staggered": (
+        c_i32,
+        [c_p, ctypes.POINTER(dm_mesh), c_p, ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p,
+         ctypes.POINTER(dm_stagger_options), c_p, c_p, ctypes.POINTER(dm_stagger_stats), c_p],
+    ),
     "dm_fit": (
         c_i32,
         [c_p, ctypes.POINTER(dm_mesh), c_p, ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p,

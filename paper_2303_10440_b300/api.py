@@ -252,6 +252,52 @@ class Renderer:
                               lr, beta1, beta2, eps, int(step), _stream(stream, param.device))
         self._check(st, "dm_adam")
 
+    def smooth_solve(self, F, n_v, B, lam=50.0, X0=None, tol=0.0, max_iter=0, stream=None):
+        """X = (1 + lam L)^-1 B for B [n_v, 3] (device), L the combinatorial mesh Laplacian.
+        Returns (X, (total iterations, most in one column, unconverged columns))."""
+        dev = B.device
+        Bt = _as_tensor(B, torch.float64, dev)
+        X = torch.zeros_like(Bt) if X0 is None else _as_tensor(X0, torch.float64, dev).clone()
+        Ft = _as_tensor(F, torch.int32, dev)
+        it = (ctypes.c_int64 * 3)()
+        st = self.lib.dm_smooth_solve(self.ctx, Ft.data_ptr(), Ft.shape[0], int(n_v), float(lam), Bt.data_ptr(),
+                                      X.data_ptr(), float(tol), int(max_iter), it, _stream(stream, dev))
+        self._check(st, "dm_smooth_solve")
+        return X, tuple(int(v) for v in it)
+
+    def adam_uniform(self, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-20, stream=None):
+        """One uniform-Adam step; m, v updated in place; returns delta (the parameter moves by -delta)."""
+        delta = torch.empty_like(grad)
+        st = self.lib.dm_adam_uniform(self.ctx, grad.data_ptr(), m.data_ptr(), v.data_ptr(), delta.data_ptr(),
+                                      grad.numel(), lr, beta1, beta2, eps, int(step), _stream(stream, grad.device))
+        self._check(st, "dm_adam_uniform")
+        return delta
+
+    def fit_staggered(self, V, F, grid, psf, target, rounds, shape_steps, psf_steps, lr_vertex, lr_psf,
+                      optimizer="large_steps", lam=50.0, shape_loss="weighted", psf_loss="l2", label="surface",
+                      weights=None, beta1=0.9, beta2=0.999, eps=1e-20, cg_tol=0.0, cg_max_iter=0, stream=None):
+        """Staggered shape/PSF fit on the device (shape steps on the narrow band, PSF steps on the
+        whole half spectrum). Returns (V_fitted, PSF with the fitted covariance, shape losses,
+        PSF losses, smoothing-solve statistics)."""
+        dev = self._dev(V)
+        Vw = _as_tensor(V, torch.float64, dev).clone()
+        m, keep = self._mesh(Vw, F, label, weights, dev)
+        T = _as_tensor(target, self.real, dev if isinstance(target, torch.Tensor) and target.is_cuda else None)
+        g, p = _grid(grid), _psf(psf)
+        o = _lib.dm_stagger_options(int(rounds), int(shape_steps), int(psf_steps), _lib.LOSSES[shape_loss],
+                                    _lib.LOSSES[psf_loss], _lib.OPTIMIZERS[optimizer], float(lr_vertex), float(lr_psf),
+                                    float(lam), beta1, beta2, eps, float(cg_tol), int(cg_max_iter), 0)
+        hs = torch.empty(max(1, rounds * shape_steps), dtype=torch.float64)
+        hp = torch.empty(max(1, rounds * psf_steps), dtype=torch.float64)
+        stats = _lib.dm_stagger_stats()
+        st = self.lib.dm_fit_staggered(self.ctx, ctypes.byref(m), Vw.data_ptr(), ctypes.byref(p), ctypes.byref(g),
+                                       T.data_ptr(), ctypes.byref(o), hs.data_ptr(), hp.data_ptr(), ctypes.byref(stats),
+                                       _stream(stream, dev))
+        self._check(st, "dm_fit_staggered")
+        out_psf = PSF(sigma=tuple(p.sigma), band_tau=p.band_tau, cov=tuple(p.cov))
+        cg = dict(iterations=stats.cg_iterations, max=stats.cg_max, unconverged=stats.cg_unconverged)
+        return Vw, out_psf, hs[: rounds * shape_steps], hp[: rounds * psf_steps], cg
+
     def fit(self, V, F, grid, psf, target, steps, lr_vertex, lr_psf=0.0, loss="mse", label="surface", weights=None,
             beta1=0.9, beta2=0.999, eps=1e-20, stream=None):
         """Adam fit on the device. Returns (V_fitted, sigma_fitted, loss_history).

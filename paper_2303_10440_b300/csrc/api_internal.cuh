@@ -359,6 +359,7 @@ struct Outputs {
     void* image;     // device, nullable (else internal)
     double* dV;      // device, nullable
     bool want_grad;  // run the adjoint
+    bool psf_only = false;  // stop after dL/dpsf (no vertex adjoint)
 };
 
 // Runs the full chain on device buffers; results: b.d_params[17] = L, [24..29] = dpsf, out.dV.
@@ -455,6 +456,7 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
                                             G, (FreqRec*)b.fr, z.M_pad, b.partial, &ng, st));
         LAUNCH(1, launch_sum(b.partial, ng, 8, 8, d_dpsf, st));  // [24..29] dpsf, [30] coef
     }
+    if (out.psf_only) return DM_OK;
     {
         Stage sg(ctx, DM_STAGE_ADJ, st);
         if (sizeof(R) == 4)

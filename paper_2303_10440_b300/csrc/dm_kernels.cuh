@@ -180,6 +180,30 @@ cudaError_t launch_csr(const int32_t* F, int64_t n_t, int64_t n_v, int32_t* cnt,
 cudaError_t launch_vertex_gather(const int32_t* ptr, const int32_t* ent, const double* contrib, int64_t n_v,
                                  double* dV, cudaStream_t st);
 
+// Exclusive prefix sum of n counts into ptr[0..n] (ptr[n] = total); one CTA.
+cudaError_t launch_scan_i32(const int32_t* cnt, int64_t n, int32_t* ptr, cudaStream_t st);
+
+// Optimiser layer (optim.cu). Combinatorial Laplacian rows (unique neighbours, sorted) from
+// the vertex star (sptr, ent of launch_csr); lcol needs room for 2 * (3 n_t) entries.
+cudaError_t launch_laplacian(const int32_t* F, const int32_t* sptr, const int32_t* ent, int64_t n_v, int32_t* cnt,
+                             int32_t* lptr, int32_t* lcol, int* d_err, cudaStream_t st);
+// (1 + lam L) X = B for the 3 columns of [n_v][3] doubles; X is the start and the result;
+// sub_into (nullable) -= X. work: pcg_work_elems(n_v) values of R (used when the vectors do
+// not fit in shared memory). stats (nullable, device): total / most iterations, unconverged.
+size_t pcg_work_elems(int64_t n_v);
+template <class R>
+cudaError_t launch_pcg(const int32_t* lptr, const int32_t* lcol, int64_t n_v, double lam, const double* B, double* X,
+                       double* sub_into, R* work, double tol, int max_iter, unsigned long long* stats,
+                       cudaStream_t st);
+// Uniform Adam: m, v updated; delta = lr m_hat / (sqrt(max v_hat) + eps). part_max holds
+// adam_uniform_partials(n) doubles.
+int adam_uniform_partials(int64_t n);
+cudaError_t launch_adam_uniform(const double* g, double* m, double* v, double* delta, int64_t n, double lr, double b1,
+                                double b2, double eps, int64_t step, double* part_max, cudaStream_t st);
+// Sigma = C C^T into the covariance numbers of the device PSF parameters, and dL/dC from dL/dcov.
+cudaError_t launch_chol_to_cov(const double* C, double* d_psf, cudaStream_t st);
+cudaError_t launch_chol_grad(const double* C, const double* gcov, double* gC, cudaStream_t st);
+
 // Adam update on n doubles.
 cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2,
                         double eps, int64_t step, cudaStream_t st);

@@ -672,6 +672,11 @@ cudaError_t launch_csr(const int32_t* F, int64_t n_t, int64_t n_v, int32_t* cnt,
     return cudaGetLastError();
 }
 
+cudaError_t launch_scan_i32(const int32_t* cnt, int64_t n, int32_t* ptr, cudaStream_t st) {
+    k_scan_i32<<<1, 1024, 0, st>>>(cnt, n, ptr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_vertex_gather(const int32_t* ptr, const int32_t* ent, const double* contrib, int64_t n_v,
                                  double* dV, cudaStream_t st) {
     k_vertex_gather<<<nblk(n_v), NT, 0, st>>>(ptr, ent, contrib, n_v, dV);

@@ -51,3 +51,5 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(_lib.dm_mesh) == 48
     assert ctypes.sizeof(_lib.dm_options) == 16
     assert ctypes.sizeof(_lib.dm_fit_options) == 8 + 40
+    assert ctypes.sizeof(_lib.dm_stagger_options) == 24 + 56 + 8
+    assert ctypes.sizeof(_lib.dm_stagger_stats) == 24

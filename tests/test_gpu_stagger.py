@@ -1,0 +1,152 @@
+"""Staggered fit on the GPU (Section 5.1-5.2) vs the oracle: the smoothing solve of the
+large-steps update, the uniform-Adam step, and whole staggered fits.
+
+Tolerances: the FP64 path's conjugate gradients stop at a relative residual of 1e-12, so
+solutions agree to ~kappa * 1e-12 (kappa <= 1 + lambda * 2 * max degree ~ 600 for the meshes
+here); the FP32 path stops at 1e-6, hence 1e-3.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle.optim as opt
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.fixture(scope="module")
+def r64():
+    from paper_2303_10440_b300 import Renderer
+
+    r = Renderer("fp64")
+    yield r
+    r.close()
+
+
+@pytest.fixture(scope="module")
+def r32():
+    from paper_2303_10440_b300 import Renderer
+
+    r = Renderer("fp32")
+    yield r
+    r.close()
+
+
+def _meshes():
+    out = {}
+    out["sh_l3"] = synth.sh_deformed_sphere(3, 8.0, (0, 0, 0), lmax=4, coef_sigma=0.5, seed=1)
+    out["sh_l5"] = synth.sh_deformed_sphere(5, 30.0, (0, 0, 0), lmax=6, coef_sigma=1.0, seed=2)
+    Vt, Ft = synth.random_triangles(60, seed=3, extent=6.0, center=(0, 0, 0))
+    out["soup"] = (Vt, Ft)
+    # two cells sharing a wall: non-manifold edges along the wall's rim
+    Va, Fa = synth.box_mesh((0, 0, 0), (2, 2, 2))
+    Vb, Fb = synth.box_mesh((2, 0, 0), (4, 2, 2))
+    V = np.concatenate([Va, Vb])
+    F = np.concatenate([Fa, Fb + len(Va)])
+    key = {tuple(np.round(v, 9)): i for i, v in enumerate(V)}  # merge the coincident corners
+    remap = np.array([key[tuple(np.round(v, 9))] for v in V])
+    out["two_boxes"] = (V, remap[F].astype(np.int32))
+    return out
+
+
+@pytest.mark.parametrize("name", ["sh_l3", "sh_l5", "soup", "two_boxes"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_smooth_solve_matches_oracle(name, prec, r64, r32):
+    V, F = _meshes()[name]
+    n_v = len(V)
+    B = np.random.default_rng(7).normal(size=(n_v, 3))
+    ref = opt.smooth_solve(F, n_v, 50.0, B)
+    r = r64 if prec == "fp64" else r32
+    X, (total, most, unconv) = r.smooth_solve(torch.as_tensor(F).cuda(), n_v, torch.as_tensor(B).cuda(), 50.0)
+    assert unconv == 0 and most > 0 and total >= most
+    assert rel(X.cpu().numpy(), ref) < (1e-9 if prec == "fp64" else 1e-3)
+    # started at the solution, the solve stops at once (FP64) or after a few corrections of the
+    # rounding of the start to FP32
+    X2, (total2, _, _) = r.smooth_solve(torch.as_tensor(F).cuda(), n_v, torch.as_tensor(B).cuda(), 50.0,
+                                        X0=torch.as_tensor(ref).cuda(), tol=1e-6)
+    assert total2 <= 3 if prec == "fp64" else total2 < total
+
+
+def test_smooth_solve_of_zero_and_of_lambda_zero(r64):
+    V, F = _meshes()["sh_l3"]
+    n_v = len(V)
+    X, it = r64.smooth_solve(torch.as_tensor(F).cuda(), n_v, torch.zeros(n_v, 3, dtype=torch.float64).cuda(),
+                             X0=torch.ones(n_v, 3, dtype=torch.float64).cuda())
+    assert torch.count_nonzero(X) == 0 and it[0] == 0
+    B = torch.as_tensor(np.random.default_rng(1).normal(size=(n_v, 3))).cuda()
+    X, _ = r64.smooth_solve(torch.as_tensor(F).cuda(), n_v, B, lam=0.0)
+    assert torch.allclose(X, B, rtol=1e-12, atol=0)
+
+
+def test_adam_uniform_matches_oracle(r64):
+    rng = np.random.default_rng(3)
+    n = 3 * 700
+    m0, v0 = np.zeros(n), np.zeros(n)
+    m, v = torch.zeros(n, dtype=torch.float64).cuda(), torch.zeros(n, dtype=torch.float64).cuda()
+    for t in range(1, 5):
+        g = rng.normal(size=n) * 1e-9
+        d0, m0, v0 = opt.adam_uniform(g, m0, v0, t, 0.3, 0.9, 0.999, 1e-20)
+        d = r64.adam_uniform(torch.as_tensor(g).cuda(), m, v, t, 0.3, 0.9, 0.999, 1e-20)
+        assert rel(d.cpu().numpy(), d0) < 1e-14
+        assert rel(m.cpu().numpy(), m0) < 1e-15 and rel(v.cpu().numpy(), v0) < 1e-15
+
+
+def _tiny_case():
+    grid = synth.Grid(n=(12, 12, 10), h=(1.0, 1.0, 1.5), origin=(0.2, -0.1, 0.3))
+    V0, F = synth.sphere_mesh(1, 3.2, grid.center)
+    Vt = synth.scale_about(V0, (1.08, 0.95, 1.0), grid.center)
+    true_cov = (1.0, 1.1, 2.0, 0.25, 0.1, -0.15)
+    T = oracle.render(Vt, F, grid, opt._psf_full(true_cov, 0.0))["image"]
+    T = synth.add_gaussian_noise(T, 0.02, seed=4)
+    return grid, V0, F, T
+
+
+@pytest.mark.parametrize("optimizer,lr_vertex", [("large_steps", 0.5), ("adam", 0.03)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fit_staggered_matches_oracle(optimizer, lr_vertex, prec, r64, r32):
+    grid, V0, F, T = _tiny_case()
+    psf0 = synth.Psf(sigma=(1.1, 1.1, 1.3), band_tau=1e-3)
+    kw = dict(rounds=2, shape_steps=3, psf_steps=2, lr_vertex=lr_vertex, lr_psf=0.02, optimizer=optimizer)
+    V1, cov1, hs1, hp1 = opt.fit_staggered(V0, F, grid, psf0, T, **kw)
+    r = r64 if prec == "fp64" else r32
+    V, psf, hs, hp, cg = r.fit_staggered(torch.as_tensor(V0).cuda(), torch.as_tensor(F).cuda(), grid, psf0,
+                                         torch.as_tensor(T).cuda(), **kw)
+    tv, tc, tl = (1e-8, 1e-9, 1e-9) if prec == "fp64" else (2e-2, 2e-3, 2e-3)
+    assert rel(V.cpu().numpy() - V0, V1 - V0) < tv
+    assert rel(psf.cov, cov1) < tc
+    assert rel(hs.numpy(), hs1) < tl and rel(hp.numpy(), hp1) < tl
+    if optimizer == "large_steps":
+        assert cg["iterations"] > 0 and cg["unconverged"] == 0
+    else:
+        assert cg["iterations"] == 0
+
+
+def test_fit_staggered_recovers_shape_and_covariance(r32):
+    """FP32 path, 64^3: an anisotropic cell under an oblique PSF, started from a sphere and a round PSF."""
+    grid = synth.Grid(n=(64, 64, 64), h=(0.5, 0.5, 1.0))
+    V0, F = synth.sphere_mesh(3, 8.0, grid.center)
+    Vt = synth.scale_about(V0, (1.06, 0.96, 1.0), grid.center)
+    true_cov = (0.16, 0.2, 0.5, 0.04, 0.02, -0.03)
+    Fd = torch.as_tensor(F).cuda()
+    from paper_2303_10440_b300 import PSF
+
+    T = r32.render(torch.as_tensor(Vt).cuda(), Fd, grid, PSF(cov=true_cov))
+    psf0 = PSF(sigma=(0.45, 0.45, 0.8), band_tau=1e-3)
+    V, psf, hs, hp, cg = r32.fit_staggered(torch.as_tensor(V0).cuda(), Fd, grid, psf0, T, rounds=8, shape_steps=10,
+                                           psf_steps=5, lr_vertex=2.0, lr_psf=0.01)
+    err0 = np.abs(np.array([0.45**2, 0.45**2, 0.64, 0, 0, 0]) - true_cov).sum()
+    err1 = np.abs(np.array(psf.cov) - true_cov).sum()
+    d0 = np.abs(np.linalg.norm(V0 - grid.center, axis=1) - np.linalg.norm(Vt - grid.center, axis=1)).mean()
+    d1 = np.abs(np.linalg.norm(V.cpu().numpy() - grid.center, axis=1) - np.linalg.norm(Vt - grid.center, axis=1)).mean()
+    print(f"\n[staggered 8x(10+5)] shape loss {hs[0]:.3e} -> {hs[-1]:.3e}; psf loss {hp[0]:.3e} -> {hp[-1]:.3e}; "
+          f"cov err {err0:.3f} -> {err1:.3f}; radial err {d0:.3f} -> {d1:.3f}; cg {cg}")
+    assert hp[-1] < 0.5 * hp[0]
+    assert err1 < 0.5 * err0
+    assert d1 < 0.7 * d0
