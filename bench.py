@@ -53,9 +53,11 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5"], default="step",
+    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger"], default="step",
                    help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
-                   "serve-c5: Poisson stream of serving requests")
+                   "serve-c5: Poisson stream of serving requests; stagger: the staggered shape/PSF fit "
+                   "(large-steps shape steps on the narrow band, PSF steps on the whole spectrum)")
+    p.add_argument("--rounds", type=int, default=4, help="staggered rounds in the stagger mode")
     p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 10)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
     return p.parse_args()
@@ -642,8 +644,78 @@ def run_serve_mode(args):
     print(json.dumps(out), flush=True)
 
 
+def run_stagger_mode(args):
+    """Times the staggered fit: per shape step (narrow band, large-steps update with its two smoothing
+    solves) and per PSF step (whole half spectrum, no vertex adjoint), with the library's stage split."""
+    import torch
+
+    import synth
+    from paper_2303_10440_b300 import PSF, Renderer
+
+    dev = torch.device("cuda", 0)
+    case = make_case(args.workload)
+    r = Renderer("fp32" if args.precision == "fp32" else "fp64")
+    Fd = torch.as_tensor(case.F).to(dev)
+    sig = case.psf.sigma
+    true_cov = (sig[0] ** 2, sig[1] ** 2, sig[2] ** 2, 0.15 * sig[0] * sig[1], 0.1 * sig[0] * sig[2],
+                -0.1 * sig[1] * sig[2])
+    T = r.render(torch.as_tensor(case.V_true).to(dev), Fd, case.grid, PSF(cov=true_cov))
+    tau = case.psf.band_tau if case.psf.band_tau > 0 else 1e-2
+    psf0 = PSF(sigma=tuple(1.15 * s for s in sig), band_tau=tau)
+    S, P = 5, 5
+    kw = dict(lr_vertex=0.5, lr_psf=0.01 * min(sig))
+    r.fit_staggered(torch.as_tensor(case.V_init).to(dev), Fd, case.grid, psf0, T, rounds=1, shape_steps=1, psf_steps=1,
+                    **kw)
+    band = int(r.band(case.grid, psf0).numel())
+    nH = case.grid.n[0] * case.grid.n[1] * (case.grid.n[2] // 2 + 1)
+
+    def timed(shape_steps, psf_steps, prof=False):
+        r.profile(prof)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = r.fit_staggered(torch.as_tensor(case.V_init).to(dev), Fd, case.grid, psf0, T, rounds=args.rounds,
+                              shape_steps=shape_steps, psf_steps=psf_steps, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        st = r.profile_read() if prof else None
+        r.profile(False)
+        return a.elapsed_time(b), out, st
+
+    t_shape, _, _ = timed(S, 0)
+    t_psf, _, _ = timed(0, P)
+    t_all, (V, psf, hs, hp, cg), stages = timed(S, P, prof=True)
+    n_t = len(case.F)
+    out = {
+        "metric": "staggered fit: ms per shape step and per PSF step",
+        "mode": "stagger",
+        "precision": args.precision,
+        "workload": f"{case.name}: {n_t} triangles, grid {tuple(case.grid.n)}; target rendered with an oblique "
+                    f"covariance {tuple(round(c, 4) for c in true_cov)}; start: the initial mesh and a round PSF "
+                    f"1.15x wider; {args.rounds} rounds of {S} shape + {P} PSF steps",
+        "band_frequencies_shape_step": band,
+        "half_spectrum_frequencies_psf_step": nH,
+        "ms_per_shape_step": t_shape / (args.rounds * S),
+        "ms_per_psf_step": t_psf / (args.rounds * P),
+        "ms_per_round": t_all / args.rounds,
+        # the headline's unit: forward and adjoint terms both counted
+        "shape_terms_per_s": 2 * n_t * band / (t_shape / (args.rounds * S) * 1e-3),
+        "cg_iterations_per_column_solve": cg["iterations"] / max(1, 2 * 3 * args.rounds * S),
+        "cg_max": cg["max"],
+        "stage_ms_per_round": {k: v[0] / args.rounds for k, v in stages.items() if v[1]},
+        "shape_loss": [float(hs[0]), float(hs[-1])],
+        "psf_loss": [float(hp[0]), float(hp[-1])],
+        "cov_fitted": [round(c, 5) for c in psf.cov],
+        "cov_true": [round(c, 5) for c in true_cov],
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "stagger":
+        run_stagger_mode(args)
+        return
     if args.mode != "step":
         run_serve_mode(args)
         return
