@@ -323,7 +323,9 @@ typedef struct {
     dm_psf psf;            /* DM_PSF_DIAG; sigma is the initial value when fit.lr_psf > 0 */
     dm_fit_options fit;    /* steps, loss, learning rates, Adam constants */
     int32_t label;         /* DM_SURFACE or DM_VOLUME */
-    int32_t reserved;
+    int32_t optimizer;     /* vertex optimiser: DM_OPT_ADAM or DM_OPT_LARGE_STEPS (uniform Adam on
+                              u = (1 + lambda L) v, FP32 smoothing solves, tolerance 1e-6) */
+    double lambda;         /* large-steps smoothing weight (<= 0: 50) */
 } dm_job;
 
 #define DM_JOB_QUEUED 0

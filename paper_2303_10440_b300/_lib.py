@@ -107,7 +107,8 @@ class dm_job(ctypes.Structure):
         ("psf", dm_psf),
         ("fit", dm_fit_options),
         ("label", c_i32),
-        ("reserved", c_i32),
+        ("optimizer", c_i32),
+        ("lam", c_f64),
     ]
 
 

@@ -9,6 +9,7 @@
 // keeps the iterate, residual, search direction, product and inverse diagonal in
 // shared memory whenever 5 n_v values fit (10,000+ vertices in FP32). There is no
 // inter-CTA waiting anywhere.
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -303,8 +304,13 @@ cudaError_t launch_pcg(const int32_t* lptr, const int32_t* lcol, int64_t n_v, do
     const size_t want = (PCG_RED + 5 * (size_t)n_v) * sizeof(R);
     const bool smem = want <= (size_t)max_smem;
     const size_t bytes = smem ? want : PCG_RED * sizeof(R);
-    e = cudaFuncSetAttribute(k_pcg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
+    // raise the kernel's dynamic shared-memory limit to the opt-in maximum once per device
+    static std::atomic<int> raised[64];
+    if (bytes > 48 * 1024 && (dev >= 64 || raised[dev].load() == 0)) {
+        e = cudaFuncSetAttribute(k_pcg<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+        if (dev < 64) raised[dev].store(1);
+    }
     PcgArgs<R> a;
     a.lp = lptr;
     a.lc = lcol;

@@ -89,6 +89,8 @@ struct SJob {
     dm_psf psf;
     dm_fit_options fit;
     int label = DM_SURFACE;
+    int optimizer = DM_OPT_ADAM;
+    double lambda = 50.0;
     int state = DM_JOB_QUEUED;
     int steps_done = 0;
     double t_submit = 0, t_start = 0, t_end = 0, last_loss = NAN;
@@ -97,6 +99,11 @@ struct SJob {
     Sizes z;
     Bufs b;
     double *mV = nullptr, *vV = nullptr, *ms = nullptr, *vs = nullptr, *hist = nullptr;
+    // large-steps state: Laplacian rows, solver work, warm starts, uniform-Adam step and maxima
+    int32_t *lptr = nullptr, *lcol = nullptr;
+    float* pcg_work = nullptr;
+    double *gu = nullptr, *wv = nullptr, *dl = nullptr, *aup = nullptr;
+    unsigned long long* cg_stats = nullptr;
     FFTAxis ax[3];
     int chunk_tiles = 1;
     cudaStream_t stream = nullptr;  // the job's stream for its own stage kernels (held while admitted)
@@ -119,10 +126,21 @@ int job_chunk_tiles(const Sizes& z, int max_tiles, int sm_count) {
     return (int)c;
 }
 
-size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, double** mom, double** hist) {
+size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, double** mom, double** hist,
+                  SJob* J) {
     layout(z, A, b, true, true, false, true, false);
     *mom = A.take<double>(6 * n_v + 8);
     *hist = A.take<double>(steps);
+    if (J->optimizer == DM_OPT_LARGE_STEPS) {
+        J->lptr = A.take<int32_t>(n_v + 1);
+        J->lcol = A.take<int32_t>(6 * z.n_t);
+        J->pcg_work = A.take<float>(pcg_work_elems(n_v));
+        J->gu = A.take<double>(3 * n_v);
+        J->wv = A.take<double>(3 * n_v);
+        J->dl = A.take<double>(3 * n_v);
+        J->aup = A.take<double>(adam_uniform_partials(3 * n_v));
+        J->cg_stats = A.take<unsigned long long>(4);
+    }
     return A.off + 256;
 }
 
@@ -189,12 +207,12 @@ bool setup_job(dm_server* S, SJob* J) {
     Arena A;
     Bufs b;
     double *mom, *hist;
-    const size_t bytes = job_layout(z, J->fit.steps, z.n_v, A, b, &mom, &hist);
+    const size_t bytes = job_layout(z, J->fit.steps, z.n_v, A, b, &mom, &hist, J);
     size_t off;
     if (!S->arena.alloc(bytes, &off)) return false;
     A.base = S->arena.base + off;
     A.off = 0;
-    job_layout(z, J->fit.steps, z.n_v, A, b, &mom, &hist);
+    job_layout(z, J->fit.steps, z.n_v, A, b, &mom, &hist, J);
     J->off = off;
     J->bytes = bytes;
     J->z = z;
@@ -230,6 +248,12 @@ bool setup_job(dm_server* S, SJob* J) {
               launch_csr(b.F, z.n_t, z.n_v, b.cnt, b.ptr, b.ent, ctx->d_err, st) == cudaSuccess &&
               fft_axes(ctx, J->grid.n, J->ax) == DM_OK;
     g_launches += 5;
+    if (ok && J->optimizer == DM_OPT_LARGE_STEPS) {
+        ok = launch_laplacian(b.F, b.ptr, b.ent, z.n_v, b.cnt, J->lptr, J->lcol, ctx->d_err, st) == cudaSuccess &&
+             cudaMemsetAsync(J->gu, 0, 6 * z.n_v * sizeof(double), st) == cudaSuccess &&
+             cudaMemsetAsync(J->cg_stats, 0, 4 * sizeof(unsigned long long), st) == cudaSuccess;
+        g_launches += 3;
+    }
     // host vectors stay until the uploads have run (synchronised at the end of the iteration)
     if (!ok) {
         cudaGetLastError();
@@ -393,9 +417,20 @@ bool iterate(dm_server* S, bool sync) {
         ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, js) ==
               cudaSuccess;
         const dm_fit_options& o = J->fit;
-        ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps, J->steps_done + 1,
-                          js) == cudaSuccess;
-        g_launches += 4;
+        if (J->optimizer == DM_OPT_LARGE_STEPS) {
+            // v -= (1 + lambda L)^-1 AdamUniform((1 + lambda L)^-1 dL/dv)
+            ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, b.dV, J->gu, nullptr, J->pcg_work, 1e-6, 2000,
+                                    J->cg_stats, js) == cudaSuccess;
+            ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
+                                      J->steps_done + 1, J->aup, js) == cudaSuccess;
+            ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, J->dl, J->wv, b.V, J->pcg_work, 1e-6, 2000,
+                                    J->cg_stats, js) == cudaSuccess;
+            g_launches += 7;
+        } else {
+            ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
+                              J->steps_done + 1, js) == cudaSuccess;
+            g_launches += 4;
+        }
         if (o.lr_psf > 0) {
             ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
                               J->steps_done + 1, js) == cudaSuccess;
@@ -511,6 +546,8 @@ dm_status validate_job(const dm_job* j) {
     if (j->fit.steps < 1 || j->fit.loss < 0 || j->fit.loss > 2) return DM_ERR_ARG;
     if (j->psf.kind != DM_PSF_DIAG) return DM_ERR_UNSUPPORTED;
     if (j->label != DM_SURFACE && j->label != DM_VOLUME) return DM_ERR_ARG;
+    if (j->optimizer != DM_OPT_ADAM && j->optimizer != DM_OPT_LARGE_STEPS) return DM_ERR_ARG;
+    if (std::isnan(j->lambda)) return DM_ERR_ARG;
     for (int a = 0; a < 3; ++a) {
         if (!(j->psf.sigma[a] > 0) || !(j->grid.h[a] > 0) || j->grid.n[a] < 1) return DM_ERR_ARG;
         FFTAxis ax;
@@ -584,6 +621,8 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     J->psf = job->psf;
     J->fit = job->fit;
     J->label = job->label;
+    J->optimizer = job->optimizer;
+    J->lambda = job->lambda > 0 ? job->lambda : 50.0;
     // a job whose state can never fit the arena is refused now rather than queued forever
     Sizes z = make_sizes(S->ctx, &job->grid, job->n_v, job->n_t, job->psf.band_tau > 0, job->label);
     const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
@@ -592,7 +631,7 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     Arena A;
     Bufs b;
     double *mom, *hist;
-    if (job_layout(z, job->fit.steps, job->n_v, A, b, &mom, &hist) > S->arena.total) {
+    if (job_layout(z, job->fit.steps, job->n_v, A, b, &mom, &hist, J) > S->arena.total) {
         delete J;
         return DM_ERR_OOM;
     }

@@ -47,7 +47,8 @@ class FitServer:
         return float(self.lib.dm_server_clock(self.h))
 
     def submit(self, V, F, target, grid, psf, steps: int, lr_vertex: float, lr_psf: float = 0.0, loss: str = "mse",
-               label: str = "surface", beta1=0.9, beta2=0.999, eps=1e-20) -> int:
+               label: str = "surface", beta1=0.9, beta2=0.999, eps=1e-20, optimizer: str = "adam",
+               lam: float = 50.0) -> int:
         V = np.ascontiguousarray(V, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.int32)
         T = np.ascontiguousarray(target, dtype=np.float32)
@@ -61,6 +62,8 @@ class FitServer:
         j.psf = _psf(psf)
         j.fit = _lib.dm_fit_options(int(steps), _lib.LOSSES[loss], float(lr_vertex), float(lr_psf), beta1, beta2, eps)
         j.label = _lib.DM_VOLUME if label == "volume" else _lib.DM_SURFACE
+        j.optimizer = _lib.OPTIMIZERS[optimizer]
+        j.lam = float(lam)
         jid = ctypes.c_int64()
         st = self.lib.dm_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid))  # copies every input
         if st != _lib.DM_OK:

@@ -11,6 +11,7 @@ from .meshes import (
     icosphere,
     sphere_mesh,
     sh_deformed_sphere,
+    sh_radius,
     box_mesh,
     scale_about,
     random_triangles,
@@ -23,6 +24,7 @@ __all__ = [
     "icosphere",
     "sphere_mesh",
     "sh_deformed_sphere",
+    "sh_radius",
     "box_mesh",
     "scale_about",
     "random_triangles",

@@ -109,6 +109,15 @@ def sh_deformed_sphere(
     ``aniso_scale`` scales the deformed shape about its centre afterwards.
     """
     U, F = icosphere(level)
+    r = sh_radius(U, radius, lmax, coef_sigma, seed)
+    V = U * r[:, None] * np.asarray(aniso_scale, dtype=np.float64)
+    return V + np.asarray(center, dtype=np.float64), F
+
+
+def sh_radius(U: np.ndarray, radius: float, lmax: int, coef_sigma: float, seed: int) -> np.ndarray:
+    """The radius r(theta, phi) of ``sh_deformed_sphere`` along unit directions U [n, 3]
+    (same coefficients for the same seed), so that distances to that surface can be measured."""
+    U = np.asarray(U, dtype=np.float64)
     rng = np.random.default_rng(seed)
     theta = np.arccos(np.clip(U[:, 2], -1.0, 1.0))
     phi = np.arctan2(U[:, 1], U[:, 0])
@@ -116,9 +125,7 @@ def sh_deformed_sphere(
     for l in range(lmax + 1):
         for m in range(-l, l + 1):
             r += rng.normal(0.0, coef_sigma) * _real_sph_harm(l, m, theta, phi)
-    r = np.maximum(r, 0.2 * radius)
-    V = U * r[:, None] * np.asarray(aniso_scale, dtype=np.float64)
-    return V + np.asarray(center, dtype=np.float64), F
+    return np.maximum(r, 0.2 * radius)
 
 
 def box_mesh(lo, hi) -> tuple[np.ndarray, np.ndarray]:

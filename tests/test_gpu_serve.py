@@ -156,3 +156,43 @@ def test_invalid_jobs_are_refused(setup):
     with pytest.raises(RuntimeError, match="DM_ERR_UNSUPPORTED"):
         s.submit(**bad)
     s.shutdown()
+
+
+def test_large_steps_job_matches_the_staggered_shape_fit(setup):
+    """A served job with the large-steps optimiser (Section 5.1) follows dm_fit_staggered's shape steps."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    j = dict(jobs[1], optimizer="large_steps", lr_vertex=0.5)
+    s = FitServer(max_jobs=2)
+    i = s.submit(**j)
+    assert s.wait(i, timeout=300)
+    res = s.result(i)
+    s.shutdown()
+    V, _, hs, _, cg = r32.fit_staggered(torch.as_tensor(j["V"]).cuda(), torch.as_tensor(j["F"]).cuda(), j["grid"],
+                                        j["psf"], torch.as_tensor(j["target"]).cuda(), rounds=1, shape_steps=STEPS,
+                                        psf_steps=0, lr_vertex=0.5, lr_psf=0.0, shape_loss="mse")
+    moved = np.linalg.norm(V.cpu().numpy() - j["V"])
+    assert moved > 0 and cg["iterations"] > 0
+    assert np.linalg.norm(res.V - V.cpu().numpy()) < 1e-3 * moved
+    assert np.allclose(res.loss_history, hs.numpy(), rtol=1e-4)
+
+
+def test_large_steps_job_is_the_same_alone_and_among_adam_jobs(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    ls = dict(jobs[2], optimizer="large_steps", lr_vertex=0.5)
+    s1 = FitServer(max_jobs=4)
+    a = s1.submit(**ls)
+    assert s1.wait(a, timeout=300)
+    alone = s1.result(a)
+    s1.shutdown()
+    s2 = FitServer(max_jobs=4)
+    ids = [s2.submit(**jobs[1]), s2.submit(**ls), s2.submit(**jobs[3])]
+    for i in ids:
+        assert s2.wait(i, timeout=300)
+    mix = s2.result(ids[1])
+    s2.shutdown()
+    assert np.array_equal(alone.V, mix.V)
+    assert np.array_equal(alone.loss_history, mix.loss_history)
