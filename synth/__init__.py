@@ -13,6 +13,7 @@ from .meshes import (
     sh_deformed_sphere,
     sh_radius,
     box_mesh,
+    box_foam,
     scale_about,
     random_triangles,
     pack_cells,
@@ -26,6 +27,7 @@ __all__ = [
     "sh_deformed_sphere",
     "sh_radius",
     "box_mesh",
+    "box_foam",
     "scale_about",
     "random_triangles",
     "pack_cells",

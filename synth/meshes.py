@@ -197,3 +197,43 @@ def pack_cells(
         if all(np.linalg.norm(c - c2) >= r + r2 + clearance for c2, r2 in cells):
             cells.append((c, r))
     return cells
+
+
+def box_foam(cells=(2, 2, 1), cell_size=(6.0, 6.0, 6.0), subdiv: int = 4, origin=(0.0, 0.0, 0.0), jitter: float = 0.0,
+             seed: int = 0):
+    """A tissue of box cells in one non-manifold mesh: every face of the cell lattice is split into
+    subdiv x subdiv quads of two triangles; a wall between two cells appears once and carries
+    density 2 (two membranes), an outer face density 1. Corner positions are shared; ``jitter``
+    moves every vertex by N(0, jitter^2) (seeded). Returns (V, F, rho)."""
+    nc = np.asarray(cells, dtype=np.int64)
+    h = np.asarray(cell_size, dtype=np.float64) / subdiv
+    npts = nc * subdiv + 1  # lattice points per axis
+    index = {}
+    V = []
+
+    def vid(p):
+        key = tuple(int(x) for x in p)
+        if key not in index:
+            index[key] = len(V)
+            V.append(np.asarray(origin, dtype=np.float64) + np.asarray(key, dtype=np.float64) * h)
+        return index[key]
+
+    F, rho = [], []
+    for axis in range(3):
+        u, w = [a for a in range(3) if a != axis]
+        for plane in range(0, int(nc[axis]) + 1):
+            c = plane * subdiv
+            outer = plane == 0 or plane == nc[axis]
+            for i in range(int(npts[u]) - 1):
+                for j in range(int(npts[w]) - 1):
+                    q = []
+                    for di, dj in ((0, 0), (1, 0), (1, 1), (0, 1)):
+                        p = [0, 0, 0]
+                        p[axis], p[u], p[w] = c, i + di, j + dj
+                        q.append(vid(p))
+                    F += [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
+                    rho += [1.0 if outer else 2.0] * 2
+    V = np.array(V)
+    if jitter > 0:
+        V = V + np.random.default_rng(seed).normal(0.0, jitter, size=V.shape)
+    return V, np.asarray(F, dtype=np.int32), np.asarray(rho, dtype=np.float64)

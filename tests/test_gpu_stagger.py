@@ -128,6 +128,37 @@ def test_fit_staggered_matches_oracle(optimizer, lr_vertex, prec, r64, r32):
         assert cg["iterations"] == 0
 
 
+@pytest.mark.parametrize("variant", ["volume", "tissue_foam"])
+def test_fit_staggered_variants_match_oracle(variant, r64):
+    """FP64 staggered fits of a volume-labelled cell and of a weighted multi-cell foam."""
+    if variant == "volume":
+        grid, V0, F, T = _tiny_case()
+        kw = dict(mode="volume")
+        gkw = dict(label="volume")
+        T = oracle.render(synth.scale_about(V0, (1.06, 0.96, 1.0), grid.center), F, grid,
+                          opt._psf_full((1.0, 1.1, 2.0, 0.25, 0.1, -0.15), 0.0), "volume")["image"]
+    else:
+        grid = synth.Grid(n=(16, 16, 12), h=(1.0, 1.0, 1.25))
+        V0, F, rho = synth.box_foam((2, 1, 1), (5.0, 6.0, 6.0), subdiv=2, origin=(3.0, 5.0, 4.5), jitter=0.1, seed=2)
+        Vt = V0 + 0.25 * np.cos(V0[:, [2, 0, 1]] / 2.5)
+        T = oracle.render(Vt, F, grid, opt._psf_full((1.0, 1.1, 1.8, 0.2, 0.0, 0.1), 0.0), weights=rho)["image"]
+        kw = dict(weights=rho)  # densities 1 and 2: exact in the FP32 weights the library takes
+        gkw = dict(weights=torch.as_tensor(rho.astype(np.float32)).cuda())
+    psf0 = synth.Psf(sigma=(1.1, 1.1, 1.3), band_tau=1e-3)
+    common = dict(rounds=2, shape_steps=2, psf_steps=2, lr_vertex=0.3, lr_psf=0.02)
+    V1, cov1, hs1, hp1 = opt.fit_staggered(V0, F, grid, psf0, T, **common, **kw)
+    V, psf, hs, hp, cg = r64.fit_staggered(torch.as_tensor(V0).cuda(), torch.as_tensor(F).cuda(), grid, psf0,
+                                           torch.as_tensor(T).cuda(), **common, **gkw)
+    # the smoothing filter (1 + lambda L)^-2 keeps the low modes of dL/dv and drops the rest, so a
+    # relative gradient error e (1e-9 on the FP64 path) can grow up to kappa e in the displacement,
+    # kappa = 1 + 2 lambda (max degree) the smoothing matrix's condition bound
+    kappa = 1.0 + 2 * 50.0 * opt.laplacian(F, len(V0)).diagonal().max()
+    assert rel(V.cpu().numpy() - V0, V1 - V0) < 1e-9 * kappa
+    assert rel(psf.cov, cov1) < 1e-9
+    assert rel(hs.numpy(), hs1) < 1e-9 and rel(hp.numpy(), hp1) < 1e-9
+    assert cg["unconverged"] == 0
+
+
 def test_fit_staggered_recovers_shape_and_covariance(r32):
     """FP32 path, 64^3: an anisotropic cell under an oblique PSF, started from a sphere and a round PSF."""
     grid = synth.Grid(n=(64, 64, 64), h=(0.5, 0.5, 1.0))

@@ -124,3 +124,21 @@ def test_mesh_adjoint_matches_finite_differences(mode):
     S = oracle.mesh_ft(V, F, xi, mode, c0)
     ref = np.real(np.conj(Gs)[:, None] * (-1j * xi * S[:, None])).sum(axis=0)
     assert np.allclose(dV.sum(axis=0), ref, atol=1e-10)
+
+
+def test_box_foam_with_doubled_walls_is_the_sum_of_its_cells():
+    """A tissue of 2 x 2 x 1 box cells in one non-manifold mesh, shared walls at density 2
+    (Section 3.3), equals the sum of the four cells' closed surfaces (closed-form sinc products)."""
+    size, org = np.array([6.0, 5.0, 7.0]), np.array([2.0, 1.5, 3.0])
+    V, F, rho = synth.box_foam((2, 2, 1), size, subdiv=3, origin=org)
+    grid = synth.Grid(n=(16, 16, 12), h=(1.0, 1.0, 1.25))
+    nvec, _ = oracle.half_spectrum(grid.n)
+    xi = oracle.wavevectors(nvec, grid)[::7]
+    S = oracle.mesh_ft(V, F, xi, "surface", weights=rho)
+    ref = np.zeros(len(xi), dtype=complex)
+    for i in range(2):
+        for j in range(2):
+            lo = org + size * np.array([i, j, 0])
+            ref += np.array([_box_surface(x, lo, lo + size) for x in xi])
+    assert np.max(np.abs(S - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert abs(oracle.surface_area(V, F, rho) - 4 * 2 * (size[0] * size[1] + size[1] * size[2] + size[0] * size[2])) < 1e-9
