@@ -13,8 +13,9 @@
 //   df/dphi_mid  = e^{-i phi_m} i (q(d2) + conj q(d1)) / s                    (Eq. 10)
 //   df/dphi_hi   = e^{-i phi_m} (i r(d2) - f_m) / s
 // (f_m = i (E(d2) - conj E(d1)) / s). E and q switch to their Taylor series for
-// gaps below TG; terms whose three phases lie within TS of each other take the
-// series branch of meshft_math.cuh. phi_m = phi_1 + (phi_m - phi_1), where phi_1
+// gaps below TG; terms whose three phases lie within TS of each other replace f_m
+// and the derivatives by their series in the same frame (series_f / series_adj),
+// so every term shares the vertex mapping. phi_m = phi_1 + (phi_m - phi_1), where phi_1
 // comes from exact integer reduction (n . U mod 2^32) and the offset from the
 // FP32 edge projections.
 //
@@ -85,6 +86,14 @@ __device__ __forceinline__ Order order3(float a, float b) {
     return o;
 }
 
+// Reciprocal by the PTX approximate instruction (one MUFU op; arguments here are >= TG or >= TS,
+// never subnormal). __fdividef(1, x) adds range handling that measurably costs issue slots.
+__device__ __forceinline__ float rcpa(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Gap functions for both lanes of both gaps: E(d1), E(d2) and (adjoint) q(d1), q(d2).
 // Since s = d1 + d2 >= TS >= 2 TG here, at most one gap per lane is below TG, so a single
 // Taylor evaluation on min(d1, d2) serves whichever gap needs it.
@@ -104,9 +113,9 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
     __sincosf(d2.y, &s2b, &c2b);
     const bool m1a = d1.x < TG, m1b = d1.y < TG, m2a = d2.x < TG, m2b = d2.y < TG;
     // reciprocals on the MUFU pipe (the FP32 pipe is the busier one); 1/d only used for d >= TG
-    const F2 inv1 = mk(__fdividef(1.f, fmaxf(d1.x, TG)), __fdividef(1.f, fmaxf(d1.y, TG)));
-    const F2 inv2 = mk(__fdividef(1.f, fmaxf(d2.x, TG)), __fdividef(1.f, fmaxf(d2.y, TG)));
-    g.invs = mk(__fdividef(1.f, s.x), __fdividef(1.f, s.y));
+    const F2 inv1 = mk(rcpa(fmaxf(d1.x, TG)), rcpa(fmaxf(d1.y, TG)));
+    const F2 inv2 = mk(rcpa(fmaxf(d2.x, TG)), rcpa(fmaxf(d2.y, TG)));
+    g.invs = mk(rcpa(s.x), rcpa(s.y));  // inf when s = 0; such lanes take the series below
     const F2 dm = mk(fminf(d1.x, d2.x), fminf(d1.y, d2.y));
     const F2 tm = mul2(dm, dm);
     F2 pr, pi;
@@ -127,6 +136,77 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
         g.q1y = sel2(m1a, m1b, pi, mul2(E1yd, inv1));
         g.q2x = sel2(m2a, m2b, qtx, mul2(add2(E2xd, mone), inv2));
         g.q2y = sel2(m2a, m2b, pi, mul2(E2yd, inv2));
+    }
+}
+
+// Middle-frame series for terms whose three phases lie within TS (s < TS). With the nodes
+// (-d1, 0, d2) relative to the middle phase and F(x) = -e^{-ix}, the divided differences are
+// sums over the complete homogeneous symmetric polynomials h_k of the nonzero nodes:
+//   f_m  = DD2[F](-d1, 0, d2)      = sum_k (-i)^k h_k(-d1, d2) / (k+2)!
+//   D_mid = DD3[F](-d1, 0, 0, d2)  = sum_k (-i)^(k+1) h_k(-d1, d2) / (k+3)!
+//   D_lo  = DD3[F](-d1, -d1, 0, d2) = sum_k (-i)^(k+1) h_k(-d1, -d1, d2) / (k+3)!
+//   D_hi  = -(i f_m + D_lo + D_mid)     (the three phase derivatives sum to -i f_m)
+// h_k(-d1, d2) = (d2 - d1) h_{k-1} + d1 d2 h_{k-2}; h_k(-d1, -d1, d2) = e1 h_{k-1} - e2 h_{k-2}
+// + e3 h_{k-3} with e1 = d2 - 2 d1, e2 = d1^2 - 2 d1 d2, e3 = d1^2 d2. With s < 0.5 the terms fall
+// below 1e-7 of the sum by k = 7, so KS = 8 terms serve FP32. Both lanes at once.
+constexpr int KS = 8;
+
+// (-i)^j = sign * (1 or i): real for even j; sign + for j mod 4 in {0, 3}.
+__host__ __device__ constexpr float isign(int j) { return (j % 4 == 0 || j % 4 == 3) ? 1.f : -1.f; }
+
+__device__ __forceinline__ void series_f(F2 d1, F2 d2, F2& fr, F2& fi) {
+    const F2 del = sub2(d2, d1), pr = mul2(d1, d2);
+    F2 hm2 = mk(1.f, 1.f), hm1 = del;
+    fr = mk((float)inv_fact(2), (float)inv_fact(2));
+    fi = mul2(del, mk(-(float)inv_fact(3), -(float)inv_fact(3)));
+#pragma unroll
+    for (int k = 2; k < KS; ++k) {
+        const F2 h = fma2(del, hm1, mul2(pr, hm2));
+        const float c = isign(k) * (float)inv_fact(k + 2);
+        if (k % 2 == 0)
+            fr = fma2(h, mk(c, c), fr);
+        else
+            fi = fma2(h, mk(c, c), fi);
+        hm2 = hm1;
+        hm1 = h;
+    }
+}
+
+__device__ __forceinline__ void series_adj(F2 d1, F2 d2, F2& fr, F2& fi, F2& lr, F2& li, F2& mr, F2& mi) {
+    const F2 del = sub2(d2, d1), pr = mul2(d1, d2);
+    const F2 d1s = mul2(d1, d1);
+    const F2 e1 = sub2(del, d1);                        // d2 - 2 d1
+    const F2 e2 = fma2(pr, mk(-2.f, -2.f), d1s);        // d1^2 - 2 d1 d2
+    const F2 e3 = mul2(d1s, d2);                        // d1^2 d2
+    // k = 0, 1
+    fr = mk((float)inv_fact(2), (float)inv_fact(2));
+    fi = mul2(del, mk(-(float)inv_fact(3), -(float)inv_fact(3)));
+    mi = mk(-(float)inv_fact(3), -(float)inv_fact(3));  // j = 1: -i h_0 / 3!
+    mr = mul2(del, mk(-(float)inv_fact(4), -(float)inv_fact(4)));  // j = 2: -h_1 / 4!
+    li = mi;
+    lr = mul2(e1, mk(-(float)inv_fact(4), -(float)inv_fact(4)));
+    F2 hm2 = mk(1.f, 1.f), hm1 = del;               // h(-d1, d2)
+    F2 gm3 = mk(0.f, 0.f), gm2 = mk(1.f, 1.f), gm1 = e1;  // h(-d1, -d1, d2)
+#pragma unroll
+    for (int k = 2; k < KS; ++k) {
+        const F2 h = fma2(del, hm1, mul2(pr, hm2));
+        const F2 g = fma2(e3, gm3, fms2(e1, gm1, mul2(e2, gm2)));
+        const float cf = isign(k) * (float)inv_fact(k + 2);
+        const float cd = isign(k + 1) * (float)inv_fact(k + 3);
+        if (k % 2 == 0) {
+            fr = fma2(h, mk(cf, cf), fr);
+            mi = fma2(h, mk(cd, cd), mi);
+            li = fma2(g, mk(cd, cd), li);
+        } else {
+            fi = fma2(h, mk(cf, cf), fi);
+            mr = fma2(h, mk(cd, cd), mr);
+            lr = fma2(g, mk(cd, cd), lr);
+        }
+        hm2 = hm1;
+        hm1 = h;
+        gm3 = gm2;
+        gm2 = gm1;
+        gm1 = g;
     }
 }
 
@@ -181,24 +261,6 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
             const Order oA = order3(a.x, b.x), oB = order3(a.y, b.y);
             const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
             const F2 s = sub2(hi, lo);
-            if (s.x < TS || s.y < TS) {
-                // near-degenerate: evaluate each lane with the series branch (rare)
-                const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y}, ww[2] = {w.x, w.y};
-                float fx[2], fy[2];
-        #pragma unroll
-                for (int l = 0; l < 2; ++l) {
-                    TriLocal<float, false> o;
-                    tri_local<float, false>(aa[l], bb[l], o);
-                    float sp, cp;
-                    __sincosf(pp[l], &sp, &cp);
-                    const Cx<float> f = cmul(cmul(Cx<float>{cp, -sp}, o.rho), o.f);
-                    fx[l] = ww[l] * f.x;
-                    fy[l] = ww[l] * f.y;
-                }
-                PX = add2(PX, mk(fx[0], fx[1]));
-                PY = add2(PY, mk(fy[0], fy[1]));
-                continue;
-            }
             const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
             const F2 phm = add2(ph, mid);
             Gaps<false> g;
@@ -207,13 +269,22 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
             __sincosf(phm.x, &sma, &cma);
             __sincosf(phm.y, &smb, &cmb);
             const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
-            // f = (cm - i sm) (-gy + i gx) invs, gx = E2x - E1x, gy = E2y + E1y
+            // f_m = i (E2 - conj E1) / s = -fmr + i fmi with gx = E2x - E1x, gy = E2y + E1y
             const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
-            const F2 fx = fms2(sm, gx, mul2(cm, gy));
-            const F2 fy = fma2(cm, gx, mul2(sm, gy));
-            const F2 we = mul2(w, g.invs);
-            PX = fma2(we, fx, PX);
-            PY = fma2(we, fy, PY);
+            F2 fmr = mul2(gy, g.invs), fmi = mul2(gx, g.invs);
+            if (s.x < TS || s.y < TS) {
+                // three phases within TS: the series in the same frame (warp-divergent, rare)
+                F2 sr, si;
+                series_f(d1, d2, sr, si);
+                const bool ta = s.x < TS, tb = s.y < TS;
+                fmr = sel2(ta, tb, mk(-sr.x, -sr.y), fmr);
+                fmi = sel2(ta, tb, si, fmi);
+            }
+            // f = e^{-i phi_m} f_m = (cm - i sm)(-fmr + i fmi)
+            const F2 fx = fms2(sm, fmi, mul2(cm, fmr));
+            const F2 fy = fma2(cm, fmi, mul2(sm, fmr));
+            PX = fma2(w, fx, PX);
+            PY = fma2(w, fy, PY);
         }
         kahan_add(SX.x, CX.x, PX.x);
         kahan_add(SX.y, CX.y, PX.y);
@@ -295,30 +366,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
             const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
             const F2 s = sub2(hi, lo);
             F2 rf, tv1, tv2, tv3;
-            if (s.x < TS || s.y < TS) {
-                // near-degenerate: each lane by the series branch in the vertex-1 frame (rare)
-                const float aa[2] = {a.x, a.y}, bb[2] = {b.x, b.y}, pp[2] = {ph.x, ph.y};
-                const float gr[2] = {R.Gr.x, R.Gr.y}, gi[2] = {R.Gi.x, R.Gi.y};
-                float o_rf[2], o1[2], o2[2], o3[2];
-            #pragma unroll
-                for (int l = 0; l < 2; ++l) {
-                    TriLocal<float, true> o;
-                    tri_local<float, true>(aa[l], bb[l], o);
-                    float sp, cp;
-                    __sincosf(pp[l], &sp, &cp);
-                    const Cx<float> H = cmul(Cx<float>{gr[l], -gi[l]}, cmul(Cx<float>{cp, -sp}, o.rho));
-                    o_rf[l] = re_mul(H, o.f);
-                    const float t0 = re_mul(H, o.D[0]), t1 = re_mul(H, o.D[1]), t2 = re_mul(H, o.D[2]);
-                    const float tlo = sel3(o.plo, t0, t1, t2), thi = sel3(o.phi, t0, t1, t2);
-                    o1[l] = sel3(o.p1, t0, t1, t2);
-                    o2[l] = o.ab ? tlo : thi;
-                    o3[l] = o.ab ? thi : tlo;
-                }
-                rf = mk(o_rf[0], o_rf[1]);
-                tv1 = mk(o1[0], o1[1]);
-                tv2 = mk(o2[0], o2[1]);
-                tv3 = mk(o3[0], o3[1]);
-            } else {
+            {
                 const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
                 const F2 phm = add2(ph, mid);
                 Gaps<true> g;
@@ -332,18 +380,37 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
                 const F2 r2x = sub2(g.E2y, g.q2x), r2y = mk(-g.E2x.x - g.q2y.x, -g.E2x.y - g.q2y.y);
                 // f_m = i (E2 - conj E1) invs = (-gy, gx) invs
                 const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
-                const F2 mfx = mul2(gy, g.invs);  // -f_m.x
-                const F2 fyv = mul2(gx, g.invs);  // f_m.y
+                F2 mfx = mul2(gy, g.invs);  // -f_m.x
+                F2 fyv = mul2(gx, g.invs);  // f_m.y
                 // unscaled derivatives (times s): D_lo = f + i conj r1, D_mid = i (q2 + conj q1), D_hi = i r2 - f
-                const F2 Dlx = sub2(r1y, mfx), Dly = add2(fyv, r1x);
-                const F2 Dmx = sub2(g.q1y, g.q2y), Dmy = add2(g.q2x, g.q1x);
-                const F2 Dhx = sub2(mfx, r2y), Dhy = sub2(r2x, fyv);
+                F2 Dlx = sub2(r1y, mfx), Dly = add2(fyv, r1x);
+                F2 Dmx = sub2(g.q1y, g.q2y), Dmy = add2(g.q2x, g.q1x);
+                F2 Dhx = sub2(mfx, r2y), Dhy = sub2(r2x, fyv);
+                F2 inv = g.invs;
+                if (s.x < TS || s.y < TS) {
+                    // three phases within TS: the series in the same frame gives f_m and the true
+                    // derivatives (not times s), so those lanes take scale 1 (warp-divergent, rare)
+                    F2 fr, fi, lr, li, mr, mi;
+                    series_adj(d1, d2, fr, fi, lr, li, mr, mi);
+                    const F2 hr = sub2(sub2(fi, lr), mr);                      // D_hi = -(i f_m + D_lo + D_mid)
+                    const F2 hi_ = mk(-fr.x - li.x - mi.x, -fr.y - li.y - mi.y);
+                    const bool ta = s.x < TS, tb = s.y < TS;
+                    mfx = sel2(ta, tb, mk(-fr.x, -fr.y), mfx);
+                    fyv = sel2(ta, tb, fi, fyv);
+                    Dlx = sel2(ta, tb, lr, Dlx);
+                    Dly = sel2(ta, tb, li, Dly);
+                    Dmx = sel2(ta, tb, mr, Dmx);
+                    Dmy = sel2(ta, tb, mi, Dmy);
+                    Dhx = sel2(ta, tb, hr, Dhx);
+                    Dhy = sel2(ta, tb, hi_, Dhy);
+                    inv = sel2(ta, tb, mk(1.f, 1.f), inv);
+                }
                 // conj(Gw) e^{-i phi_m} = h - i k with h = Gr cm - Gi sm, k = Gr sm + Gi cm;
                 // Re((h - i k)(u + i v)) = h u + k v
                 const F2 h = fms2(R.Gr, cm, mul2(R.Gi, sm));
                 const F2 k = fma2(R.Gr, sm, mul2(R.Gi, cm));
                 rf = fms2(k, fyv, mul2(h, mfx));  // h f.x + k f.y with f.x = -mfx
-                const F2 hs = mul2(h, g.invs), ks = mul2(k, g.invs);
+                const F2 hs = mul2(h, inv), ks = mul2(k, inv);
                 const F2 tlo = fma2(hs, Dlx, mul2(ks, Dly));
                 const F2 tmd = fma2(hs, Dmx, mul2(ks, Dmy));
                 const F2 thi = fma2(hs, Dhx, mul2(ks, Dhy));
