@@ -112,9 +112,10 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
     __sincosf(d2.x, &s2a, &c2a);
     __sincosf(d2.y, &s2b, &c2b);
     const bool m1a = d1.x < TG, m1b = d1.y < TG, m2a = d2.x < TG, m2b = d2.y < TG;
-    // reciprocals on the MUFU pipe (the FP32 pipe is the busier one); 1/d only used for d >= TG
-    const F2 inv1 = mk(rcpa(fmaxf(d1.x, TG)), rcpa(fmaxf(d1.y, TG)));
-    const F2 inv2 = mk(rcpa(fmaxf(d2.x, TG)), rcpa(fmaxf(d2.y, TG)));
+    // reciprocals on the MUFU pipe (the FP32 pipe is the busier one); 1/d is only used for
+    // d >= TG, so the inf / NaN of a zero gap never leaves the unselected lane value
+    const F2 inv1 = mk(rcpa(d1.x), rcpa(d1.y));
+    const F2 inv2 = mk(rcpa(d2.x), rcpa(d2.y));
     g.invs = mk(rcpa(s.x), rcpa(s.y));  // inf when s = 0; such lanes take the series below
     const F2 dm = mk(fminf(d1.x, d2.x), fminf(d1.y, d2.y));
     const F2 tm = mul2(dm, dm);
@@ -353,7 +354,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
             F2 part[NACC];
             #pragma unroll
             for (int k = 0; k < NACC; ++k) part[k] = mk(0.f, 0.f);
-            #pragma unroll 1
+            #pragma unroll 2
             for (int j = 0; j < PAIRS; ++j) {
             const FreqPairF32& R = tile[j];
             const uint32_t PA = (uint32_t)R.nA[0] * T.U[0] + (uint32_t)R.nA[1] * T.U[1] + (uint32_t)R.nA[2] * T.U[2];
