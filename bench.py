@@ -453,7 +453,7 @@ def run_ours(args):
 
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels from
     # one ncu capture of this command on the 128^3 workload; other workloads were not captured
-    measured_traffic = {}  # the kernels changed after the last capture
+    measured_traffic = {("c2", "k_adj_f32"): 34960896 + 3072, ("c2", "k_fwd_f32"): 4813568 + 0}
 
     # roofline of the dominant kernel (event-timed inside the library on this stream)
     dom = max(("fwd", "adj"), key=lambda s: stages[s][0])
@@ -472,7 +472,7 @@ def run_ours(args):
         "unit": "Tops/s",
         "frac": achieved / peak,
         "traffic": measured_traffic.get((args.workload, kern[dom])),
-        "traffic_unit": "bytes per launch (ncu, profiles/dram_c2_cell_128cube.md)",
+        "traffic_unit": "bytes per launch (ncu, profiles/k_adj_f32_k_fwd_f32_c2_128cube.md)",
         "ops_per_term": OPS_PER_TERM[dom],
         "mufu_per_term": MUFU_PER_TERM[dom],
         "terms_per_launch": terms_launch,
