@@ -291,12 +291,12 @@ def _stats(lat, span, n):
             "span_s": span}
 
 
-def _served_run(jobs, arrivals, dev):
+def _served_run(jobs, arrivals, dev, **server_kw):
     import threading
 
     from paper_2303_10440_b300.serve import FitServer
 
-    srv = FitServer(device=dev.index or 0, max_jobs=32)
+    srv = FitServer(device=dev.index or 0, max_jobs=32, **server_kw)
     ids = [None] * len(jobs)
     t0 = srv.clock()
 
@@ -639,10 +639,14 @@ def run_serve_mode(args):
     for name, arr in rates.items():
         served = _served_run(jobs, arr, dev)
         served["terms_per_s"] = total_terms / served["span_s"]
+        # least-remaining-work scheduling within a per-iteration term budget (about 10 ms of work)
+        shortest = _served_run(jobs, arr, dev, policy="shortest", batch_terms=3e9)
+        shortest["terms_per_s"] = total_terms / shortest["span_s"]
         lat, span = _queue_latencies(arr, durs)
         lat64, span64 = _queue_latencies(arr, fp64_durs)
         out["results"][name] = {
             "served_fp32": served,
+            "served_fp32_shortest_first": shortest,
             "sequential_fp32": dict(_stats(lat, span, len(jobs)), terms_per_s=total_terms / span),
             "plain_fp64_from_measured_rate": dict(_stats(lat64, span64, len(jobs)), terms_per_s=fp64),
         }

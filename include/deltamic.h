@@ -304,13 +304,19 @@ dm_status dm_fit_staggered(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_ps
  * iteration and queued jobs join at the start of the next. */
 typedef struct dm_server dm_server;
 
+#define DM_SCHED_FIFO 0     /* admit in arrival order; every admitted job advances every iteration */
+#define DM_SCHED_SHORTEST 1 /* admit and advance the jobs with the least remaining work first */
+
 typedef struct {
     int32_t device;        /* CUDA device ordinal */
-    int32_t max_jobs;      /* jobs advanced concurrently (batch slots), >= 1 */
+    int32_t max_jobs;      /* jobs resident on the device at once (batch slots), >= 1 */
     size_t memory_bytes;   /* device arena for job state (0: half of the free device memory) */
     int32_t chunk_tiles;   /* most adjoint frequency tiles (256 frequencies) per work unit (0: 1024); each
                               job uses fewer so that it alone yields ~8 units per SM */
-    int32_t reserved;
+    int32_t policy;        /* DM_SCHED_FIFO or DM_SCHED_SHORTEST */
+    double batch_terms;    /* DM_SCHED_SHORTEST: most triangle-frequency terms per step that one iteration
+                              takes on (jobs in policy order; the first always runs); <= 0: no limit */
+    double max_wait_s;     /* a resident job that has not advanced for this long goes first (<= 0: never) */
 } dm_server_options;
 
 typedef struct {

@@ -93,7 +93,10 @@ class dm_stagger_stats(ctypes.Structure):
 
 class dm_server_options(ctypes.Structure):
     _fields_ = [("device", c_i32), ("max_jobs", c_i32), ("memory_bytes", ctypes.c_size_t), ("chunk_tiles", c_i32),
-                ("reserved", c_i32)]
+                ("policy", c_i32), ("batch_terms", c_f64), ("max_wait_s", c_f64)]
+
+
+POLICIES = {"fifo": 0, "shortest": 1}
 
 
 class dm_job(ctypes.Structure):

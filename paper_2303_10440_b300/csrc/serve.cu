@@ -93,6 +93,8 @@ struct SJob {
     double lambda = 50.0;
     int state = DM_JOB_QUEUED;
     int steps_done = 0;
+    double terms_step = 0;  // triangle-frequency terms of one step (triangles x half-spectrum size)
+    double t_last = 0;      // when the job last advanced (or was admitted)
     double t_submit = 0, t_start = 0, t_end = 0, last_loss = NAN;
     // device state
     size_t off = 0, bytes = 0;
@@ -151,6 +153,9 @@ struct dm_server {
     cudaStream_t st = nullptr;
     DeviceArena arena;
     int device = 0, max_jobs = 1, chunk_tiles = 32;
+    int policy = DM_SCHED_FIFO;
+    double batch_terms = 0, max_wait_s = 0;
+    std::vector<SJob*> run;  // the resident jobs advanced by the current iteration
     std::mutex mu;
     std::condition_variable cv;
     std::deque<SJob*> pending;
@@ -265,14 +270,14 @@ bool setup_job(dm_server* S, SJob* J) {
 }
 
 bool rebuild_units(dm_server* S) {
-    const size_t nj = S->active.size();
+    const size_t nj = S->run.size();
     S->fj.resize(nj);
     S->aj.resize(nj);
     S->uf.clear();
     S->ua.clear();
     std::vector<int> order(nj);
     for (size_t j = 0; j < nj; ++j) {
-        SJob* J = S->active[j];
+        SJob* J = S->run[j];
         const Sizes& z = J->z;
         const Bufs& b = J->b;
         const Geom G = make_geom(&J->grid);
@@ -305,13 +310,13 @@ bool rebuild_units(dm_server* S) {
     }
     // largest triangle counts first: their forward units cost the most
     std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return S->active[x]->z.n_t > S->active[y]->z.n_t; });
+                     [&](int x, int y) { return S->run[x]->z.n_t > S->run[y]->z.n_t; });
     for (int j : order) {
-        const int64_t nb = (S->active[j]->z.nH + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
+        const int64_t nb = (S->run[j]->z.nH + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
         for (int64_t k = 0; k < nb; ++k) S->uf.push_back({j, (int)k, 0, 0});
     }
     for (int j : order) {
-        const Sizes& z = S->active[j]->z;
+        const Sizes& z = S->run[j]->z;
         const int64_t tb = z.n_t_pad / ADJ_THREADS;
         for (int c = 0; c < z.n_chunks; ++c)
             for (int64_t t = 0; t < tb; ++t) S->ua.push_back({j, (int)t, c, 0});
@@ -320,27 +325,30 @@ bool rebuild_units(dm_server* S) {
               grow((void**)&S->d_aj, &S->cap_aj, nj, sizeof(BatchAdjJob)) &&
               grow((void**)&S->d_uf, &S->cap_uf, S->uf.size(), sizeof(BatchUnit)) &&
               grow((void**)&S->d_ua, &S->cap_ua, S->ua.size(), sizeof(BatchUnit));
+    // the tables change only with the set of jobs advanced, so they are uploaded here (stream-ordered
+    // after the previous iteration's batched launches) and not every iteration
+    cudaStream_t st = S->st;
+    ok = ok && cudaMemcpyAsync(S->d_fj, S->fj.data(), nj * sizeof(BatchFwdJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(S->d_aj, S->aj.data(), nj * sizeof(BatchAdjJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(S->d_uf, S->uf.data(), S->uf.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
+                   cudaSuccess;
+    ok = ok && cudaMemcpyAsync(S->d_ua, S->ua.data(), S->ua.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
+                   cudaSuccess;
     S->dirty = !ok;
     return ok;
 }
 
-// Enqueue one Adam step of every active job. Each job's own stage kernels run on its stream;
+// Enqueue one Adam step of every job in S->run. Each job's own stage kernels run on its stream;
 // the two batched launches run on the server stream after every job's preceding stage (events).
 // Synchronises only when `sync` is set; returns false on a device fault seen at a sync.
 bool iterate(dm_server* S, bool sync) {
     dm_ctx* ctx = S->ctx;
     cudaStream_t st = S->st;
     if (S->dirty && !rebuild_units(S)) return false;
-    const size_t nj = S->active.size();
+    const size_t nj = S->run.size();
     bool ok = true;
-    ok &= cudaMemcpyAsync(S->d_fj, S->fj.data(), nj * sizeof(BatchFwdJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
-    ok &= cudaMemcpyAsync(S->d_aj, S->aj.data(), nj * sizeof(BatchAdjJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
-    ok &= cudaMemcpyAsync(S->d_uf, S->uf.data(), S->uf.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
-          cudaSuccess;
-    ok &= cudaMemcpyAsync(S->d_ua, S->ua.data(), S->ua.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
-          cudaSuccess;
     // triangle records, normalisers, bands
-    for (SJob* J : S->active) {
+    for (SJob* J : S->run) {
         cudaStream_t js = J->stream;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
@@ -362,7 +370,7 @@ bool iterate(dm_server* S, bool sync) {
     ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
     g_launches += 1;
     // image, loss, adjoint records
-    for (SJob* J : S->active) {
+    for (SJob* J : S->run) {
         cudaStream_t js = J->stream;
         ok &= cudaStreamWaitEvent(js, S->ev_fwd, 0) == cudaSuccess;
         const Geom G = make_geom(&J->grid);
@@ -401,7 +409,7 @@ bool iterate(dm_server* S, bool sync) {
     g_launches += 1;
     // per-vertex gradients and Adam
     for (size_t j = 0; j < nj; ++j) {
-        SJob* J = S->active[j];
+        SJob* J = S->run[j];
         cudaStream_t js = J->stream;
         ok &= cudaStreamWaitEvent(js, S->ev_adj, 0) == cudaSuccess;
         const Geom G = make_geom(&J->grid);
@@ -440,17 +448,17 @@ bool iterate(dm_server* S, bool sync) {
         ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
         ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
     }
-    for (size_t j = 0; j < nj; ++j) S->active[j]->steps_done += 1;
+    for (size_t j = 0; j < nj; ++j) S->run[j]->steps_done += 1;
     if (sync) {
         ok &= cudaStreamSynchronize(st) == cudaSuccess;
-        for (SJob* J : S->active) ok &= cudaStreamSynchronize(J->stream) == cudaSuccess;
+        for (SJob* J : S->run) ok &= cudaStreamSynchronize(J->stream) == cudaSuccess;
         int h = 0;
         ok &= cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
         if (h) {
             cudaMemset(ctx->d_err, 0, sizeof(int));
             ok = false;
         }
-        for (size_t j = 0; j < nj; ++j) S->active[j]->last_loss = S->h_loss[j];
+        for (size_t j = 0; j < nj; ++j) S->run[j]->last_loss = S->h_loss[j];
     }
     if (!ok) cudaGetLastError();
     return ok;
@@ -477,44 +485,93 @@ void finish_job(dm_server* S, SJob* J, int state) {
     if (state == DM_JOB_DONE) S->stats.jobs_done += 1;
 }
 
+// Remaining work of a job in triangle-frequency terms.
+double remaining(const SJob* J) { return (double)(J->fit.steps - J->steps_done) * J->terms_step; }
+
+// The resident jobs an iteration advances: all of them (FIFO), or (SHORTEST) jobs idle for longer
+// than max_wait_s, then the least remaining work first, while the iteration's terms stay within
+// batch_terms (the first job always runs).
+std::vector<SJob*> select_run(dm_server* S) {
+    if (S->policy != DM_SCHED_SHORTEST) return S->active;
+    std::vector<SJob*> c = S->active;
+    const double now = S->now();
+    const auto aged = [&](const SJob* J) { return S->max_wait_s > 0 && now - J->t_last > S->max_wait_s; };
+    std::stable_sort(c.begin(), c.end(), [&](const SJob* x, const SJob* y) {
+        const bool ax = aged(x), ay = aged(y);
+        if (ax != ay) return ax;
+        return remaining(x) < remaining(y);
+    });
+    std::vector<SJob*> run;
+    double terms = 0;
+    for (SJob* J : c) {
+        if (!run.empty() && S->batch_terms > 0 && terms + J->terms_step > S->batch_terms) continue;
+        run.push_back(J);
+        terms += J->terms_step;
+    }
+    return run;
+}
+
 void engine_main(dm_server* S) {
     cudaSetDevice(S->device);
     while (true) {
-        // admission (FIFO; a job that does not fit yet blocks the ones behind it)
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
             if (S->stop) break;
         }
+        // admission: FIFO takes the head of the queue (a job that does not fit yet blocks the ones
+        // behind it); SHORTEST takes the queued job with the least work, a long-waiting one first
         while ((int)S->active.size() < S->max_jobs) {
             SJob* J = nullptr;
+            size_t pos = 0;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 if (S->pending.empty()) break;
-                J = S->pending.front();
+                if (S->policy == DM_SCHED_SHORTEST) {
+                    const double now = S->now();
+                    bool best_aged = false;
+                    for (size_t k = 0; k < S->pending.size(); ++k) {
+                        SJob* C = S->pending[k];
+                        const bool aged = S->max_wait_s > 0 && now - C->t_submit > S->max_wait_s;
+                        if (!J || (aged && !best_aged) || (aged == best_aged && remaining(C) < remaining(J))) {
+                            J = C;
+                            pos = k;
+                            best_aged = aged;
+                        }
+                    }
+                } else {
+                    J = S->pending.front();
+                }
             }
             if (!setup_job(S, J)) break;
             {
                 std::lock_guard<std::mutex> lk(S->mu);
-                S->pending.pop_front();
+                S->pending.erase(S->pending.begin() + (std::ptrdiff_t)pos);
                 J->state = DM_JOB_RUNNING;
                 J->t_start = S->now();
+                J->t_last = J->t_start;
             }
             S->active.push_back(J);
-            S->dirty = true;
         }
         if (S->active.empty()) continue;
         S->stats.peak_active = std::max<int64_t>(S->stats.peak_active, (int64_t)S->active.size());
+        std::vector<SJob*> run = select_run(S);
+        if (run != S->run) {
+            S->run.swap(run);
+            S->dirty = true;
+        }
         const double t_it = S->now();
         bool sync = ++S->since_sync >= 16;
-        for (SJob* J : S->active) sync = sync || J->steps_done + 1 >= J->fit.steps;
+        for (SJob* J : S->run) sync = sync || J->steps_done + 1 >= J->fit.steps;
         if (sync) S->since_sync = 0;
         const bool ok = iterate(S, sync);
+        const double t_done = S->now();
+        for (SJob* J : S->run) J->t_last = t_done;
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->stats.iterations += 1;
-            S->stats.job_steps += (int64_t)S->active.size();
-            S->stats.busy_s += S->now() - t_it;
+            S->stats.job_steps += (int64_t)S->run.size();
+            S->stats.busy_s += t_done - t_it;
         }
         // retire
         std::vector<SJob*> keep;
@@ -526,7 +583,10 @@ void engine_main(dm_server* S) {
             else
                 keep.push_back(J);
         }
-        if (keep.size() != S->active.size()) S->dirty = true;
+        if (keep.size() != S->active.size()) {
+            S->dirty = true;
+            S->run.clear();
+        }
         S->active.swap(keep);
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -538,6 +598,7 @@ void engine_main(dm_server* S) {
     // shutdown: release whatever is still admitted
     for (SJob* J : S->active) finish_job(S, J, DM_JOB_FAILED);
     S->active.clear();
+    S->run.clear();
     S->cv.notify_all();
 }
 
@@ -566,6 +627,7 @@ extern "C" {
 
 dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     if (!out || !opt || opt->max_jobs < 1) return DM_ERR_ARG;
+    if (opt->policy != DM_SCHED_FIFO && opt->policy != DM_SCHED_SHORTEST) return DM_ERR_ARG;
     *out = nullptr;
     dm_options o{DM_FP32_MIXED, opt->device, 1, 0};
     dm_ctx* ctx = nullptr;
@@ -576,6 +638,9 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     S->device = opt->device;
     S->max_jobs = opt->max_jobs;
     S->chunk_tiles = opt->chunk_tiles > 0 ? opt->chunk_tiles : 1024;
+    S->policy = opt->policy;
+    S->batch_terms = opt->batch_terms;
+    S->max_wait_s = opt->max_wait_s;
     S->t0 = std::chrono::steady_clock::now();
     memset(&S->stats, 0, sizeof(S->stats));
     DeviceGuard dg(opt->device);
@@ -622,6 +687,7 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     J->fit = job->fit;
     J->label = job->label;
     J->optimizer = job->optimizer;
+    J->terms_step = (double)job->n_t * (double)job->grid.n[0] * job->grid.n[1] * (job->grid.n[2] / 2 + 1);
     J->lambda = job->lambda > 0 ? job->lambda : 50.0;
     // a job whose state can never fit the arena is refused now rather than queued forever
     Sizes z = make_sizes(S->ctx, &job->grid, job->n_v, job->n_t, job->psf.band_tau > 0, job->label);

@@ -196,3 +196,30 @@ def test_large_steps_job_is_the_same_alone_and_among_adam_jobs(setup):
     s2.shutdown()
     assert np.array_equal(alone.V, mix.V)
     assert np.array_equal(alone.loss_history, mix.loss_history)
+
+
+def test_shortest_policy_runs_small_jobs_first_with_unchanged_results(setup):
+    """DM_SCHED_SHORTEST: resident jobs with the least remaining work advance first, within a per-iteration
+    term budget; a big job submitted first waits for the small ones, and every result is the same as alone."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    big = dict(jobs[0], steps=30)          # 64^3, 1280 triangles: 1.7e8 terms per step
+    small = dict(jobs[1], steps=STEPS)     # 32^3, 320 triangles: 5.6e6 terms per step
+    s0 = FitServer(max_jobs=2)
+    i0 = s0.submit(**small)
+    assert s0.wait(i0, timeout=300)
+    alone = s0.result(i0)
+    s0.shutdown()
+    s = FitServer(max_jobs=8, policy="shortest", batch_terms=1e8)
+    a = s.submit(**big)
+    ids = [s.submit(**small) for _ in range(3)]
+    for i in [a] + ids:
+        assert s.wait(i, timeout=300)
+    rb = s.result(a)
+    rs = [s.result(i) for i in ids]
+    s.shutdown()
+    assert all(r.t_end < rb.t_end for r in rs)
+    for r in rs:
+        assert np.array_equal(r.V, alone.V) and np.array_equal(r.loss_history, alone.loss_history)
+    assert len(rb.loss_history) == 30 and rb.loss_history[-1] < rb.loss_history[0]
