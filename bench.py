@@ -53,11 +53,12 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger", "robust"], default="step",
+    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger", "robust", "fft"], default="step",
                    help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
                    "serve-c5: Poisson stream of serving requests; stagger: the staggered shape/PSF fit "
                    "(large-steps shape steps on the narrow band, PSF steps on the whole spectrum); robust: "
-                   "sweeps of initial scale, initial shift and image noise through the fit server")
+                   "sweeps of initial scale, initial shift and image noise through the fit server; fft: the inverse "
+                   "and forward real 3D transforms alone, GB/s against the measured HBM copy bandwidth")
     p.add_argument("--rounds", type=int, default=4, help="staggered rounds in the stagger mode")
     p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 10)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
@@ -794,8 +795,61 @@ def run_robust_mode(args):
     print(json.dumps(out), flush=True)
 
 
+def run_fft_mode(args):
+    """The half-spectrum inverse (C2R) and forward (R2C) 3D transforms through dm_c2r / dm_r2c on device
+    buffers, CUDA-event timed (L2 flushed before each call). Bytes per transform: each of the three axis
+    passes reads and writes the array once (two complex passes over the half spectrum, one real/complex
+    z pass), i.e. 2 * (2 |H| * 8 B) + (|H| * 8 B + N * 4 B); dm_c2r first copies its (const) input
+    spectrum into its workspace, another 2 |H| * 8 B (the fit pipeline scatters straight into it)."""
+    import torch
+
+    from paper_2303_10440_b300 import Grid, Renderer
+
+    dev = torch.device("cuda", 0)
+    r = Renderer("fp32")
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for n in (128, 256, 512):
+        grid = Grid(n=(n, n, n), h=(0.5, 0.5, 1.0))
+        nH = n * n * (n // 2 + 1)
+        spec = torch.randn(n, n, n // 2 + 1, dtype=torch.complex64, device=dev)
+        img = torch.randn(n, n, n, dtype=torch.float32, device=dev)
+        passes = 2 * (2 * nH * 8) + (nH * 8 + n**3 * 4)
+        res = {}
+        for name, fn, nbytes in (("c2r", lambda: r.c2r(grid, spec), passes + 2 * nH * 8),
+                                 ("r2c", lambda: r.r2c(grid, img), passes)):
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(10):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            ms = float(np.median(ts))
+            res[name] = {"ms": ms, "bytes": nbytes, "GB_per_s": nbytes / (ms * 1e-3) / 1e9,
+                         "frac_of_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm}
+        rows.append({"grid": [n, n, n], **res})
+        del spec, img
+    print(json.dumps({"metric": "3D real FFT (C2R / R2C) throughput", "mode": "fft", "hbm_peak_gbs": hbm,
+                      "hbm_peak_source": "MEASURED_PEAKS.json" if "hbm_gbs" in peaks else "fallback", "rows": rows}),
+          flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "fft":
+        run_fft_mode(args)
+        return
     if args.mode == "robust":
         run_robust_mode(args)
         return

@@ -24,6 +24,19 @@ __device__ __forceinline__ Cx<R> twiddle(const Cx<R>* tw, int idx, int dir) {
     return dir < 0 ? w : Cx<R>{w.x, -w.y};
 }
 
+// 4-point DFT in place: y[m] = sum_q v[q] exp(dir 2 pi i q m / 4).
+template <class R>
+__device__ __forceinline__ void dft4(Cx<R>* v, int dir) {
+    const Cx<R> s02 = {v[0].x + v[2].x, v[0].y + v[2].y}, d02 = {v[0].x - v[2].x, v[0].y - v[2].y};
+    const Cx<R> s13 = {v[1].x + v[3].x, v[1].y + v[3].y}, d13 = {v[1].x - v[3].x, v[1].y - v[3].y};
+    // w = exp(dir i pi/2) = dir * i ;  w * d13 = dir * (-d13.y, d13.x)
+    const Cx<R> wd = {-(R)dir * d13.y, (R)dir * d13.x};
+    v[0] = {s02.x + s13.x, s02.y + s13.y};
+    v[1] = {d02.x + wd.x, d02.y + wd.y};
+    v[2] = {s02.x - s13.x, s02.y - s13.y};
+    v[3] = {d02.x - wd.x, d02.y - wd.y};
+}
+
 // y[m] = sum_q v[q] exp(dir 2 pi i q m / r), in place.
 template <class R>
 __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
@@ -32,14 +45,7 @@ __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
         v[0] = {a.x + b.x, a.y + b.y};
         v[1] = {a.x - b.x, a.y - b.y};
     } else if (r == 4) {
-        const Cx<R> s02 = {v[0].x + v[2].x, v[0].y + v[2].y}, d02 = {v[0].x - v[2].x, v[0].y - v[2].y};
-        const Cx<R> s13 = {v[1].x + v[3].x, v[1].y + v[3].y}, d13 = {v[1].x - v[3].x, v[1].y - v[3].y};
-        // w = exp(dir i pi/2) = dir * i ;  w * d13 = dir * (-d13.y, d13.x)
-        const Cx<R> wd = {-(R)dir * d13.y, (R)dir * d13.x};
-        v[0] = {s02.x + s13.x, s02.y + s13.y};
-        v[1] = {d02.x + wd.x, d02.y + wd.y};
-        v[2] = {s02.x - s13.x, s02.y - s13.y};
-        v[3] = {d02.x - wd.x, d02.y - wd.y};
+        dft4(v, dir);
     } else if (r == 3) {
         const R h = (R)0.86602540378443864676 * (R)dir;  // dir * sqrt(3)/2
         const Cx<R> t = {v[1].x + v[2].x, v[1].y + v[2].y}, d = {v[1].x - v[2].x, v[1].y - v[2].y};
@@ -48,6 +54,24 @@ __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
         v[0] = {v[0].x + t.x, v[0].y + t.y};
         v[1] = {m.x + id.x, m.y + id.y};
         v[2] = {m.x - id.x, m.y - id.y};
+    } else if (r == 8) {
+        // two 4-point DFTs on the even and odd inputs, combined with the powers of exp(dir 2 pi i / 8)
+        Cx<R> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+        dft4(e, dir);
+        dft4(o, dir);
+        const R c = (R)0.70710678118654752440;
+        const R d = (R)dir;
+        const Cx<R> t1 = {c * (o[1].x - d * o[1].y), c * (o[1].y + d * o[1].x)};   // (1 + dir i)/sqrt2 o1
+        const Cx<R> t2 = {-d * o[2].y, d * o[2].x};                                  // dir i o2
+        const Cx<R> t3 = {c * (-o[3].x - d * o[3].y), c * (-o[3].y + d * o[3].x)};  // (-1 + dir i)/sqrt2 o3
+        v[0] = {e[0].x + o[0].x, e[0].y + o[0].y};
+        v[4] = {e[0].x - o[0].x, e[0].y - o[0].y};
+        v[1] = {e[1].x + t1.x, e[1].y + t1.y};
+        v[5] = {e[1].x - t1.x, e[1].y - t1.y};
+        v[2] = {e[2].x + t2.x, e[2].y + t2.y};
+        v[6] = {e[2].x - t2.x, e[2].y - t2.y};
+        v[3] = {e[3].x + t3.x, e[3].y + t3.y};
+        v[7] = {e[3].x - t3.x, e[3].y - t3.y};
     } else {  // r == 5: direct 5-point DFT
         const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
         const R s1 = (R)0.95105651629515357212 * (R)dir, s2 = (R)0.58778525229247312917 * (R)dir;
@@ -69,6 +93,9 @@ __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
         for (int mm = 0; mm < 5; ++mm) v[mm] = y[mm];
     }
 }
+
+// Lines per block: a batch of about 2048 elements, at most 16 lines (a power of two for power-of-two N).
+__host__ __device__ constexpr int lines_per_block(int N) { return 2048 / N > 16 ? 16 : (2048 / N < 1 ? 1 : 2048 / N); }
 
 // Stockham FFT of `nl` lines of length N stored as a[k * LS + line]; returns the buffer holding the result.
 template <class R>
@@ -107,20 +134,54 @@ __device__ Cx<R>* fft_lines(Cx<R>* a, Cx<R>* b, const FFTAxis ax, int LS, int nl
     return a;
 }
 
-__host__ __device__ inline int lines_per_block(int N) {
-    int nl = 4096 / N;
-    if (nl > 16) nl = 16;
-    if (nl < 1) nl = 1;
-    return nl;
+
+// The same Stockham FFT for a power-of-two length known at compile time: radix-8 stages, then one
+// radix-4 or radix-2 stage for the rest, every index computation on constants (no run-time division).
+template <class R, int N, int NL, int NS>
+__device__ __forceinline__ Cx<R>* stockham_p2(Cx<R>* a, Cx<R>* b, const Cx<R>* tw, int dir) {
+    if constexpr (NS >= N) {
+        return a;
+    } else {
+        constexpr int r = ((N / NS) % 8 == 0) ? 8 : (((N / NS) % 4 == 0) ? 4 : 2);
+        constexpr int nb = N / r;
+        constexpr int tstride = N / (NS * r);
+        constexpr int LS = NL + 1;
+        for (int w = threadIdx.x; w < nb * NL; w += FFT_THREADS) {
+            const int line = w % NL, j = w / NL;
+            const int k = j % NS;
+            Cx<R> v[8];
+#pragma unroll
+            for (int q = 0; q < r; ++q) v[q] = a[(j + q * nb) * LS + line];
+            if constexpr (NS > 1) {
+#pragma unroll
+                for (int q = 1; q < r; ++q) v[q] = cmul(v[q], twiddle(tw, q * k * tstride, dir));
+            }
+            small_dft(v, r, dir);
+            const int base = (j / NS) * NS * r + k;
+#pragma unroll
+            for (int q = 0; q < r; ++q) b[(base + q * NS) * LS + line] = v[q];
+        }
+        __syncthreads();
+        return stockham_p2<R, N, NL, NS * r>(b, a, tw, dir);
+    }
+}
+
+// Line transform: the compile-time power-of-two path when NC != 0, else the mixed-radix one.
+template <class R, int NC>
+__device__ __forceinline__ Cx<R>* transform_lines(Cx<R>* a, Cx<R>* b, const FFTAxis& ax, int LS, int nl, int dir) {
+    if constexpr (NC != 0)
+        return stockham_p2<R, NC, lines_per_block(NC), 1>(a, b, (const Cx<R>*)ax.tw, dir);
+    else
+        return fft_lines<R>(a, b, ax, LS, nl, dir);
 }
 
 // Complex transform of all lines along an axis with element stride `inner`:
 // element (o, k, c) at o*N*inner + k*inner + c, lines indexed by (o, c).
-template <class R>
+template <class R, int NC>
 __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const FFTAxis ax, int64_t inner,
                                                              int dir) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = ax.N;
+    const int N = NC ? NC : ax.N;
     const int nl = lines_per_block(N);
     const int LS = nl + 1;
     Cx<R>* a = (Cx<R>*)smem_raw;
@@ -135,7 +196,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const 
         a[k * LS + c] = c < ncols ? base[(int64_t)k * inner + c] : Cx<R>{0, 0};
     }
     __syncthreads();
-    Cx<R>* res = fft_lines<R>(a, b, ax, LS, nl, dir);
+    Cx<R>* res = transform_lines<R, NC>(a, b, ax, LS, nl, dir);
     for (int i = threadIdx.x; i < N * nl; i += blockDim.x) {
         const int c = i % nl, k = i / nl;
         if (c < ncols) base[(int64_t)k * inner + c] = res[k * LS + c];
@@ -143,11 +204,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const 
 }
 
 // Inverse z pass: lines of Nzh complex (contiguous) -> Nz reals (contiguous).
-template <class R>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R* out, const FFTAxis ax, int Nzh,
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R* out, const FFTAxis ax, int Nzh_,
                                                            int64_t nlines) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = ax.N;
+    const int N = NC ? NC : ax.N;
+    const int Nzh = NC ? NC / 2 + 1 : Nzh_;
     const int nl = lines_per_block(N);
     const int LS = nl + 1;
     Cx<R>* a = (Cx<R>*)smem_raw;
@@ -163,7 +225,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R*
         if (k > 0 && 2 * k < N) a[(N - k) * LS + c] = Cx<R>{v.x, -v.y};
     }
     __syncthreads();
-    Cx<R>* res = fft_lines<R>(a, b, ax, LS, nl, +1);
+    Cx<R>* res = transform_lines<R, NC>(a, b, ax, LS, nl, +1);
     for (int i = threadIdx.x; i < N * nl; i += blockDim.x) {
         const int k = i % N, c = i / N;
         if (c < nv) out[(l0 + c) * N + k] = res[k * LS + c].x;
@@ -171,11 +233,12 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R*
 }
 
 // Forward z pass: lines of Nz reals -> first Nzh complex outputs.
-template <class R>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* spec, const FFTAxis ax, int Nzh,
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* spec, const FFTAxis ax, int Nzh_,
                                                            int64_t nlines) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = ax.N;
+    const int N = NC ? NC : ax.N;
+    const int Nzh = NC ? NC / 2 + 1 : Nzh_;
     const int nl = lines_per_block(N);
     const int LS = nl + 1;
     Cx<R>* a = (Cx<R>*)smem_raw;
@@ -187,7 +250,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* s
         a[k * LS + c] = Cx<R>{c < nv ? in[(l0 + c) * N + k] : (R)0, (R)0};
     }
     __syncthreads();
-    Cx<R>* res = fft_lines<R>(a, b, ax, LS, nl, -1);
+    Cx<R>* res = transform_lines<R, NC>(a, b, ax, LS, nl, -1);
     for (int i = threadIdx.x; i < Nzh * nl; i += blockDim.x) {
         const int k = i % Nzh, c = i / Nzh;
         if (c < nv) spec[(l0 + c) * Nzh + k] = res[k * LS + c];
@@ -219,6 +282,48 @@ size_t fft_smem_bytes(int N, int elem_bytes) {
     return (size_t)2 * N * (nl + 1) * elem_bytes;
 }
 
+// One pass over every line of an axis, with the kernel instantiated for the line length when it is a
+// power of two up to 1024 (NC = N) and the mixed-radix kernel otherwise (NC = 0).
+enum PassKind { PASS_STRIDED, PASS_Z_C2R, PASS_Z_R2C };
+
+template <class R, int NC>
+cudaError_t run_pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, int64_t inner, int64_t outer,
+                     int Nzh, int dir, cudaStream_t st) {
+    const int N = ax.N;
+    const int nl = lines_per_block(N);
+    const size_t sm = fft_smem_bytes(N, sizeof(Cx<R>));
+    cudaError_t e;
+    if (kind == PASS_STRIDED) {
+        if ((e = set_smem<R>((const void*)k_fft_strided<R, NC>, sm)) != cudaSuccess) return e;
+        const int64_t blocks = outer * ((inner + nl - 1) / nl);
+        k_fft_strided<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((Cx<R>*)dst, ax, inner, dir);
+    } else if (kind == PASS_Z_C2R) {
+        if ((e = set_smem<R>((const void*)k_fft_z_c2r<R, NC>, sm)) != cudaSuccess) return e;
+        const int64_t blocks = (outer + nl - 1) / nl;
+        k_fft_z_c2r<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const Cx<R>*)src, (R*)dst, ax, Nzh, outer);
+    } else {
+        if ((e = set_smem<R>((const void*)k_fft_z_r2c<R, NC>, sm)) != cudaSuccess) return e;
+        const int64_t blocks = (outer + nl - 1) / nl;
+        k_fft_z_r2c<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const R*)src, (Cx<R>*)dst, ax, Nzh, outer);
+    }
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, int64_t inner, int64_t outer, int Nzh,
+                 int dir, cudaStream_t st) {
+    switch (ax.N) {
+        case 16: return run_pass<R, 16>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 32: return run_pass<R, 32>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 64: return run_pass<R, 64>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 128: return run_pass<R, 128>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 256: return run_pass<R, 256>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 512: return run_pass<R, 512>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 1024: return run_pass<R, 1024>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        default: return run_pass<R, 0>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+    }
+}
+
 template <class R>
 cudaError_t launch_c2r(const Cx<R>* spec_in, Cx<R>* work, R* out, int Nx, int Ny, int Nz, const FFTAxis* ax,
                        cudaStream_t st) {
@@ -230,54 +335,23 @@ cudaError_t launch_c2r(const Cx<R>* spec_in, Cx<R>* work, R* out, int Nx, int Ny
         if (e != cudaSuccess) return e;
     }
     // x pass (stride Ny*Nzh), y pass (stride Nzh), then the real z pass.
-    {
-        const size_t sm = fft_smem_bytes(Nx, sizeof(Cx<R>));
-        if ((e = set_smem<R>((const void*)k_fft_strided<R>, sm)) != cudaSuccess) return e;
-        const int64_t inner = (int64_t)Ny * Nzh;
-        const int64_t blocks = (inner + lines_per_block(Nx) - 1) / lines_per_block(Nx);
-        if (Nx > 1) k_fft_strided<R><<<(unsigned)blocks, FFT_THREADS, sm, st>>>(work, ax[0], inner, +1);
-    }
-    {
-        const size_t sm = fft_smem_bytes(Ny, sizeof(Cx<R>));
-        if ((e = set_smem<R>((const void*)k_fft_strided<R>, sm)) != cudaSuccess) return e;
-        const int64_t blocks = (int64_t)Nx * ((Nzh + lines_per_block(Ny) - 1) / lines_per_block(Ny));
-        if (Ny > 1) k_fft_strided<R><<<(unsigned)blocks, FFT_THREADS, sm, st>>>(work, ax[1], Nzh, +1);
-    }
-    {
-        const size_t sm = fft_smem_bytes(Nz, sizeof(Cx<R>));
-        if ((e = set_smem<R>((const void*)k_fft_z_c2r<R>, sm)) != cudaSuccess) return e;
-        const int64_t nlines = (int64_t)Nx * Ny;
-        const int64_t blocks = (nlines + lines_per_block(Nz) - 1) / lines_per_block(Nz);
-        k_fft_z_c2r<R><<<(unsigned)blocks, FFT_THREADS, sm, st>>>(work, out, ax[2], Nzh, nlines);
-    }
-    return cudaGetLastError();
+    if (Nx > 1 && (e = pass<R>(PASS_STRIDED, work, work, ax[0], (int64_t)Ny * Nzh, 1, Nzh, +1, st)) != cudaSuccess)
+        return e;
+    if (Ny > 1 && (e = pass<R>(PASS_STRIDED, work, work, ax[1], Nzh, Nx, Nzh, +1, st)) != cudaSuccess) return e;
+    return pass<R>(PASS_Z_C2R, work, out, ax[2], 0, (int64_t)Nx * Ny, Nzh, +1, st);
 }
 
 template <class R>
 cudaError_t launch_r2c(const R* in, Cx<R>* spec_out, int Nx, int Ny, int Nz, const FFTAxis* ax, cudaStream_t st) {
     const int Nzh = Nz / 2 + 1;
     cudaError_t e;
-    {
-        const size_t sm = fft_smem_bytes(Nz, sizeof(Cx<R>));
-        if ((e = set_smem<R>((const void*)k_fft_z_r2c<R>, sm)) != cudaSuccess) return e;
-        const int64_t nlines = (int64_t)Nx * Ny;
-        const int64_t blocks = (nlines + lines_per_block(Nz) - 1) / lines_per_block(Nz);
-        k_fft_z_r2c<R><<<(unsigned)blocks, FFT_THREADS, sm, st>>>(in, spec_out, ax[2], Nzh, nlines);
-    }
-    {
-        const size_t sm = fft_smem_bytes(Ny, sizeof(Cx<R>));
-        if ((e = set_smem<R>((const void*)k_fft_strided<R>, sm)) != cudaSuccess) return e;
-        const int64_t blocks = (int64_t)Nx * ((Nzh + lines_per_block(Ny) - 1) / lines_per_block(Ny));
-        if (Ny > 1) k_fft_strided<R><<<(unsigned)blocks, FFT_THREADS, sm, st>>>(spec_out, ax[1], Nzh, -1);
-    }
-    {
-        const size_t sm = fft_smem_bytes(Nx, sizeof(Cx<R>));
-        if ((e = set_smem<R>((const void*)k_fft_strided<R>, sm)) != cudaSuccess) return e;
-        const int64_t inner = (int64_t)Ny * Nzh;
-        const int64_t blocks = (inner + lines_per_block(Nx) - 1) / lines_per_block(Nx);
-        if (Nx > 1) k_fft_strided<R><<<(unsigned)blocks, FFT_THREADS, sm, st>>>(spec_out, ax[0], inner, -1);
-    }
-    return cudaGetLastError();
+    if ((e = pass<R>(PASS_Z_R2C, in, spec_out, ax[2], 0, (int64_t)Nx * Ny, Nzh, -1, st)) != cudaSuccess) return e;
+    if (Ny > 1 && (e = pass<R>(PASS_STRIDED, spec_out, spec_out, ax[1], Nzh, Nx, Nzh, -1, st)) != cudaSuccess)
+        return e;
+    if (Nx > 1 && (e = pass<R>(PASS_STRIDED, spec_out, spec_out, ax[0], (int64_t)Ny * Nzh, 1, Nzh, -1, st)) !=
+                      cudaSuccess)
+        return e;
+    return cudaSuccess;
 }
 
 template cudaError_t launch_c2r<float>(const Cx<float>*, Cx<float>*, float*, int, int, int, const FFTAxis*,

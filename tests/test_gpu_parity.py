@@ -301,3 +301,25 @@ def test_tissue_foam_matches_oracle(prec, r64, r32):
     assert abs(L - L0) <= tl * abs(L0)
     assert rel(dV.cpu().numpy(), dV0) < tg
     assert rel(dpsf.numpy(), dpsf0) < tg
+
+
+@pytest.mark.parametrize("scale", [0.02, 0.15, 0.6])
+@pytest.mark.parametrize("label", ["surface", "volume"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_in_and_around_the_series_region(scale, label, prec, r64, r32):
+    """Small triangles: at scale 0.02 every term has its three phases within 0.5 (series only), at 0.15
+    and 0.6 the terms straddle the switch between the series and the closed form with Taylor gaps."""
+    V, F = synth.sh_deformed_sphere(1, 1.0, (0.0, 0.0, 0.0), lmax=2, coef_sigma=0.1, seed=4)
+    V = V * (scale * 8.0) + np.array([8.0, 7.5, 9.0])
+    fn = _freqs(3, M=256)
+    xi = oracle.wavevectors(fn, GRID)
+    rng = np.random.default_rng(10)
+    G = (rng.normal(size=len(fn)) + 1j * rng.normal(size=len(fn))) / np.sqrt(len(fn))
+    Vo = V - np.asarray(GRID.origin)
+    S0 = oracle.mesh_ft(Vo, F, xi, label, c0=0.5 * GRID.L)
+    dV0 = oracle.mesh_ft_adjoint(Vo, F, xi, G, label, c0=0.5 * GRID.L)
+    r = r64 if prec == "fp64" else r32
+    S = r.meshft(_cuda(V), _cuda(F), GRID, _cuda(fn), label=label).cpu().numpy()
+    dV = r.meshft_adjoint(_cuda(V), _cuda(F), GRID, _cuda(fn), _cuda(G), label=label).cpu().numpy()
+    assert rel(S, S0) < (1e-11 if prec == "fp64" else 2e-6)
+    assert rel(dV, dV0) < (1e-10 if prec == "fp64" else 1e-4)
