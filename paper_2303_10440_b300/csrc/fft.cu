@@ -96,6 +96,9 @@ __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
 
 // Lines per block: a batch of about 2048 elements, at most 16 lines (a power of two for power-of-two N).
 __host__ __device__ constexpr int lines_per_block(int N) { return 2048 / N > 16 ? 16 : (2048 / N < 1 ? 1 : 2048 / N); }
+// Shared-memory row stride (elements) of a batch of nl lines: element k of line c sits at k * stride + c.
+// Every kernel, the Stockham stages and the shared-memory size use this one definition.
+__host__ __device__ constexpr int line_stride(int nl) { return nl + 1; }
 
 // Stockham FFT of `nl` lines of length N stored as a[k * LS + line]; returns the buffer holding the result.
 template <class R>
@@ -145,7 +148,7 @@ __device__ __forceinline__ Cx<R>* stockham_p2(Cx<R>* a, Cx<R>* b, const Cx<R>* t
         constexpr int r = ((N / NS) % 8 == 0) ? 8 : (((N / NS) % 4 == 0) ? 4 : 2);
         constexpr int nb = N / r;
         constexpr int tstride = N / (NS * r);
-        constexpr int LS = NL + 1;
+        constexpr int LS = line_stride(NL);
         for (int w = threadIdx.x; w < nb * NL; w += FFT_THREADS) {
             const int line = w % NL, j = w / NL;
             const int k = j % NS;
@@ -183,7 +186,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NC ? NC : ax.N;
     const int nl = lines_per_block(N);
-    const int LS = nl + 1;
+    const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
     Cx<R>* b = a + N * LS;
     const int64_t col_blocks = (inner + nl - 1) / nl;
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R*
     const int N = NC ? NC : ax.N;
     const int Nzh = NC ? NC / 2 + 1 : Nzh_;
     const int nl = lines_per_block(N);
-    const int LS = nl + 1;
+    const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
     Cx<R>* b = a + N * LS;
     const int64_t l0 = (int64_t)blockIdx.x * nl;
@@ -240,7 +243,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* s
     const int N = NC ? NC : ax.N;
     const int Nzh = NC ? NC / 2 + 1 : Nzh_;
     const int nl = lines_per_block(N);
-    const int LS = nl + 1;
+    const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
     Cx<R>* b = a + N * LS;
     const int64_t l0 = (int64_t)blockIdx.x * nl;
@@ -279,7 +282,7 @@ bool fft_factor(int N, FFTAxis& a) {
 
 size_t fft_smem_bytes(int N, int elem_bytes) {
     const int nl = lines_per_block(N);
-    return (size_t)2 * N * (nl + 1) * elem_bytes;
+    return (size_t)2 * N * line_stride(nl) * elem_bytes;
 }
 
 // One pass over every line of an axis, with the kernel instantiated for the line length when it is a
