@@ -18,6 +18,7 @@ Metric: forward + backward (triangle x frequency) terms per second,
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import subprocess
@@ -53,12 +54,15 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
-    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger", "robust", "fft"], default="step",
+    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger", "robust", "fft", "scaling", "mufu"],
+                   default="step",
                    help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
                    "serve-c5: Poisson stream of serving requests; stagger: the staggered shape/PSF fit "
                    "(large-steps shape steps on the narrow band, PSF steps on the whole spectrum); robust: "
                    "sweeps of initial scale, initial shift and image noise through the fit server; fft: the inverse "
-                   "and forward real 3D transforms alone, GB/s against the measured HBM copy bandwidth")
+                   "and forward real 3D transforms alone, GB/s against the measured HBM copy bandwidth; scaling: "
+                   "step time against grid size and triangle count (the paper's GPU timing figure) and a "
+                   "narrow-band case")
     p.add_argument("--rounds", type=int, default=4, help="staggered rounds in the stagger mode")
     p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 10)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
@@ -845,8 +849,100 @@ def run_fft_mode(args):
           flush=True)
 
 
+def run_scaling_mode(args):
+    """Fit-step time (forward + adjoint through dm_loss_and_grad, device buffers, CUDA events) against
+    (i) the grid side for an 80-triangle icosphere on the whole spectrum, (ii) the triangle count on
+    100^3, and (iii) a narrow-band case (128^3, h = 1, sigma = (2, 2, 5) voxels, tau = 1e-3); the FP64
+    oracle is timed on the small cases for the GPU / CPU ratio."""
+    import torch
+
+    import synth
+    from paper_2303_10440_b300 import Renderer
+
+    dev = torch.device("cuda", 0)
+    r = Renderer("fp32")
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)
+
+    def step_ms(V, F, grid, psf, reps=5):
+        Vd, Fd = torch.as_tensor(V).to(dev), torch.as_tensor(F).to(dev)
+        T = r.render(Vd * 1.01, Fd, grid, psf)
+        for _ in range(2):
+            r.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
+        ts = []
+        for _ in range(reps):
+            flush.fill_(0.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), int(r.band(grid, psf).numel())
+
+    def oracle_ms(V, F, grid, psf):
+        import oracle
+
+        T = oracle.render(V * 1.01, F, grid, psf)["image"]
+        t0 = time.perf_counter()
+        oracle.loss_and_grad(V, F, grid, psf, T, "mse")
+        return (time.perf_counter() - t0) * 1e3
+
+    out = {"metric": "fit-step time against grid size and triangle count", "mode": "scaling", "grid_sweep": [],
+           "triangle_sweep": [], "narrow_band": None}
+    V1, F1 = synth.sphere_mesh(1, 1.0, (0, 0, 0))
+    for n in (16, 32, 64, 128, 256):
+        grid = synth.Grid(n=(n, n, n), h=(1.0, 1.0, 1.0))
+        V = V1 * (0.3 * n) + np.asarray(grid.center)
+        psf = synth.Psf(sigma=(0.8, 0.8, 0.8))
+        ms, M = step_ms(V, F1, grid, psf)
+        row = {"grid": n, "triangles": len(F1), "band": M, "ms": ms, "terms_per_s": 2 * M * len(F1) / (ms * 1e-3)}
+        if n <= 32:
+            row["oracle_ms"] = oracle_ms(V, F1, grid, psf)
+            row["gpu_over_oracle"] = row["oracle_ms"] / ms
+        out["grid_sweep"].append(row)
+    grid = synth.Grid(n=(100, 100, 100), h=(1.0, 1.0, 1.0))
+    for lev in (1, 2, 3, 4, 5, 6):
+        V, F = synth.sphere_mesh(lev, 30.0, (50.0, 50.0, 50.0))
+        ms, M = step_ms(V, F, grid, synth.Psf(sigma=(0.8, 0.8, 0.8)), reps=3 if lev >= 5 else 5)
+        out["triangle_sweep"].append({"grid": 100, "triangles": len(F), "band": M, "ms": ms,
+                                      "terms_per_s": 2 * M * len(F) / (ms * 1e-3)})
+    grid = synth.Grid(n=(128, 128, 128), h=(1.0, 1.0, 1.0))
+    V, F = synth.sh_deformed_sphere(4, 30.0, (64.0, 64.0, 64.0), lmax=6, coef_sigma=1.8, seed=2)
+    psf = synth.Psf(sigma=(2.0, 2.0, 5.0), band_tau=1e-3)
+    ms, M = step_ms(V, F, grid, psf)
+    full_ms, Mf = step_ms(V, F, grid, synth.Psf(sigma=(2.0, 2.0, 5.0)))
+    out["narrow_band"] = {"grid": 128, "triangles": len(F), "sigma_voxels": [2, 2, 5], "tau": 1e-3, "band": M,
+                          "half_spectrum": Mf, "ms": ms, "ms_whole_spectrum": full_ms,
+                          "terms_per_s": 2 * M * len(F) / (ms * 1e-3)}
+    print(json.dumps(out), flush=True)
+
+
+def run_mufu_probe(args):
+    """Throughput of the MUFU sin/cos and reciprocal instructions the mesh-transform sums use, measured with
+    a kernel of independent chains (the XU roofline of the forward sum)."""
+    import torch
+
+    from paper_2303_10440_b300 import _lib
+
+    lib = _lib.load()
+    res = {}
+    for kind, name in ((0, "sincos"), (1, "rcp")):
+        ops = ctypes.c_double()
+        st = lib.dm_probe_mufu(kind, 0, ctypes.byref(ops))
+        if st != 0:
+            raise RuntimeError(f"dm_probe_mufu: {st}")
+        res[name] = ops.value
+    print(json.dumps({"metric": "MUFU throughput", "mode": "mufu", **res}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mode == "mufu":
+        run_mufu_probe(args)
+        return
+    if args.mode == "scaling":
+        run_scaling_mode(args)
+        return
     if args.mode == "fft":
         run_fft_mode(args)
         return

@@ -148,6 +148,12 @@ dm_status dm_profile_enable(dm_ctx* ctx, int32_t enable);
 /* ms, calls: arrays of DM_NUM_STAGES (either may be NULL). */
 dm_status dm_profile_read(dm_ctx* ctx, double* ms, int64_t* calls);
 
+/* Instrumentation with no counterpart in the paper: the throughput of the MUFU operations the mesh
+ * transform spends per term, kind 0 = sin/cos pairs (__sincosf), kind 1 = approximate reciprocals, in
+ * operations per second on `device` (a sin/cos pair counts 2). Runs two launches of independent
+ * dependency chains on the default stream and synchronises. */
+dm_status dm_probe_mufu(int32_t kind, int32_t device, double* ops_per_s);
+
 /* ---------------------------------------------------------------- stages */
 
 /* Narrow band (Sec. 5.1). Writes the band's indices into H (ordered) to idx_out

@@ -162,6 +162,7 @@ _SIGS = {
     "dm_server_get_stats": (c_i32, [c_p, ctypes.POINTER(dm_server_stats)]),
     "dm_server_clock": (c_f64, [c_p]),
     "dm_server_shutdown": (c_i32, [c_p]),
+    "dm_probe_mufu": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_f64)]),
     "dm_smooth_solve": (c_i32, [c_p, c_p, c_i64, c_i64, c_f64, c_p, c_p, c_f64, c_i32, c_p, c_p]),
     "dm_adam_uniform": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i64, c_f64, c_f64, c_f64, c_f64, c_i64, c_p]),
     "dm_fit_staggered": (

@@ -249,6 +249,7 @@ enum Job { JOB_RENDER = 1, JOB_LOSS = 2, JOB_ADJOINT = 4 };
 
 struct Sizes {
     bool f64;
+    int sm_count;
     int64_t nH, N, n_v, n_t, n_t_pad, M_max, M_pad;
     int n_chunks, nacc;
     bool band;  // narrow band active (tau > 0)
@@ -259,6 +260,7 @@ struct Bufs {
     double* partial;   // block partials (norm / loss / gather)
     void* tris;
     void* S;
+    void* S_part;  // FP32 forward: partial spectra of triangle splits (small bands)
     void* spec;
     void* image;
     void* resid;
@@ -287,6 +289,7 @@ size_t layout(const Sizes& z, Arena& A, Bufs& b, bool stageV, bool stageF, bool 
     b.partial = A.take<double>(nparts);
     b.tris = A.take<char>(z.n_t_pad * (z.f64 ? sizeof(TriF64) : sizeof(TriF32)));
     b.S = A.take<char>(z.M_max * 2 * R);
+    b.S_part = z.f64 ? nullptr : A.take<char>(fwd_partial_elems(z.M_max, z.sm_count) * sizeof(float2));
     b.spec = A.take<char>(z.nH * 2 * R);
     b.image = A.take<char>(z.N * R);
     b.resid = A.take<char>(z.N * R);
@@ -312,6 +315,7 @@ size_t layout(const Sizes& z, Arena& A, Bufs& b, bool stageV, bool stageF, bool 
 Sizes make_sizes(const dm_ctx* ctx, const dm_grid* g, int64_t n_v, int64_t n_t, bool band, int label) {
     Sizes z;
     z.f64 = ctx->precision == DM_FP64;
+    z.sm_count = ctx->sm_count;
     const int Nzh = g->n[2] / 2 + 1;
     z.nH = (int64_t)g->n[0] * g->n[1] * Nzh;
     z.N = (int64_t)g->n[0] * g->n[1] * g->n[2];
@@ -412,8 +416,8 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
     {
         Stage sg(ctx, DM_STAGE_FWD, st);
         if (sizeof(R) == 4)
-            LAUNCH(1, launch_fwd_f32(mode, (const TriF32*)b.tris, z.n_t_pad, fs, G, d_norm, (float2*)b.S, ctx->d_err,
-                                     st));
+            LAUNCH(2, launch_fwd_f32(mode, (const TriF32*)b.tris, z.n_t_pad, fs, G, d_norm, (float2*)b.S,
+                                     (float2*)b.S_part, z.sm_count, ctx->d_err, st));
         else
             LAUNCH(1, launch_fwd_f64(mode, (const TriF64*)b.tris, z.n_t, fs, G, d_norm, (double2*)b.S, st));
     }

@@ -84,8 +84,12 @@ struct Geom {
 
 // ---------------------------------------------------------------- launchers (return cudaGetLastError())
 // Mesh transform (FP32 mixed path).
+// S_part (nullable): room for fwd_partial_elems(fs.M, sm_count) partial spectra; when given, a band with
+// fewer than about 8 x SMs frequency blocks splits the triangle list over several blocks and the
+// partial spectra are summed in a fixed order; when NULL every block takes the whole triangle list.
 cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const FreqSrc& fs, const Geom& g,
-                           const double* d_vol, float2* S, int* d_err, cudaStream_t st);
+                           const double* d_vol, float2* S, float2* S_part, int sm_count, int* d_err, cudaStream_t st);
+size_t fwd_partial_elems(int64_t M_max, int sm_count);
 cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_t_pad, const FreqF32* fr,
                            const int64_t* dM, int64_t M_max, float* partial, int n_chunks, int* d_err, cudaStream_t st);
 int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count);
@@ -123,6 +127,16 @@ cudaError_t launch_adj_batch_f32(const BatchAdjJob* jobs, const BatchUnit* units
 int batch_blocks_per_sm_fwd();
 int batch_blocks_per_sm_adj();
 constexpr int FWD_BLOCK_FREQS = 2 * FWD_THREADS;  // band frequencies per forward block
+
+// Triangle splits per forward frequency block: about `target` work units over the band's fb blocks,
+// at most one per triangle tile and 64 in all (1 when target <= 0).
+__host__ __device__ inline int fwd_splits(int64_t fb, int n_tiles, int target) {
+    if (target <= 0 || fb <= 0) return 1;
+    int64_t sp = (target + fb - 1) / fb;
+    if (sp > n_tiles) sp = n_tiles;
+    if (sp > 64) sp = 64;
+    return sp < 1 ? 1 : (int)sp;
+}
 constexpr int FWD_REC_TILE = 64;                  // triangle records per forward pipeline stage
 
 // Mesh transform (FP64 plain path).

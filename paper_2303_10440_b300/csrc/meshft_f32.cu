@@ -218,7 +218,8 @@ template <int MODE, bool EXPLICIT>
 __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n_tiles, const FreqSrc& fs, float tpx,
                                           float tpy, float tpz, const double* __restrict__ d_vol,
                                           float2* __restrict__ S, int* __restrict__ err, int64_t bidx,
-                                          TriF32 (*stage)[kFwdTile], uint64_t* full, uint64_t* empty) {
+                                          TriF32 (*stage)[kFwdTile], uint64_t* full, uint64_t* empty,
+                                          bool vol_term = true) {
     constexpr int PER_BLOCK = 2 * FWD_THREADS;
     const int tid = threadIdx.x;
     const int64_t M = fs.dM ? *fs.dM : fs.M;
@@ -300,7 +301,7 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
 #pragma unroll
         for (int l = 0; l < 2; ++l) {
             if (n[l][0] == 0 && n[l][1] == 0 && n[l][2] == 0) {
-                sx[l] = (float)*d_vol;
+                sx[l] = vol_term ? (float)*d_vol : 0.f;  // added once when the triangles are split
                 sy[l] = 0.f;
             } else {
                 const float ik2 = 1.0f / (xs[l] * xs[l] + ys[l] * ys[l] + zs[l] * zs[l]);
@@ -319,14 +320,53 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
     return true;
 }
 
+// Work units of the forward: (frequency block, triangle split). A small band splits the triangle list so
+// that enough blocks run; the split count follows from the band size on the device (dM), identically
+// in the sums and in the reduction below.
+__device__ __forceinline__ void fwd_units(const FreqSrc& fs, int n_tiles, int target, int64_t& M, int64_t& fb,
+                                          int& splits) {
+    M = fs.dM ? *fs.dM : fs.M;
+    fb = (M + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
+    splits = fwd_splits(fb, n_tiles, target);
+}
+
 template <int MODE, bool EXPLICIT>
-__global__ void __launch_bounds__(FWD_THREADS) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, FreqSrc fs,
+__global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, FreqSrc fs,
                                                          float tpx, float tpy, float tpz,
                                                          const double* __restrict__ d_vol, float2* __restrict__ S,
+                                                         float2* __restrict__ S_part, int target,
                                                          int* __restrict__ err) {
     __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
     __shared__ __align__(8) uint64_t full[kFwdStages], empty[kFwdStages];
-    fwd_block<MODE, EXPLICIT>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, err, blockIdx.x, stage, full, empty);
+    int64_t M, fb;
+    int splits;
+    fwd_units(fs, n_tiles, S_part ? target : 0, M, fb, splits);
+    const int64_t u = blockIdx.x;
+    if (u >= fb * splits) return;  // uniform per block
+    const int64_t b = u / splits;
+    const int ts = (int)(u - b * splits);
+    const int t0 = (int)((int64_t)n_tiles * ts / splits), t1 = (int)((int64_t)n_tiles * (ts + 1) / splits);
+    float2* out = splits == 1 ? S : S_part + (int64_t)ts * M;
+    fwd_block<MODE, EXPLICIT>(tris + (int64_t)t0 * kFwdTile, t1 - t0, fs, tpx, tpy, tpz, d_vol, out, err, b, stage,
+                              full, empty, ts == 0);
+}
+
+// S[m] = sum over the triangle splits of the partial spectra (fixed order, FP64); nothing when unsplit.
+__global__ void __launch_bounds__(256) k_fwd_reduce(FreqSrc fs, int n_tiles, int target,
+                                                    const float2* __restrict__ S_part, float2* __restrict__ S) {
+    int64_t M, fb;
+    int splits;
+    fwd_units(fs, n_tiles, target, M, fb, splits);
+    if (splits == 1) return;
+    for (int64_t m = (int64_t)blockIdx.x * 256 + threadIdx.x; m < M; m += (int64_t)gridDim.x * 256) {
+        double sx = 0.0, sy = 0.0;
+        for (int ts = 0; ts < splits; ++ts) {
+            const float2 v = S_part[(int64_t)ts * M + m];
+            sx += v.x;
+            sy += v.y;
+        }
+        S[m] = make_float2((float)sx, (float)sy);
+    }
 }
 
 // ------------------------------------------------------------------------------------- adjoint
@@ -467,8 +507,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
     const int64_t M = dM ? *dM : M_max;
     const int n_ftiles = (int)((M + ADJ_FTILE - 1) / ADJ_FTILE);
-    const int f0 = blockIdx.y * tiles_per_chunk;
-    const int f1 = min(f0 + tiles_per_chunk, n_ftiles);
+    // the chunks share the band's tiles as it is on the device (a narrow band still uses every chunk)
+    const int tpc = (n_ftiles + (int)gridDim.y - 1) / (int)gridDim.y;
+    (void)tiles_per_chunk;
+    const int f0 = blockIdx.y * tpc;
+    const int f1 = min(f0 + tpc, n_ftiles);
     adj_block<MODE>(tris, n_t, n_t_pad, fr, f0, f1, blockIdx.x, partial + (int64_t)blockIdx.y * NACC * n_t_pad, err,
                     stage, full, empty);
 }
@@ -545,20 +588,34 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_batch_f32(const BatchAdjJob
 
 }  // namespace
 
+int fwd_target_units(int sm_count) { return 8 * sm_count; }
+
+size_t fwd_partial_elems(int64_t M_max, int sm_count) {
+    const int64_t fb = (M_max + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
+    return (size_t)(fwd_target_units(sm_count) + fb) * FWD_BLOCK_FREQS;
+}
+
 cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const FreqSrc& fs, const Geom& g,
-                           const double* d_vol, float2* S, int* d_err, cudaStream_t st) {
+                           const double* d_vol, float2* S, float2* S_part, int sm_count, int* d_err, cudaStream_t st) {
     const int n_tiles = (int)(n_t_pad / kFwdTile);
     const float tpx = (float)(2.0 * M_PI / g.L[0]), tpy = (float)(2.0 * M_PI / g.L[1]),
                 tpz = (float)(2.0 * M_PI / g.L[2]);
-    const int64_t per_block = 2 * FWD_THREADS;
-    const int64_t blocks = (fs.M + per_block - 1) / per_block;
-    if (blocks <= 0 || n_tiles <= 0) return cudaSuccess;
+    const int64_t fb_max = (fs.M + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
+    if (fb_max <= 0 || n_tiles <= 0) return cudaSuccess;
+    // enough blocks for any band size up to fs.M: fb * splits <= target + fb
+    const int target = fwd_target_units(sm_count);
+    const int64_t blocks = S_part ? fb_max + target : fb_max;
     const dim3 grid((unsigned)blocks);
     const bool ex = fs.nlist != nullptr;
-    if (mode == 0 && !ex) k_fwd_f32<0, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, d_err);
-    if (mode == 0 && ex) k_fwd_f32<0, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, d_err);
-    if (mode == 1 && !ex) k_fwd_f32<1, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, d_err);
-    if (mode == 1 && ex) k_fwd_f32<1, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, d_err);
+    if (mode == 0 && !ex)
+        k_fwd_f32<0, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+    if (mode == 0 && ex)
+        k_fwd_f32<0, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+    if (mode == 1 && !ex)
+        k_fwd_f32<1, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+    if (mode == 1 && ex)
+        k_fwd_f32<1, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+    if (S_part) k_fwd_reduce<<<4 * sm_count, 256, 0, st>>>(fs, n_tiles, target, S_part, S);
     return cudaGetLastError();
 }
 
