@@ -232,11 +232,32 @@ typedef struct {
     double beta1, beta2, eps;
 } dm_fit_options;
 
+/* Optimiser state of a fit, for checkpoint and resume. The arrays are HOST memory owned by the
+ * caller ([n_v][3] doubles each); warm may be NULL (Adam fits have no smoothing solves). */
+typedef struct {
+    int64_t step;        /* optimiser steps taken so far (Adam's bias correction continues from here) */
+    double sigma[3];     /* current PSF sigma */
+    double m_sigma[3];   /* Adam moments of sigma */
+    double v_sigma[3];
+    double* m_V;         /* [n_v][3] first moments of the vertex optimiser */
+    double* v_V;         /* [n_v][3] second moments */
+    double* warm;        /* [2][n_v][3] starting guesses of the two large-steps smoothing solves, or NULL */
+} dm_fit_state;
+
 /* Fit vertices (and sigma when lr_psf > 0) to target by Adam, entirely on the device.
  * V_io: [n_v][3] initial positions in, fitted positions out. psf_io->sigma updated in place
  * (host struct). loss_history (nullable): [steps] doubles, the loss before each step. */
 dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
                  const void* target, const dm_fit_options* opt, double* loss_history, void* stream);
+
+/* dm_fit continued from a checkpoint: state (host, in/out) holds the optimiser state after
+ * state->step steps (zeros and step 0 for a fresh start) and V_io the vertices at that point; the
+ * call takes opt->steps more steps, sigma starts from state->sigma, and the state after the last
+ * step is written back (moments, sigma, step). A fit of a + b steps equals a fit of a steps
+ * followed by a resumed fit of b steps, bit for bit. Synchronises the stream. */
+dm_status dm_fit_resume(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
+                        const void* target, const dm_fit_options* opt, dm_fit_state* state, double* loss_history,
+                        void* stream);
 
 /* ---------------------------------------------------------------- staggered fit
  * Section 5.1 ("A staggered optimization scheme") and Section 5.2 ("PSF optimization step"):
@@ -338,12 +359,15 @@ typedef struct {
     int32_t optimizer;     /* vertex optimiser: DM_OPT_ADAM or DM_OPT_LARGE_STEPS (uniform Adam on
                               u = (1 + lambda L) v, FP32 smoothing solves, tolerance 1e-6) */
     double lambda;         /* large-steps smoothing weight (<= 0: 50) */
+    const dm_fit_state* resume; /* NULL, or the state of a preempted job (copied at submit): V is then
+                              that job's vertices and fit.steps the steps still to take */
 } dm_job;
 
 #define DM_JOB_QUEUED 0
 #define DM_JOB_RUNNING 1
 #define DM_JOB_DONE 2
 #define DM_JOB_FAILED 3
+#define DM_JOB_PREEMPTED 4
 
 typedef struct {
     int32_t state;         /* DM_JOB_* */
@@ -375,6 +399,12 @@ dm_status dm_server_wait(dm_server* srv, int64_t job_id, double timeout_s);
 /* Copy a finished job's results (host buffers, each nullable): V_out [n_v][3], sigma_out [3],
  * loss_history [steps]; then forget the job. */
 dm_status dm_server_result(dm_server* srv, int64_t job_id, double* V_out, double* sigma_out, double* loss_history);
+/* Checkpoint: stop a queued or running job at the next iteration boundary and copy its vertices
+ * (V_out, host [n_v][3]) and optimiser state (state: host arrays of the caller, each nullable) out;
+ * the job ends in DM_JOB_PREEMPTED and is forgotten. Submitting it again with dm_job.resume = state,
+ * V = V_out and fit.steps = the steps still to take continues it bit for bit. Waits up to timeout_s
+ * (< 0: no limit; DM_ERR_TIMEOUT). DM_ERR_ARG: unknown job, or it finished first (take its result). */
+dm_status dm_server_preempt(dm_server* srv, int64_t job_id, double timeout_s, double* V_out, dm_fit_state* state);
 dm_status dm_server_get_stats(dm_server* srv, dm_server_stats* out);
 /* Seconds since the server was created (the clock of dm_job_status). */
 double dm_server_clock(const dm_server* srv);

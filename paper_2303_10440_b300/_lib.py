@@ -91,6 +91,11 @@ class dm_stagger_stats(ctypes.Structure):
     _fields_ = [("cg_iterations", c_i64), ("cg_max", c_i64), ("cg_unconverged", c_i64)]
 
 
+class dm_fit_state(ctypes.Structure):
+    _fields_ = [("step", c_i64), ("sigma", c_f64 * 3), ("m_sigma", c_f64 * 3), ("v_sigma", c_f64 * 3), ("m_V", c_p),
+                ("v_V", c_p), ("warm", c_p)]
+
+
 class dm_server_options(ctypes.Structure):
     _fields_ = [("device", c_i32), ("max_jobs", c_i32), ("memory_bytes", ctypes.c_size_t), ("chunk_tiles", c_i32),
                 ("policy", c_i32), ("batch_terms", c_f64), ("max_wait_s", c_f64)]
@@ -112,6 +117,7 @@ class dm_job(ctypes.Structure):
         ("label", c_i32),
         ("optimizer", c_i32),
         ("lam", c_f64),
+        ("resume", ctypes.POINTER(dm_fit_state)),
     ]
 
 
@@ -126,7 +132,34 @@ class dm_server_stats(ctypes.Structure):
                 ("bytes_total", ctypes.c_size_t)]
 
 
-JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "preempted"}
+
+
+def fit_state_struct(state: dict, n_v: int, keep: list) -> "dm_fit_state":
+    """A dm_fit_state over host arrays of the state dict (step, sigma, m_sigma, v_sigma, m_V, v_V, warm);
+    the arrays are appended to `keep` so that they outlive the call."""
+    import numpy as np
+
+    st = dm_fit_state()
+    st.step = int(state.get("step", 0))
+    for a in range(3):
+        st.sigma[a] = float(state["sigma"][a])
+        st.m_sigma[a] = float(state.get("m_sigma", (0, 0, 0))[a])
+        st.v_sigma[a] = float(state.get("v_sigma", (0, 0, 0))[a])
+    for name, shape in (("m_V", (n_v, 3)), ("v_V", (n_v, 3)), ("warm", (2, n_v, 3))):
+        arr = state.get(name)
+        if arr is None and name == "warm":
+            continue
+        arr = np.ascontiguousarray(np.zeros(shape) if arr is None else arr, dtype=np.float64).reshape(shape)
+        state[name] = arr
+        keep.append(arr)
+        setattr(st, name, arr.ctypes.data)
+    return st
+
+
+def fit_state_dict(st: "dm_fit_state", arrays: dict) -> dict:
+    return {"step": int(st.step), "sigma": tuple(st.sigma), "m_sigma": tuple(st.m_sigma),
+            "v_sigma": tuple(st.v_sigma), **arrays}
 
 _SIGS = {
     "dm_create": (c_i32, [ctypes.POINTER(c_p), ctypes.POINTER(dm_options)]),
@@ -159,6 +192,7 @@ _SIGS = {
     "dm_server_status": (c_i32, [c_p, c_i64, ctypes.POINTER(dm_job_status)]),
     "dm_server_wait": (c_i32, [c_p, c_i64, c_f64]),
     "dm_server_result": (c_i32, [c_p, c_i64, c_p, c_p, c_p]),
+    "dm_server_preempt": (c_i32, [c_p, c_i64, c_f64, c_p, ctypes.POINTER(dm_fit_state)]),
     "dm_server_get_stats": (c_i32, [c_p, ctypes.POINTER(dm_server_stats)]),
     "dm_server_clock": (c_f64, [c_p]),
     "dm_server_shutdown": (c_i32, [c_p]),
@@ -169,6 +203,11 @@ _SIGS = {
         c_i32,
         [c_p, ctypes.POINTER(dm_mesh), c_p, ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p,
          ctypes.POINTER(dm_stagger_options), c_p, c_p, ctypes.POINTER(dm_stagger_stats), c_p],
+    ),
+    "dm_fit_resume": (
+        c_i32,
+        [c_p, ctypes.POINTER(dm_mesh), c_p, ctypes.POINTER(dm_psf), ctypes.POINTER(dm_grid), c_p,
+         ctypes.POINTER(dm_fit_options), ctypes.POINTER(dm_fit_state), c_p, c_p],
     ),
     "dm_fit": (
         c_i32,

@@ -252,6 +252,30 @@ class Renderer:
                               lr, beta1, beta2, eps, int(step), _stream(stream, param.device))
         self._check(st, "dm_adam")
 
+    def fit_resume(self, V, F, grid, psf, target, steps, lr_vertex, state=None, lr_psf=0.0, loss="mse",
+                   label="surface", weights=None, beta1=0.9, beta2=0.999, eps=1e-20, stream=None):
+        """dm_fit continued from a checkpoint. state: None (a fresh start from psf.sigma) or the dict
+        returned by an earlier call (step, sigma, Adam moments). Returns (V, sigma, loss_history, state);
+        a fit of a + b steps equals a fit of a steps and a resumed fit of b steps, bit for bit."""
+        dev = self._dev(V)
+        Vw = _as_tensor(V, torch.float64, dev).clone()
+        m, keep = self._mesh(Vw, F, label, weights, dev)
+        T = _as_tensor(target, self.real, dev if isinstance(target, torch.Tensor) and target.is_cuda else None)
+        g, p = _grid(grid), _psf(psf)
+        if state is None:
+            state = {"step": 0, "sigma": tuple(p.sigma)}
+        state = dict(state)
+        arrays = []
+        st = _lib.fit_state_struct(state, m.n_v, arrays)
+        o = _lib.dm_fit_options(int(steps), _lib.LOSSES[loss], float(lr_vertex), float(lr_psf), beta1, beta2, eps)
+        hist = torch.empty(int(steps), dtype=torch.float64)
+        rc = self.lib.dm_fit_resume(self.ctx, ctypes.byref(m), Vw.data_ptr(), ctypes.byref(p), ctypes.byref(g),
+                                    T.data_ptr(), ctypes.byref(o), ctypes.byref(st), hist.data_ptr(),
+                                    _stream(stream, dev))
+        self._check(rc, "dm_fit_resume")
+        new_state = _lib.fit_state_dict(st, {"m_V": state["m_V"].copy(), "v_V": state["v_V"].copy()})
+        return Vw, tuple(p.sigma), hist, new_state
+
     def smooth_solve(self, F, n_v, B, lam=50.0, X0=None, tol=0.0, max_iter=0, stream=None):
         """X = (1 + lam L)^-1 B for B [n_v, 3] (device), L the combinatorial mesh Laplacian.
         Returns (X, (total iterations, most in one column, unconverged columns))."""

@@ -570,8 +570,9 @@ dm_status dm_adam(dm_ctx* ctx, double* param, const double* grad, double* m, dou
     return DM_OK;
 }
 
-dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
-                 const void* target, const dm_fit_options* opt, double* loss_history, void* stream) {
+dm_status dm_fit_resume(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
+                        const void* target, const dm_fit_options* opt, dm_fit_state* state, double* loss_history,
+                        void* stream) {
     if (!ctx) return DM_ERR_ARG;
     ctx->err.clear();
     DeviceGuard dg(ctx->device);
@@ -579,6 +580,15 @@ dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io,
     dm_status s;
     if (!opt || opt->steps < 1) return fail(ctx, DM_ERR_ARG, "fit options: steps >= 1");
     if (!V_io || !target) return fail(ctx, DM_ERR_ARG, "V_io or target is NULL");
+    if (state && (state->step < 0 || !state->m_V || !state->v_V))
+        return fail(ctx, DM_ERR_ARG, "fit state: step >= 0 and both vertex moment arrays");
+    dm_psf* const psf_user = psf_io;
+    dm_psf psf_start;
+    if (state && psf_io) {  // sigma continues from the checkpoint
+        psf_start = *psf_io;
+        for (int a = 0; a < 3; ++a) psf_start.sigma[a] = state->sigma[a];
+        psf_io = &psf_start;
+    }
     if ((s = check_grid(ctx, grid)) != DM_OK) return s;
     if ((s = check_psf(ctx, psf_io)) != DM_OK) return s;
     if (opt->lr_psf > 0 && psf_io->kind != DM_PSF_DIAG)
@@ -609,6 +619,13 @@ dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io,
     // the fit owns a device copy of V
     CK(cudaMemcpyAsync(b.V, V_io, nV * sizeof(double), cudaMemcpyDefault, st));
     CK(cudaMemsetAsync(mom, 0, (2 * nV + 8) * sizeof(double), st));
+    const int64_t step0 = state ? state->step : 0;
+    if (state) {
+        CK(cudaMemcpyAsync(mV, state->m_V, nV * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(vV, state->v_V, nV * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ms, state->m_sigma, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(vs, state->v_sigma, 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
     Inputs in;
     in.V = b.V;
     in.F = mesh->F;
@@ -644,20 +661,36 @@ dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io,
         if (s != DM_OK) return s;
         CK(cudaMemcpyAsync(hist + it, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToDevice, st));
         Stage sg(ctx, DM_STAGE_ADAM, st);
-        LAUNCH(1, launch_adam(b.V, b.dV, mV, vV, nV, opt->lr_vertex, opt->beta1, opt->beta2, opt->eps, it + 1, st));
+        LAUNCH(1, launch_adam(b.V, b.dV, mV, vV, nV, opt->lr_vertex, opt->beta1, opt->beta2, opt->eps,
+                              step0 + it + 1, st));
         if (opt->lr_psf > 0)
             LAUNCH(1, launch_adam(b.d_params, b.d_params + 24, ms, vs, 3, opt->lr_psf, opt->beta1, opt->beta2,
-                                  opt->eps, it + 1, st));
+                                  opt->eps, step0 + it + 1, st));
     }
     CK(cudaMemcpyAsync(V_io, b.V, nV * sizeof(double), cudaMemcpyDefault, st));
     double sig[3];
     CK(cudaMemcpyAsync(sig, b.d_params, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (loss_history) CK(cudaMemcpyAsync(loss_history, hist, opt->steps * sizeof(double), cudaMemcpyDefault, st));
+    if (state) {
+        CK(cudaMemcpyAsync(state->m_V, mV, nV * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(state->v_V, vV, nV * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(state->m_sigma, ms, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(state->v_sigma, vs, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     s = check_dev_err(ctx, st);
     if (s != DM_OK) return s;
+    if (state) {
+        state->step = step0 + opt->steps;
+        for (int a = 0; a < 3; ++a) state->sigma[a] = sig[a];
+    }
     if (opt->lr_psf > 0)
-        for (int a = 0; a < 3; ++a) psf_io->sigma[a] = sig[a];
+        for (int a = 0; a < 3; ++a) psf_user->sigma[a] = sig[a];
     return DM_OK;
+}
+
+dm_status dm_fit(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* psf_io, const dm_grid* grid,
+                 const void* target, const dm_fit_options* opt, double* loss_history, void* stream) {
+    return dm_fit_resume(ctx, mesh, V_io, psf_io, grid, target, opt, nullptr, loss_history, stream);
 }
 
 }  // extern "C"

@@ -95,6 +95,14 @@ struct SJob {
     int steps_done = 0;
     double terms_step = 0;  // triangle-frequency terms of one step (triangles x half-spectrum size)
     double t_last = 0;      // when the job last advanced (or was admitted)
+    // checkpoint / resume: the optimiser state the job starts from, and the one it stopped at
+    int64_t step0 = 0;
+    bool has_resume = false, preempt_req = false;
+    std::vector<double> r_mV, r_vV, r_warm;
+    double r_ms[3] = {0, 0, 0}, r_vs[3] = {0, 0, 0};
+    std::vector<double> ck_V, ck_mV, ck_vV, ck_warm;
+    double ck_sigma[3] = {0, 0, 0}, ck_ms[3] = {0, 0, 0}, ck_vs[3] = {0, 0, 0};
+    int64_t ck_step = 0;
     double t_submit = 0, t_start = 0, t_end = 0, last_loss = NAN;
     // device state
     size_t off = 0, bytes = 0;
@@ -255,9 +263,22 @@ bool setup_job(dm_server* S, SJob* J) {
     g_launches += 5;
     if (ok && J->optimizer == DM_OPT_LARGE_STEPS) {
         ok = launch_laplacian(b.F, b.ptr, b.ent, z.n_v, b.cnt, J->lptr, J->lcol, ctx->d_err, st) == cudaSuccess &&
-             cudaMemsetAsync(J->gu, 0, 6 * z.n_v * sizeof(double), st) == cudaSuccess &&
+             cudaMemsetAsync(J->gu, 0, 3 * z.n_v * sizeof(double), st) == cudaSuccess &&
+             cudaMemsetAsync(J->wv, 0, 3 * z.n_v * sizeof(double), st) == cudaSuccess &&
              cudaMemsetAsync(J->cg_stats, 0, 4 * sizeof(unsigned long long), st) == cudaSuccess;
         g_launches += 3;
+        if (ok && J->has_resume && J->r_warm.size() == (size_t)6 * z.n_v)
+            ok = cudaMemcpyAsync(J->gu, J->r_warm.data(), 3 * z.n_v * sizeof(double), cudaMemcpyHostToDevice, st) ==
+                     cudaSuccess &&
+                 cudaMemcpyAsync(J->wv, J->r_warm.data() + 3 * z.n_v, 3 * z.n_v * sizeof(double),
+                                 cudaMemcpyHostToDevice, st) == cudaSuccess;
+    }
+    if (ok && J->has_resume) {
+        const int64_t nV = 3 * z.n_v;
+        ok = cudaMemcpyAsync(J->mV, J->r_mV.data(), nV * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+             cudaMemcpyAsync(J->vV, J->r_vV.data(), nV * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+             cudaMemcpyAsync(J->ms, J->r_ms, 3 * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+             cudaMemcpyAsync(J->vs, J->r_vs, 3 * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess;
     }
     // host vectors stay until the uploads have run (synchronised at the end of the iteration)
     if (!ok) {
@@ -430,18 +451,18 @@ bool iterate(dm_server* S, bool sync) {
             ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, b.dV, J->gu, nullptr, J->pcg_work, 1e-6, 2000,
                                     J->cg_stats, js) == cudaSuccess;
             ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
-                                      J->steps_done + 1, J->aup, js) == cudaSuccess;
+                                      J->step0 + J->steps_done + 1, J->aup, js) == cudaSuccess;
             ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, J->dl, J->wv, b.V, J->pcg_work, 1e-6, 2000,
                                     J->cg_stats, js) == cudaSuccess;
             g_launches += 7;
         } else {
             ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
-                              J->steps_done + 1, js) == cudaSuccess;
+                              J->step0 + J->steps_done + 1, js) == cudaSuccess;
             g_launches += 4;
         }
         if (o.lr_psf > 0) {
             ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
-                              J->steps_done + 1, js) == cudaSuccess;
+                              J->step0 + J->steps_done + 1, js) == cudaSuccess;
             g_launches += 1;
         }
         // the next iteration's batched launches on the server stream also follow this job's Adam
@@ -465,6 +486,27 @@ bool iterate(dm_server* S, bool sync) {
 }
 
 void finish_job(dm_server* S, SJob* J, int state) {
+    if (state == DM_JOB_PREEMPTED) {
+        // the job's stage work and the batched launches that read its buffers are complete
+        cudaStreamSynchronize(J->stream);
+        cudaStreamSynchronize(S->st);
+        const int64_t nV = 3 * J->z.n_v;
+        J->ck_V.resize(nV);
+        J->ck_mV.resize(nV);
+        J->ck_vV.resize(nV);
+        cudaMemcpy(J->ck_V.data(), J->b.V, nV * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->ck_mV.data(), J->mV, nV * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->ck_vV.data(), J->vV, nV * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->ck_ms, J->ms, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->ck_vs, J->vs, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(J->ck_sigma, J->b.d_params, 3 * sizeof(double), cudaMemcpyDeviceToHost);
+        if (J->optimizer == DM_OPT_LARGE_STEPS) {
+            J->ck_warm.resize(2 * nV);
+            cudaMemcpy(J->ck_warm.data(), J->gu, nV * sizeof(double), cudaMemcpyDeviceToHost);
+            cudaMemcpy(J->ck_warm.data() + nV, J->wv, nV * sizeof(double), cudaMemcpyDeviceToHost);
+        }
+        J->ck_step = J->step0 + J->steps_done;
+    }
     if (state == DM_JOB_DONE) {
         const int64_t nV = 3 * J->z.n_v;
         J->V_out.resize(nV);
@@ -483,6 +525,59 @@ void finish_job(dm_server* S, SJob* J, int state) {
     J->state = state;
     J->t_end = S->now();
     if (state == DM_JOB_DONE) S->stats.jobs_done += 1;
+}
+
+// Jobs whose checkpoint was requested leave at this iteration boundary with their state on the host;
+// queued ones leave with the state they were submitted with.
+void handle_preempts(dm_server* S) {
+    std::vector<SJob*> keep;
+    bool any = false;
+    for (SJob* J : S->active) {
+        bool req;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            req = J->preempt_req;
+        }
+        if (req) {
+            finish_job(S, J, DM_JOB_PREEMPTED);
+            any = true;
+        } else {
+            keep.push_back(J);
+        }
+    }
+    if (any) {
+        S->active.swap(keep);
+        S->dirty = true;
+        S->run.clear();
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto it = S->pending.begin(); it != S->pending.end();) {
+        SJob* J = *it;
+        if (!J->preempt_req) {
+            ++it;
+            continue;
+        }
+        const size_t nV = J->V.size();
+        J->ck_V = J->V;
+        J->ck_mV = J->has_resume ? J->r_mV : std::vector<double>(nV, 0.0);
+        J->ck_vV = J->has_resume ? J->r_vV : std::vector<double>(nV, 0.0);
+        if (J->optimizer == DM_OPT_LARGE_STEPS)
+            J->ck_warm = J->r_warm.size() == 2 * nV ? J->r_warm : std::vector<double>(2 * nV, 0.0);
+        for (int a = 0; a < 3; ++a) {
+            J->ck_sigma[a] = J->psf.sigma[a];
+            J->ck_ms[a] = J->r_ms[a];
+            J->ck_vs[a] = J->r_vs[a];
+        }
+        J->ck_step = J->step0;
+        J->state = DM_JOB_PREEMPTED;
+        J->t_end = S->now();
+        std::vector<double>().swap(J->V);
+        std::vector<int32_t>().swap(J->F);
+        std::vector<float>().swap(J->T);
+        it = S->pending.erase(it);
+        any = true;
+    }
+    if (any) S->cv.notify_all();
 }
 
 // Remaining work of a job in triangle-frequency terms.
@@ -519,6 +614,7 @@ void engine_main(dm_server* S) {
             S->cv.wait(lk, [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
             if (S->stop) break;
         }
+        handle_preempts(S);
         // admission: FIFO takes the head of the queue (a job that does not fit yet blocks the ones
         // behind it); SHORTEST takes the queued job with the least work, a long-waiting one first
         while ((int)S->active.size() < S->max_jobs) {
@@ -608,6 +704,11 @@ dm_status validate_job(const dm_job* j) {
     if (j->psf.kind != DM_PSF_DIAG) return DM_ERR_UNSUPPORTED;
     if (j->label != DM_SURFACE && j->label != DM_VOLUME) return DM_ERR_ARG;
     if (j->optimizer != DM_OPT_ADAM && j->optimizer != DM_OPT_LARGE_STEPS) return DM_ERR_ARG;
+    if (j->resume) {
+        if (j->resume->step < 0 || !j->resume->m_V || !j->resume->v_V) return DM_ERR_ARG;
+        for (int a = 0; a < 3; ++a)
+            if (!(j->resume->sigma[a] > 0) || !std::isfinite(j->resume->sigma[a])) return DM_ERR_ARG;
+    }
     if (std::isnan(j->lambda)) return DM_ERR_ARG;
     for (int a = 0; a < 3; ++a) {
         if (!(j->psf.sigma[a] > 0) || !(j->grid.h[a] > 0) || j->grid.n[a] < 1) return DM_ERR_ARG;
@@ -687,6 +788,19 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     J->fit = job->fit;
     J->label = job->label;
     J->optimizer = job->optimizer;
+    if (job->resume) {
+        const dm_fit_state* r = job->resume;
+        J->has_resume = true;
+        J->step0 = r->step;
+        J->r_mV.assign(r->m_V, r->m_V + 3 * job->n_v);
+        J->r_vV.assign(r->v_V, r->v_V + 3 * job->n_v);
+        if (r->warm) J->r_warm.assign(r->warm, r->warm + 6 * job->n_v);
+        for (int a = 0; a < 3; ++a) {
+            J->r_ms[a] = r->m_sigma[a];
+            J->r_vs[a] = r->v_sigma[a];
+            J->psf.sigma[a] = r->sigma[a];
+        }
+    }
     J->terms_step = (double)job->n_t * (double)job->grid.n[0] * job->grid.n[1] * (job->grid.n[2] / 2 + 1);
     J->lambda = job->lambda > 0 ? job->lambda : 50.0;
     // a job whose state can never fit the arena is refused now rather than queued forever
@@ -734,12 +848,53 @@ dm_status dm_server_wait(dm_server* S, int64_t id, double timeout_s) {
     auto it = S->jobs.find(id);
     if (it == S->jobs.end()) return DM_ERR_ARG;
     SJob* J = it->second;
-    auto done = [&] { return J->state == DM_JOB_DONE || J->state == DM_JOB_FAILED || S->stop; };
+    auto done = [&] {
+        return J->state == DM_JOB_DONE || J->state == DM_JOB_FAILED || J->state == DM_JOB_PREEMPTED || S->stop;
+    };
     if (timeout_s < 0)
         S->cv.wait(lk, done);
     else if (!S->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), done))
         return DM_ERR_TIMEOUT;
+    if (J->state == DM_JOB_PREEMPTED) return DM_ERR_ARG;
     return J->state == DM_JOB_DONE ? DM_OK : DM_ERR_CUDA;
+}
+
+dm_status dm_server_preempt(dm_server* S, int64_t id, double timeout_s, double* V_out, dm_fit_state* st) {
+    if (!S) return DM_ERR_ARG;
+    SJob* J = nullptr;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->jobs.find(id);
+        if (it == S->jobs.end()) return DM_ERR_ARG;
+        J = it->second;
+        if (J->state == DM_JOB_DONE || J->state == DM_JOB_FAILED || J->state == DM_JOB_PREEMPTED) return DM_ERR_ARG;
+        J->preempt_req = true;
+        S->cv.notify_all();
+        auto done = [&] {
+            return J->state == DM_JOB_PREEMPTED || J->state == DM_JOB_DONE || J->state == DM_JOB_FAILED || S->stop;
+        };
+        if (timeout_s < 0)
+            S->cv.wait(lk, done);
+        else if (!S->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), done))
+            return DM_ERR_TIMEOUT;
+        if (J->state != DM_JOB_PREEMPTED) return J->state == DM_JOB_DONE ? DM_ERR_ARG : DM_ERR_CUDA;
+        S->jobs.erase(it);
+    }
+    const size_t nV = J->ck_V.size();
+    if (V_out) memcpy(V_out, J->ck_V.data(), nV * sizeof(double));
+    if (st) {
+        st->step = J->ck_step;
+        for (int a = 0; a < 3; ++a) {
+            st->sigma[a] = J->ck_sigma[a];
+            st->m_sigma[a] = J->ck_ms[a];
+            st->v_sigma[a] = J->ck_vs[a];
+        }
+        if (st->m_V) memcpy(st->m_V, J->ck_mV.data(), nV * sizeof(double));
+        if (st->v_V) memcpy(st->v_V, J->ck_vV.data(), nV * sizeof(double));
+        if (st->warm && J->ck_warm.size() == 2 * nV) memcpy(st->warm, J->ck_warm.data(), 2 * nV * sizeof(double));
+    }
+    delete J;
+    return DM_OK;
 }
 
 dm_status dm_server_result(dm_server* S, int64_t id, double* V_out, double* sigma_out, double* loss_history) {

@@ -53,7 +53,9 @@ class FitServer:
 
     def submit(self, V, F, target, grid, psf, steps: int, lr_vertex: float, lr_psf: float = 0.0, loss: str = "mse",
                label: str = "surface", beta1=0.9, beta2=0.999, eps=1e-20, optimizer: str = "adam",
-               lam: float = 50.0) -> int:
+               lam: float = 50.0, resume: dict | None = None) -> int:
+        """resume: the state dict of a preempted job (see preempt); V is then that job's vertices and
+        steps the steps still to take."""
         V = np.ascontiguousarray(V, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.int32)
         T = np.ascontiguousarray(target, dtype=np.float32)
@@ -69,12 +71,33 @@ class FitServer:
         j.label = _lib.DM_VOLUME if label == "volume" else _lib.DM_SURFACE
         j.optimizer = _lib.OPTIMIZERS[optimizer]
         j.lam = float(lam)
+        keep = []
+        if resume is not None:
+            st = _lib.fit_state_struct(dict(resume), V.shape[0], keep)
+            keep.append(st)
+            j.resume = ctypes.pointer(st)
         jid = ctypes.c_int64()
         st = self.lib.dm_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid))  # copies every input
         if st != _lib.DM_OK:
             raise RuntimeError(f"dm_server_submit: {_lib.STATUS.get(st, st)}")
         self._meta[jid.value] = (V.shape[0], int(steps))
         return jid.value
+
+    def preempt(self, job_id: int, timeout: float = -1.0):
+        """Stop a queued or running job at the next iteration boundary. Returns (V, state) to resubmit with
+        ``submit(..., V=V, steps=<remaining>, resume=state)``, or None if the job finished first."""
+        n_v, _ = self._meta[job_id]
+        V = np.empty((n_v, 3))
+        arrays = {"m_V": np.empty((n_v, 3)), "v_V": np.empty((n_v, 3)), "warm": np.zeros((2, n_v, 3))}
+        st = _lib.dm_fit_state()
+        st.m_V, st.v_V, st.warm = (arrays[k].ctypes.data for k in ("m_V", "v_V", "warm"))
+        rc = self.lib.dm_server_preempt(self.h, job_id, float(timeout), V.ctypes.data, ctypes.byref(st))
+        if rc == -1:  # DM_ERR_ARG: finished first (or unknown)
+            return None
+        if rc != _lib.DM_OK:
+            raise RuntimeError(f"dm_server_preempt: {_lib.STATUS.get(rc, rc)}")
+        self._meta.pop(job_id, None)
+        return V, _lib.fit_state_dict(st, arrays)
 
     def status(self, job_id: int) -> dict:
         s = _lib.dm_job_status()

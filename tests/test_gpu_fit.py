@@ -59,3 +59,21 @@ def test_fit_reduces_the_loss_and_adapts_sigma(r32):
     assert h[-1] < 0.3 * h[0]
     assert r_err1 < 0.5 * r_err0
     assert sig[0] < 0.45  # the PSF moved toward the truth (0.4)
+
+
+def test_resumed_fit_equals_the_uninterrupted_fit(r32):
+    """Checkpoint / resume: 3 + 5 steps through dm_fit_resume equal 8 steps of dm_fit, bit for bit."""
+    grid = synth.Grid(n=(48, 48, 48), h=(0.5, 0.5, 1.0))
+    V0, F = synth.sphere_mesh(3, 6.0, grid.center)
+    Fd = _dev(F)
+    T = r32.render(_dev(synth.scale_about(V0, (1.04, 0.97, 1.0), grid.center)), Fd, grid, synth.Psf(sigma=(0.4, 0.4, 0.8)))
+    psf0 = synth.Psf(sigma=(0.45, 0.45, 0.9))
+    kw = dict(lr_vertex=0.02, lr_psf=0.003)
+    V8, sig8, h8 = r32.fit(_dev(V0), Fd, grid, psf0, T, steps=8, **kw)
+    Va, siga, ha, st = r32.fit_resume(_dev(V0), Fd, grid, psf0, T, 3, state=None, **kw)
+    assert st["step"] == 3
+    Vb, sigb, hb, st2 = r32.fit_resume(Va, Fd, grid, psf0, T, 5, state=st, **kw)
+    assert st2["step"] == 8
+    assert torch.equal(Vb, V8)
+    assert sigb == sig8
+    assert np.array_equal(np.concatenate([ha.numpy(), hb.numpy()]), h8.numpy())

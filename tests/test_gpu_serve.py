@@ -223,3 +223,52 @@ def test_shortest_policy_runs_small_jobs_first_with_unchanged_results(setup):
     for r in rs:
         assert np.array_equal(r.V, alone.V) and np.array_equal(r.loss_history, alone.loss_history)
     assert len(rb.loss_history) == 30 and rb.loss_history[-1] < rb.loss_history[0]
+
+
+@pytest.mark.parametrize("optimizer,lr", [("adam", 0.02), ("large_steps", 0.5)])
+def test_preempted_job_resumes_bit_for_bit(setup, optimizer, lr):
+    """Checkpoint / resume in the server: stop a running job, resubmit it with its state, and the result
+    equals the uninterrupted run (vertices and the remaining losses)."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    steps = 14
+    job = dict(jobs[2], steps=steps, optimizer=optimizer, lr_vertex=lr, lr_psf=0.002)
+    s0 = FitServer(max_jobs=2)
+    i0 = s0.submit(**job)
+    assert s0.wait(i0, timeout=300)
+    full = s0.result(i0)
+    s0.shutdown()
+    s = FitServer(max_jobs=2)
+    i = s.submit(**job)
+    t_end = time.time() + 120
+    while s.status(i)["steps_done"] < 4 and time.time() < t_end:
+        time.sleep(0.001)
+    out = s.preempt(i, timeout=120)
+    assert out is not None
+    V, state = out
+    k = state["step"]
+    assert 4 <= k < steps
+    j = s.submit(**dict(job, V=V, steps=steps - k, resume=state))
+    assert s.wait(j, timeout=300)
+    rest = s.result(j)
+    s.shutdown()
+    assert np.array_equal(rest.V, full.V)
+    assert np.array_equal(rest.loss_history, full.loss_history[k:])
+
+
+def test_preempting_a_queued_job_returns_its_start_state(setup):
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    s = FitServer(max_jobs=1)
+    a = s.submit(**dict(jobs[0], steps=40))
+    b = s.submit(**jobs[1])
+    out = s.preempt(b, timeout=60)
+    assert s.wait(a, timeout=300)
+    s.result(a)
+    s.shutdown()
+    assert out is not None
+    V, state = out
+    assert state["step"] == 0 and np.array_equal(V, jobs[1]["V"])
+    assert not np.any(state["m_V"]) and not np.any(state["v_V"])
