@@ -189,6 +189,7 @@ struct dm_server {
     std::vector<std::pair<cudaStream_t, cudaEvent_t>> free_streams;  // job streams not in use
     cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr;                  // after each batched launch
     int64_t since_sync = 0;
+    bool prev_single = false;  // the last iteration advanced one job, all on the server stream
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
@@ -280,6 +281,8 @@ bool setup_job(dm_server* S, SJob* J) {
              cudaMemcpyAsync(J->ms, J->r_ms, 3 * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess &&
              cudaMemcpyAsync(J->vs, J->r_vs, 3 * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess;
     }
+    // iterations with a single job run its stage kernels on the server stream: order them after the uploads
+    if (ok) ok = cudaEventRecord(J->ev, st) == cudaSuccess && cudaStreamWaitEvent(S->st, J->ev, 0) == cudaSuccess;
     // host vectors stay until the uploads have run (synchronised at the end of the iteration)
     if (!ok) {
         cudaGetLastError();
@@ -367,10 +370,18 @@ bool iterate(dm_server* S, bool sync) {
     cudaStream_t st = S->st;
     if (S->dirty && !rebuild_units(S)) return false;
     const size_t nj = S->run.size();
+    // one job: its stage kernels go on the server stream and no events are needed between them
+    const bool single = nj == 1;
     bool ok = true;
+    if (!single && S->prev_single) {
+        // the previous iteration ran on the server stream only: the job streams start after it
+        ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
+        for (SJob* J : S->run) ok &= cudaStreamWaitEvent(J->stream, S->ev_fwd, 0) == cudaSuccess;
+    }
+    S->prev_single = single;
     // triangle records, normalisers, bands
     for (SJob* J : S->run) {
-        cudaStream_t js = J->stream;
+        cudaStream_t js = single ? st : J->stream;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         int nb = 0;
@@ -383,17 +394,21 @@ bool iterate(dm_server* S, bool sync) {
                               b.band_idx, b.dM, b.band_counts, js) == cudaSuccess;
             g_launches += 3;
         }
-        ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
-        ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
+        if (!single) {
+            ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
+            ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
+        }
     }
-    ok &= launch_fwd_batch_f32(S->d_fj, S->d_uf, (int)S->uf.size(), S->d_counter, S->grid_fwd, ctx->d_err, st) ==
-          cudaSuccess;
+    // persistent grids no larger than the unit lists (a small batch launches no idle blocks)
+    const int gf = (int)std::min<size_t>((size_t)S->grid_fwd, S->uf.size());
+    const int ga = (int)std::min<size_t>((size_t)S->grid_adj, S->ua.size());
+    ok &= launch_fwd_batch_f32(S->d_fj, S->d_uf, (int)S->uf.size(), S->d_counter, gf, ctx->d_err, st) == cudaSuccess;
     ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
     g_launches += 1;
     // image, loss, adjoint records
     for (SJob* J : S->run) {
-        cudaStream_t js = J->stream;
-        ok &= cudaStreamWaitEvent(js, S->ev_fwd, 0) == cudaSuccess;
+        cudaStream_t js = single ? st : J->stream;
+        if (!single) ok &= cudaStreamWaitEvent(js, S->ev_fwd, 0) == cudaSuccess;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         const Sizes& z = J->z;
@@ -421,18 +436,19 @@ bool iterate(dm_server* S, bool sync) {
                                             js) == cudaSuccess;
         ok &= launch_sum(b.partial, ng, 8, 8, b.d_params + 24, js) == cudaSuccess;
         g_launches += 12;
-        ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
-        ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
+        if (!single) {
+            ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
+            ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
+        }
     }
-    ok &= launch_adj_batch_f32(S->d_aj, S->d_ua, (int)S->ua.size(), S->d_counter, S->grid_adj, ctx->d_err, st) ==
-          cudaSuccess;
+    ok &= launch_adj_batch_f32(S->d_aj, S->d_ua, (int)S->ua.size(), S->d_counter, ga, ctx->d_err, st) == cudaSuccess;
     ok &= cudaEventRecord(S->ev_adj, st) == cudaSuccess;
     g_launches += 1;
     // per-vertex gradients and Adam
     for (size_t j = 0; j < nj; ++j) {
         SJob* J = S->run[j];
-        cudaStream_t js = J->stream;
-        ok &= cudaStreamWaitEvent(js, S->ev_adj, 0) == cudaSuccess;
+        cudaStream_t js = single ? st : J->stream;
+        if (!single) ok &= cudaStreamWaitEvent(js, S->ev_adj, 0) == cudaSuccess;
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         const Sizes& z = J->z;
@@ -466,8 +482,10 @@ bool iterate(dm_server* S, bool sync) {
             g_launches += 1;
         }
         // the next iteration's batched launches on the server stream also follow this job's Adam
-        ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
-        ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
+        if (!single) {
+            ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
+            ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
+        }
     }
     for (size_t j = 0; j < nj; ++j) S->run[j]->steps_done += 1;
     if (sync) {
