@@ -20,8 +20,9 @@
 // FP32 edge projections.
 //
 // Forward: a thread holds two band frequencies in registers; the block walks the
-// triangle list in tiles bulk-copied (TMA) into shared memory, double buffered on
-// two mbarriers. FP32 sums within a tile, Kahan across tiles.
+// triangle list (or, for a small band, a slice of it) in tiles bulk-copied (TMA)
+// into a ring of shared-memory stages with full/empty mbarriers. FP32 sums within
+// a tile, Kahan across tiles; slices are summed afterwards in FP64 in a fixed order.
 // Adjoint: a thread holds one triangle; the block walks a chunk of the band in
 // tiles of frequency-pair records bulk-copied the same way, keeping the triangle's
 // 10 (surface) or 12 (volume) sums in registers; chunks are summed afterwards in
@@ -500,8 +501,7 @@ template <int MODE>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restrict__ tris, int64_t n_t,
                                                          int64_t n_t_pad, const FreqPairF32* __restrict__ fr,
                                                          const int64_t* __restrict__ dM, int64_t M_max,
-                                                         int tiles_per_chunk, float* __restrict__ partial,
-                                                         int* __restrict__ err) {
+                                                         float* __restrict__ partial, int* __restrict__ err) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
     __shared__ __align__(128) FreqPairF32 stage[kAdjStages][kAdjPairs];
     __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
@@ -509,7 +509,6 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     const int n_ftiles = (int)((M + ADJ_FTILE - 1) / ADJ_FTILE);
     // the chunks share the band's tiles as it is on the device (a narrow band still uses every chunk)
     const int tpc = (n_ftiles + (int)gridDim.y - 1) / (int)gridDim.y;
-    (void)tiles_per_chunk;
     const int f0 = blockIdx.y * tpc;
     const int f1 = min(f0 + tpc, n_ftiles);
     adj_block<MODE>(tris, n_t, n_t_pad, fr, f0, f1, blockIdx.x, partial + (int64_t)blockIdx.y * NACC * n_t_pad, err,
@@ -632,13 +631,11 @@ int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count) {
 
 cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_t_pad, const FreqF32* fr,
                            const int64_t* dM, int64_t M_max, float* partial, int n_chunks, int* d_err, cudaStream_t st) {
-    const int64_t ftiles = (M_max + ADJ_FTILE - 1) / ADJ_FTILE;
-    const int tpc = (int)((ftiles + n_chunks - 1) / n_chunks);
     const dim3 grid((unsigned)(n_t_pad / ADJ_THREADS), (unsigned)n_chunks);
     if (mode == 0)
-        k_adj_f32<0><<<grid, ADJ_THREADS, 0, st>>>(tris, n_t, n_t_pad, fr, dM, M_max, tpc, partial, d_err);
+        k_adj_f32<0><<<grid, ADJ_THREADS, 0, st>>>(tris, n_t, n_t_pad, fr, dM, M_max, partial, d_err);
     else
-        k_adj_f32<1><<<grid, ADJ_THREADS, 0, st>>>(tris, n_t, n_t_pad, fr, dM, M_max, tpc, partial, d_err);
+        k_adj_f32<1><<<grid, ADJ_THREADS, 0, st>>>(tris, n_t, n_t_pad, fr, dM, M_max, partial, d_err);
     return cudaGetLastError();
 }
 
