@@ -154,6 +154,12 @@ dm_status dm_profile_read(dm_ctx* ctx, double* ms, int64_t* calls);
  * dependency chains on the default stream and synchronises. */
 dm_status dm_probe_mufu(int32_t kind, int32_t device, double* ops_per_s);
 
+/* Failure-detection check with no counterpart in the paper: runs one block whose threads wait on an
+ * mbarrier that nothing completes, with the bounded wait the mesh-transform pipelines use, limited to
+ * limit_ns (<= 2 s). *status = DM_ERR_TIMEOUT when the wait expired and was reported through the
+ * device error flag (the expected outcome), DM_OK otherwise; the context stays usable. Synchronises. */
+dm_status dm_probe_wait_timeout(int32_t device, uint64_t limit_ns, int32_t* status);
+
 /* ---------------------------------------------------------------- stages */
 
 /* Narrow band (Sec. 5.1). Writes the band's indices into H (ordered) to idx_out

@@ -197,6 +197,7 @@ _SIGS = {
     "dm_server_clock": (c_f64, [c_p]),
     "dm_server_shutdown": (c_i32, [c_p]),
     "dm_probe_mufu": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_f64)]),
+    "dm_probe_wait_timeout": (c_i32, [c_i32, ctypes.c_uint64, ctypes.POINTER(c_i32)]),
     "dm_smooth_solve": (c_i32, [c_p, c_p, c_i64, c_i64, c_f64, c_p, c_p, c_f64, c_i32, c_p, c_p]),
     "dm_adam_uniform": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i64, c_f64, c_f64, c_f64, c_f64, c_i64, c_p]),
     "dm_fit_staggered": (
