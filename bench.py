@@ -326,7 +326,7 @@ def _served_run(jobs, arrivals, dev, **server_kw):
     return dict(_stats(lat, span, len(jobs)), peak_batch=int(st["peak_active"]), iterations=int(st["iterations"]))
 
 
-def serving_leg(args, dev, n_jobs=16, rates=(10.0, 50.0, 500.0), steps=10, levels=(2, 3), sides=(32, 48, 64),
+def serving_leg(args, dev, n_jobs=16, rates=(10.0, 50.0, 100.0, 500.0), steps=10, levels=(2, 3), sides=(32, 48, 64),
                 with_fp64=True):
     """Served fits/s and p50/p99 latency vs one-job-at-a-time FP32 and plain FP64 at each arrival rate.
 
@@ -365,7 +365,8 @@ def serving_leg(args, dev, n_jobs=16, rates=(10.0, 50.0, 500.0), steps=10, level
         rng = np.random.default_rng(6)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
         arrivals -= arrivals[0]
-        entry = {"served_fp32": _served_run(jobs, arrivals, dev)}
+        entry = {"served_fp32": _served_run(jobs, arrivals, dev),
+                 "served_fp32_shortest_first": _served_run(jobs, arrivals, dev, policy="shortest", batch_terms=3e9)}
         for name, durs in durations.items():
             lat, span = _queue_latencies(arrivals, durs)
             entry[name] = _stats(lat, span, n_jobs)
