@@ -420,10 +420,7 @@ dm_status dm_meshft(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* grid, const
     fs.idx = nullptr;
     fs.dM = nullptr;
     fs.M = M;
-    fs.Nx = grid->n[0];
-    fs.Ny = grid->n[1];
-    fs.Nz = grid->n[2];
-    fs.Nzh = grid->n[2] / 2 + 1;
+    fs.set_dims(grid->n[0], grid->n[1], grid->n[2]);
     const Geom G = make_geom(grid);
     if (f64)
         LAUNCH(1, launch_fwd_f64(mesh->label, (const TriF64*)b.tris, mesh->n_t, fs, G, b.d_params + 16, (double2*)S, st));

@@ -396,10 +396,7 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
     // narrow band
     FreqSrc fs;
     fs.nlist = nullptr;
-    fs.Nx = grid->n[0];
-    fs.Ny = grid->n[1];
-    fs.Nz = grid->n[2];
-    fs.Nzh = grid->n[2] / 2 + 1;
+    fs.set_dims(grid->n[0], grid->n[1], grid->n[2]);
     fs.M = z.nH;
     if (z.band) {
         Stage sg(ctx, DM_STAGE_BAND, st);

@@ -181,6 +181,34 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return r;
 }
 
+// Division by a grid dimension without a run-time divide: for n < 2^32, n / d is the high word of
+// n * m with m = ceil(2^64 / d) (exact, since n (m - 2^64 / d) / 2^64 < 2^-32 < 1 / d).
+struct FastDiv {
+    unsigned long long m;
+    uint32_t d;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    f.m = d > 1 ? ~0ull / d + 1 : 0;
+    return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+    return f.d > 1 ? (uint32_t)__umul64hi((unsigned long long)n, f.m) : n;
+}
+
+// Half-spectrum index (< 2^32) -> integer frequency, with the divisions by Nzh and Ny precomputed.
+__device__ __forceinline__ void decode_h_fast(uint32_t idx, const FastDiv& dzh, const FastDiv& dy, int Nx, int Ny,
+                                              int& nx, int& ny, int& nz) {
+    const uint32_t t = fdiv(idx, dzh);
+    const int iz = (int)(idx - t * dzh.d);
+    const uint32_t ix = fdiv(t, dy);
+    const int iy = (int)(t - ix * dy.d);
+    nx = (int)ix < (Nx + 1) / 2 ? (int)ix : (int)ix - Nx;
+    ny = iy < (Ny + 1) / 2 ? iy : iy - Ny;
+    nz = iz;
+}
+
 // Half-spectrum index -> integer frequency (fftfreq convention on x, y; n_z = iz).
 __device__ __forceinline__ void decode_h(int64_t idx, int Nx, int Ny, int Nzh, int& nx, int& ny, int& nz) {
     const int iz = (int)(idx % Nzh);

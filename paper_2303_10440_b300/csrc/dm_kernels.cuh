@@ -75,7 +75,20 @@ struct FreqSrc {
     const int64_t* dM;     // device band size (nullptr: use M)
     int64_t M;             // host-side upper bound / exact size
     int Nx, Ny, Nzh, Nz;
+    FastDiv div_zh, div_y;  // divisions by Nzh and Ny for index decoding
+    // grid dimensions and their divisors
+    void set_dims(int nx, int ny, int nz) {
+        Nx = nx;
+        Ny = ny;
+        Nz = nz;
+        Nzh = nz / 2 + 1;
+        div_zh = make_fastdiv((uint32_t)Nzh);
+        div_y = make_fastdiv((uint32_t)ny);
+    }
 };
+__device__ __forceinline__ void decode_h(int64_t idx, const FreqSrc& fs, int& nx, int& ny, int& nz) {
+    decode_h_fast((uint32_t)idx, fs.div_zh, fs.div_y, fs.Nx, fs.Ny, nx, ny, nz);
+}
 
 struct Geom {
     double L[3];       // periods

@@ -239,7 +239,7 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
                 n[l][2] = fs.nlist[3 * m + 2];
             } else {
                 const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
-                decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, n[l][0], n[l][1], n[l][2]);
+                decode_h(idx, fs, n[l][0], n[l][1], n[l][2]);
             }
         }
     }

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(F64_THREADS) k_fwd_f64(const TriF64* __restric
         nz = fs.nlist[3 * m + 2];
     } else {
         const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
-        decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, nx, ny, nz);
+        decode_h(idx, fs, nx, ny, nz);
     }
     const double xx = nx * tpx, xy = ny * tpy, xz = nz * tpz;
     const uint64_t unx = (uint64_t)(int64_t)nx, uny = (uint64_t)(int64_t)ny, unz = (uint64_t)(int64_t)nz;

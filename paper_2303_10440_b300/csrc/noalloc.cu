@@ -115,10 +115,7 @@ extern "C" dm_status dm_meshft_noalloc(const dm_mesh* mesh, const dm_grid* grid,
     fs.idx = nullptr;
     fs.dM = nullptr;
     fs.M = M;
-    fs.Nx = grid->n[0];
-    fs.Ny = grid->n[1];
-    fs.Nz = grid->n[2];
-    fs.Nzh = grid->n[2] / 2 + 1;
+    fs.set_dims(grid->n[0], grid->n[1], grid->n[2]);
 
     // The fault flags must start at zero for this call; records, partials and the
     // normaliser are fully rewritten before they are read.

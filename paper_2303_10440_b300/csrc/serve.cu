@@ -313,10 +313,7 @@ bool rebuild_units(dm_server* S) {
         f.fs.idx = z.band ? b.band_idx : nullptr;
         f.fs.dM = z.band ? b.dM : nullptr;
         f.fs.M = z.nH;
-        f.fs.Nx = J->grid.n[0];
-        f.fs.Ny = J->grid.n[1];
-        f.fs.Nz = J->grid.n[2];
-        f.fs.Nzh = J->grid.n[2] / 2 + 1;
+        f.fs.set_dims(J->grid.n[0], J->grid.n[1], J->grid.n[2]);
         for (int a = 0; a < 3; ++a) f.tp[a] = (float)(2.0 * M_PI / G.L[a]);
         f.d_vol = b.d_params + 16;
         f.S = (float2*)b.S;
@@ -417,10 +414,7 @@ bool iterate(dm_server* S, bool sync) {
         fs.idx = z.band ? b.band_idx : nullptr;
         fs.dM = z.band ? b.dM : nullptr;
         fs.M = z.nH;
-        fs.Nx = J->grid.n[0];
-        fs.Ny = J->grid.n[1];
-        fs.Nz = J->grid.n[2];
-        fs.Nzh = J->grid.n[2] / 2 + 1;
+        fs.set_dims(J->grid.n[0], J->grid.n[1], J->grid.n[2]);
         const int* n = J->grid.n;
         int nl = 0, ng = 0;
         ok &= launch_scatter<float>((const Cx<float>*)b.S, fs, b.d_params, J->psf.kind, b.d_params + 16, G,

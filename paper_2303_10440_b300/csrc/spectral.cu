@@ -6,6 +6,8 @@
 // so repeated runs are bitwise identical.
 #include <cmath>
 
+#include <algorithm>
+
 #include "dm_kernels.cuh"
 
 namespace dm {
@@ -133,19 +135,46 @@ __device__ __forceinline__ double otf_expo(const double* psf, int kind, double x
     return c[0] * x * x + c[1] * y * y + c[2] * z * z + 2.0 * (c[3] * x * y + c[4] * x * z + c[5] * y * z);
 }
 
+// h_hat(xi) in the path's precision: FP32 (the FP32 images' own precision) or FP64.
+template <class R>
+__device__ __forceinline__ R otf_r(const double* psf, int kind, double x, double y, double z);
+template <>
+__device__ __forceinline__ float otf_r<float>(const double* psf, int kind, double x, double y, double z) {
+    const float xf = (float)x, yf = (float)y, zf = (float)z;
+    float e;
+    if (kind == 0) {
+        const float s0 = (float)psf[0], s1 = (float)psf[1], s2 = (float)psf[2];
+        e = s0 * s0 * xf * xf + s1 * s1 * yf * yf + s2 * s2 * zf * zf;
+    } else {
+        const double* c = psf + 3;
+        e = (float)c[0] * xf * xf + (float)c[1] * yf * yf + (float)c[2] * zf * zf +
+            2.0f * ((float)c[3] * xf * yf + (float)c[4] * xf * zf + (float)c[5] * yf * zf);
+    }
+    return expf(-0.5f * e);
+}
+template <>
+__device__ __forceinline__ double otf_r<double>(const double* psf, int kind, double x, double y, double z) {
+    return exp(-0.5 * otf_expo(psf, kind, x, y, z));
+}
+
 struct BandArgs {
     const double* psf;
     int kind;
     double tau;
+    double e_max;  // -2 ln tau: h_hat > tau  <=>  xi^T Sigma xi < e_max
     int Nx, Ny, Nz, Nzh;
+    FastDiv div_zh, div_y;
     double tp[3];
     int64_t nH;
 };
 
+// h_hat(xi) > tau, decided on the exponent (no exp) except within rounding of the threshold, where the
+// exp form decides as written.
 __device__ __forceinline__ bool in_band(const BandArgs& b, int64_t idx) {
     int nx, ny, nz;
-    decode_h(idx, b.Nx, b.Ny, b.Nzh, nx, ny, nz);
+    decode_h_fast((uint32_t)idx, b.div_zh, b.div_y, b.Nx, b.Ny, nx, ny, nz);
     const double e = otf_expo(b.psf, b.kind, nx * b.tp[0], ny * b.tp[1], nz * b.tp[2]);
+    if (fabs(e - b.e_max) > 1e-9 * b.e_max) return e < b.e_max;
     return exp(-0.5 * e) > b.tau;
 }
 
@@ -208,9 +237,9 @@ __global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, Fre
     if (m >= M) return;
     const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
     int nx, ny, nz;
-    decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, nx, ny, nz);
-    const double hh = exp(-0.5 * otf_expo(psf, kind, nx * tpx, ny * tpy, nz * tpz));
-    const R sc = (R)(hh * inv_VL / *d_norm);
+    decode_h(idx, fs, nx, ny, nz);
+    const R hh = otf_r<R>(psf, kind, nx * tpx, ny * tpy, nz * tpz);
+    const R sc = hh * (R)(inv_VL / *d_norm);
     const Cx<R> s = S[m];
     spec[idx] = Cx<R>{s.x * sc, s.y * sc};
 }
@@ -219,15 +248,17 @@ template <class R>
 __global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* __restrict__ T, int64_t n, int kind,
                                              R* __restrict__ resid, double* __restrict__ partial) {
     __shared__ double scratch[32];
+    // per voxel in the path's precision R, the sum in FP64
     double l = 0.0;
     const double inv_n = 1.0 / (double)n;
+    const R s = kind == 1 ? (R)(2.0 * inv_n) : (R)2;
     for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
-        const double d = (double)I[j] - (double)T[j];
-        double w = 1.0, s = 2.0;
-        if (kind == 1) s = 2.0 * inv_n;
-        if (kind == 2) w = (double)T[j];
-        l += w * d * d;
-        resid[j] = (R)(s * w * d);
+        const R t = T[j];
+        const R d = I[j] - t;
+        const R w = kind == 2 ? t : (R)1;
+        const R wd = w * d;
+        l += (double)(wd * d);
+        resid[j] = s * wd;
     }
     if (kind == 1) l *= inv_n;
     l = block_sum<NT>(l, scratch);
@@ -273,54 +304,62 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
                                                const double* __restrict__ d_norm, double tpx, double tpy, double tpz,
                                                double inv_VL, FR* __restrict__ fr, int64_t M_pad,
                                                double* __restrict__ partial) {
+    // Per frequency in the path's precision R; the sums over frequencies in FP64. Grid-stride over
+    // the padded band, so each block reduces its partial sums once.
     __shared__ double scratch[32];
     const int64_t M = fs.dM ? *fs.dM : fs.M;
-    const int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const R rin = (R)(1.0 / *d_norm);
+    const R cvl = (R)inv_VL;
+    const R s0 = (R)psf[0], s1 = (R)psf[1], s2 = (R)psf[2];
     double part[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (m < M) {
+    for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M_pad; m += (int64_t)gridDim.x * NT) {
+        if (m >= M) {
+            set_rec(fr, m, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
+            continue;
+        }
         const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
         int nx, ny, nz;
-        decode_h(idx, fs.Nx, fs.Ny, fs.Nzh, nx, ny, nz);
-        const double x = nx * tpx, y = ny * tpy, z = nz * tpz;
-        const double c = (nz == 0 || 2 * nz == fs.Nz) ? 1.0 : 2.0;
+        decode_h(idx, fs, nx, ny, nz);
+        const double xd = nx * tpx, yd = ny * tpy, zd = nz * tpz;
+        const R x = (R)xd, y = (R)yd, z = (R)zd;
+        const R c = (nz == 0 || 2 * nz == fs.Nz) ? (R)1 : (R)2;
         const Cx<R> F = spec[idx];
-        const double Gx = c * inv_VL * (double)F.x, Gy = c * inv_VL * (double)F.y;  // dL/dX
-        const double hh = exp(-0.5 * otf_expo(psf, kind, x, y, z));
-        const double norm = *d_norm;
-        const double ux = (double)S[m].x / norm, uy = (double)S[m].y / norm;  // u_hat
-        const double g = (Gx * ux + Gy * uy) * hh;                              // Re(conj(G) X)
+        const R Gx = c * cvl * F.x, Gy = c * cvl * F.y;  // dL/dX
+        const R hh = otf_r<R>(psf, kind, xd, yd, zd);
+        const Cx<R> Sm = S[m];
+        const R ux = Sm.x * rin, uy = Sm.y * rin;  // u_hat
+        const R g = (Gx * ux + Gy * uy) * hh;      // Re(conj(G) X)
         if (kind == 0) {
-            part[0] = -g * psf[0] * x * x;
-            part[1] = -g * psf[1] * y * y;
-            part[2] = -g * psf[2] * z * z;
+            part[0] += (double)(-g * s0 * x * x);
+            part[1] += (double)(-g * s1 * y * y);
+            part[2] += (double)(-g * s2 * z * z);
         } else {
-            part[0] = -0.5 * g * x * x;
-            part[1] = -0.5 * g * y * y;
-            part[2] = -0.5 * g * z * z;
-            part[3] = -g * x * y;
-            part[4] = -g * x * z;
-            part[5] = -g * y * z;
+            const R hg = (R)-0.5 * g;
+            part[0] += (double)(hg * x * x);
+            part[1] += (double)(hg * y * y);
+            part[2] += (double)(hg * z * z);
+            part[3] += (double)(-g * x * y);
+            part[4] += (double)(-g * x * z);
+            part[5] += (double)(-g * y * z);
         }
-        double Gur = Gx * hh / norm, Gui = Gy * hh / norm;  // dL/du_hat / norm
+        R Gur = Gx * hh * rin, Gui = Gy * hh * rin;  // dL/du_hat / norm
         const bool zero = nx == 0 && ny == 0 && nz == 0;
         if (zero) {
-            Gur = Gui = 0.0;  // u_hat(0) = 1 for every mesh: no gradient through xi = 0
+            Gur = Gui = (R)0;  // u_hat(0) = 1 for every mesh: no gradient through xi = 0
         } else {
-            part[6] = -(Gur * ux + Gui * uy);  // -cq
+            part[6] += (double)(-(Gur * ux + Gui * uy));  // -cq
         }
-        double wr = Gur, wi = Gui;
+        R wr = Gur, wi = Gui;
         if (mode == 1 && !zero) {  // volume: Gw = -i Gu / |xi|^2
-            const double ik2 = 1.0 / (x * x + y * y + z * z);
+            const R ik2 = (R)1 / (x * x + y * y + z * z);
             wr = Gui * ik2;
             wi = -Gur * ik2;
         }
-        set_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
-    } else if (m < M_pad) {
-        set_rec(fr, m, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
+        set_rec(fr, m, nx, ny, nz, xd, yd, zd, (double)wr, (double)wi);
     }
     for (int k = 0; k < 7; ++k) {
-        const double s = block_sum<NT>(part[k], scratch);
-        if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = s;
+        const double v = block_sum<NT>(part[k], scratch);
+        if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = v;
     }
     if (threadIdx.x == 0) partial[blockIdx.x * NPART + 7] = 0.0;
 }
@@ -568,10 +607,13 @@ cudaError_t launch_band(const double* d_psf, int psf_kind, double tau, int Nx, i
     b.psf = d_psf;
     b.kind = psf_kind;
     b.tau = tau;
+    b.e_max = -2.0 * log(tau);
     b.Nx = Nx;
     b.Ny = Ny;
     b.Nz = Nz;
     b.Nzh = Nz / 2 + 1;
+    b.div_zh = make_fastdiv((uint32_t)b.Nzh);
+    b.div_y = make_fastdiv((uint32_t)Ny);
     for (int a = 0; a < 3; ++a) b.tp[a] = 2.0 * M_PI / g.L[a];
     b.nH = (int64_t)Nx * Ny * b.Nzh;
     const unsigned nb = nblk(b.nH);
@@ -616,7 +658,7 @@ template <class R, class FR>
 cudaError_t launch_gather(int mode, const Cx<R>* spec, const Cx<R>* S, const FreqSrc& fs, const double* d_psf,
                           int psf_kind, const double* d_norm, const Geom& g, FR* fr, int64_t M_pad, double* partial,
                           int* n_blocks_out, cudaStream_t st) {
-    const unsigned b = nblk(M_pad);
+    const unsigned b = (unsigned)std::min<int64_t>(nblk(M_pad), 2048);  // grid-stride: one reduction per block
     *n_blocks_out = (int)b;
     const double VL = g.L[0] * g.L[1] * g.L[2];
     k_gather<R, FR><<<b, NT, 0, st>>>(mode, spec, S, fs, d_psf, psf_kind, d_norm, 2.0 * M_PI / g.L[0],
