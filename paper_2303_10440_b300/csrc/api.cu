@@ -425,7 +425,7 @@ dm_status dm_meshft(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* grid, const
     if (f64)
         LAUNCH(1, launch_fwd_f64(mesh->label, (const TriF64*)b.tris, mesh->n_t, fs, G, b.d_params + 16, (double2*)S, st));
     else
-        LAUNCH(1, launch_fwd_f32(mesh->label, (const TriF32*)b.tris, round_up(mesh->n_t, FWD_TILE), fs, G,
+        LAUNCH(1, launch_fwd_f32(mesh->label, (const TriF32*)b.tris, mesh->n_t, fs, G,
                                  b.d_params + 16, (float2*)S, nullptr, ctx->sm_count, ctx->d_err, st));
     if (!S_dev) {
         CK(cudaMemcpyAsync(S_out, b.S, M * 2 * R, cudaMemcpyDeviceToHost, st));

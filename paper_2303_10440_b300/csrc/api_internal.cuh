@@ -413,7 +413,7 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
     {
         Stage sg(ctx, DM_STAGE_FWD, st);
         if (sizeof(R) == 4)
-            LAUNCH(2, launch_fwd_f32(mode, (const TriF32*)b.tris, z.n_t_pad, fs, G, d_norm, (float2*)b.S,
+            LAUNCH(2, launch_fwd_f32(mode, (const TriF32*)b.tris, z.n_t, fs, G, d_norm, (float2*)b.S,
                                      (float2*)b.S_part, z.sm_count, ctx->d_err, st));
         else
             LAUNCH(1, launch_fwd_f64(mode, (const TriF64*)b.tris, z.n_t, fs, G, d_norm, (double2*)b.S, st));

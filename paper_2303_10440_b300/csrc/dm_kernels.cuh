@@ -100,7 +100,8 @@ struct Geom {
 // S_part (nullable): room for fwd_partial_elems(fs.M, sm_count) partial spectra; when given, a band with
 // fewer than about 8 x SMs frequency blocks splits the triangle list over several blocks and the
 // partial spectra are summed in a fixed order; when NULL every block takes the whole triangle list.
-cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const FreqSrc& fs, const Geom& g,
+// n_t: real triangles; the records are padded with zeros to whole 64-record tiles.
+cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, float2* S, float2* S_part, int sm_count, int* d_err, cudaStream_t st);
 size_t fwd_partial_elems(int64_t M_max, int sm_count);
 cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_t_pad, const FreqF32* fr,
@@ -111,6 +112,7 @@ int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count);
 struct BatchFwdJob {
     const TriF32* tris;
     int n_tiles;  // 64-record tiles
+    int last;     // real triangles in the last tile
     int mode;
     FreqSrc fs;
     float tp[3];

@@ -213,10 +213,12 @@ __device__ __forceinline__ void series_adj(F2 d1, F2 d2, F2& fr, F2& fi, F2& lr,
 }
 
 // ------------------------------------------------------------------------------------- forward
-// One forward block: band frequencies [bidx * 512, bidx * 512 + 512) against all triangles.
+// One forward block: band frequencies [bidx * 512, bidx * 512 + 512) against n_tiles tiles of
+// triangle records, of which the last holds `last` real triangles (the rest is padding, skipped).
 // Returns false (without touching the barriers) when the block lies beyond the band.
 template <int MODE, bool EXPLICIT>
-__device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n_tiles, const FreqSrc& fs, float tpx,
+__device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n_tiles, int last, const FreqSrc& fs,
+                                          float tpx,
                                           float tpy, float tpz, const double* __restrict__ d_vol,
                                           float2* __restrict__ S, int* __restrict__ err, int64_t bidx,
                                           TriF32 (*stage)[kFwdTile], uint64_t* full, uint64_t* empty,
@@ -250,10 +252,12 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
     const uint32_t uB0 = (uint32_t)n[1][0], uB1 = (uint32_t)n[1][1], uB2 = (uint32_t)n[1][2];
 
     F2 SX = mk(0.f, 0.f), SY = mk(0.f, 0.f), CX = mk(0.f, 0.f), CY = mk(0.f, 0.f);
+    int tile_no = 0;  // tiles arrive in order
     const auto consume = [&](const TriF32* tile) {
+        const int cnt = ++tile_no == n_tiles ? last : kFwdTile;
         F2 PX = mk(0.f, 0.f), PY = mk(0.f, 0.f);
         #pragma unroll 1
-        for (int j = 0; j < kFwdTile; ++j) {
+        for (int j = 0; j < cnt; ++j) {
             const TriF32& T = tile[j];
             const uint32_t PA = uA0 * T.U[0] + uA1 * T.U[1] + uA2 * T.U[2];
             const uint32_t PB = uB0 * T.U[0] + uB1 * T.U[1] + uB2 * T.U[2];
@@ -332,7 +336,8 @@ __device__ __forceinline__ void fwd_units(const FreqSrc& fs, int n_tiles, int ta
 }
 
 template <int MODE, bool EXPLICIT>
-__global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, FreqSrc fs,
+__global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_f32(const TriF32* __restrict__ tris, int n_tiles, int last,
+                                                         FreqSrc fs,
                                                          float tpx, float tpy, float tpz,
                                                          const double* __restrict__ d_vol, float2* __restrict__ S,
                                                          float2* __restrict__ S_part, int target,
@@ -348,8 +353,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_f32(const TriF32* __rest
     const int ts = (int)(u - b * splits);
     const int t0 = (int)((int64_t)n_tiles * ts / splits), t1 = (int)((int64_t)n_tiles * (ts + 1) / splits);
     float2* out = splits == 1 ? S : S_part + (int64_t)ts * M;
-    fwd_block<MODE, EXPLICIT>(tris + (int64_t)t0 * kFwdTile, t1 - t0, fs, tpx, tpy, tpz, d_vol, out, err, b, stage,
-                              full, empty, ts == 0);
+    fwd_block<MODE, EXPLICIT>(tris + (int64_t)t0 * kFwdTile, t1 - t0, t1 == n_tiles ? last : kFwdTile, fs, tpx, tpy,
+                              tpz, d_vol, out, err, b, stage, full, empty, ts == 0);
 }
 
 // S[m] = sum over the triangle splits of the partial spectra (fixed order, FP64); nothing when unsplit.
@@ -385,13 +390,17 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
     const int tid = threadIdx.x;
     const int64_t t = tblock * ADJ_THREADS + tid;
 
-    const TriF32 T = tris[t < n_t_pad ? t : 0];
+    // A padding lane evaluates the block's first triangle (its sums are dropped), so a part-padded
+    // warp branches like its real lanes; a warp of padding only skips the tiles.
+    const TriF32 T = tris[t < n_t ? t : tblock * ADJ_THREADS];
+    const bool idle = tblock * ADJ_THREADS + (tid & ~31) >= n_t;
     float tot[NACC], comp[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; ++k) tot[k] = comp[k] = 0.f;
 
     if (f1 > f0) {
         const auto consume = [&](const FreqPairF32* tile) {
+            if (idle) return;
             F2 part[NACC];
             #pragma unroll
             for (int k = 0; k < NACC; ++k) part[k] = mk(0.f, 0.f);
@@ -542,10 +551,10 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_batch_f32(const BatchFwdJob
         const BatchFwdJob& J = jobs[U.job];
         bool used;
         if (J.mode == 0)
-            used = fwd_block<0, false>(J.tris, J.n_tiles, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
+            used = fwd_block<0, false>(J.tris, J.n_tiles, J.last, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
                                        stage, full, empty);
         else
-            used = fwd_block<1, false>(J.tris, J.n_tiles, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
+            used = fwd_block<1, false>(J.tris, J.n_tiles, J.last, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
                                        stage, full, empty);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kFwdStages);
@@ -594,9 +603,10 @@ size_t fwd_partial_elems(int64_t M_max, int sm_count) {
     return (size_t)(fwd_target_units(sm_count) + fb) * FWD_BLOCK_FREQS;
 }
 
-cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const FreqSrc& fs, const Geom& g,
+cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, float2* S, float2* S_part, int sm_count, int* d_err, cudaStream_t st) {
-    const int n_tiles = (int)(n_t_pad / kFwdTile);
+    const int n_tiles = (int)((n_t + kFwdTile - 1) / kFwdTile);
+    const int last = (int)(n_t - (int64_t)(n_tiles - 1) * kFwdTile);
     const float tpx = (float)(2.0 * M_PI / g.L[0]), tpy = (float)(2.0 * M_PI / g.L[1]),
                 tpz = (float)(2.0 * M_PI / g.L[2]);
     const int64_t fb_max = (fs.M + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
@@ -607,13 +617,17 @@ cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t_pad, const 
     const dim3 grid((unsigned)blocks);
     const bool ex = fs.nlist != nullptr;
     if (mode == 0 && !ex)
-        k_fwd_f32<0, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+        k_fwd_f32<0, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, last, fs, tpx, tpy, tpz, d_vol, S, S_part,
+                                                          target, d_err);
     if (mode == 0 && ex)
-        k_fwd_f32<0, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+        k_fwd_f32<0, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, last, fs, tpx, tpy, tpz, d_vol, S, S_part,
+                                                         target, d_err);
     if (mode == 1 && !ex)
-        k_fwd_f32<1, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+        k_fwd_f32<1, false><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, last, fs, tpx, tpy, tpz, d_vol, S, S_part,
+                                                          target, d_err);
     if (mode == 1 && ex)
-        k_fwd_f32<1, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, fs, tpx, tpy, tpz, d_vol, S, S_part, target, d_err);
+        k_fwd_f32<1, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, last, fs, tpx, tpy, tpz, d_vol, S, S_part,
+                                                         target, d_err);
     if (S_part) k_fwd_reduce<<<4 * sm_count, 256, 0, st>>>(fs, n_tiles, target, S_part, S);
     return cudaGetLastError();
 }

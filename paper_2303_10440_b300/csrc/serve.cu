@@ -307,7 +307,8 @@ bool rebuild_units(dm_server* S) {
         const Geom G = make_geom(&J->grid);
         BatchFwdJob& f = S->fj[j];
         f.tris = (const TriF32*)b.tris;
-        f.n_tiles = (int)(z.n_t_pad / FWD_REC_TILE);
+        f.n_tiles = (int)((z.n_t + FWD_REC_TILE - 1) / FWD_REC_TILE);
+        f.last = (int)(z.n_t - (int64_t)(f.n_tiles - 1) * FWD_REC_TILE);
         f.mode = J->label;
         f.fs.nlist = nullptr;
         f.fs.idx = z.band ? b.band_idx : nullptr;
