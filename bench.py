@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--rounds", type=int, default=4, help="staggered rounds in the stagger mode")
     p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 10)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
+    p.add_argument("--rates", default="10,20,50,100,200,500", help="Poisson arrival rates (1/s) in serve-c5")
+    p.add_argument("--capacity-fracs", default="0.25,0.5,1",
+                   help="serve-c5 arrival rates as fractions of the measured saturated throughput ('' for none)")
     return p.parse_args()
 
 
@@ -560,6 +563,12 @@ def _job_terms(j):
     return 2.0 * n[0] * n[1] * (n[2] // 2 + 1) * j["F"].shape[0] * j["steps"]
 
 
+def _poisson_arrivals(rate, n, seed=7):
+    """Open-loop arrival times: exponential gaps at `rate` per second, the first request at t = 0."""
+    a = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=n))
+    return a - a[0]
+
+
 def _one_at_a_time(r, jobs, dev):
     import torch
 
@@ -629,20 +638,18 @@ def run_serve_mode(args):
             jobs.append(dict(V=c["V_init"], F=c["F"], target=T, grid=c["grid"], psf=c["psf"], steps=steps,
                              lr_vertex=1e-2 * min(c["grid"].h)))
         workload = (f"{len(jobs)} serving requests (levels 2-6 = 320-81920 triangles, cubic grids 64-256 of "
-                    f"(0.5, 0.5, 1) um, random anisotropic sigma), {steps} Adam steps each (reduced from 100 to bound "
-                    f"the run), open-loop Poisson arrivals")
-        rates = {}
-        for rate in (10.0, 100.0, 500.0):
-            r = np.random.default_rng(7)
-            a = np.cumsum(r.exponential(1.0 / rate, size=len(jobs)))
-            rates[f"{rate:g}/s"] = a - a[0]
+                    f"(0.5, 0.5, 1) um, random anisotropic sigma), {steps} Adam steps each (reduced from 100, and "
+                    f"from ~200 requests, to bound the run), open-loop Poisson arrivals")
+        rates = {f"{rate:g}/s": _poisson_arrivals(rate, len(jobs)) for rate in
+                 (float(x) for x in args.rates.split(",") if x)}
     total_terms = sum(_job_terms(j) for j in jobs)
     durs = _one_at_a_time(r32, jobs, dev)
     fp64 = _fp64_rate(jobs, dev)
     out = {"metric": "served fits/s and p50/p99 latency vs one-at-a-time FP32 and plain FP64", "mode": args.mode,
            "workload": workload, "n_jobs": len(jobs), "total_terms": total_terms, "results": {}}
     fp64_durs = [_job_terms(j) / fp64 for j in jobs]
-    for name, arr in rates.items():
+
+    def legs(arr, rate=None):
         served = _served_run(jobs, arr, dev)
         served["terms_per_s"] = total_terms / served["span_s"]
         # least-remaining-work scheduling within a per-iteration term budget (about 10 ms of work)
@@ -650,12 +657,26 @@ def run_serve_mode(args):
         shortest["terms_per_s"] = total_terms / shortest["span_s"]
         lat, span = _queue_latencies(arr, durs)
         lat64, span64 = _queue_latencies(arr, fp64_durs)
-        out["results"][name] = {
+        e = {
             "served_fp32": served,
             "served_fp32_shortest_first": shortest,
             "sequential_fp32": dict(_stats(lat, span, len(jobs)), terms_per_s=total_terms / span),
             "plain_fp64_from_measured_rate": dict(_stats(lat64, span64, len(jobs)), terms_per_s=fp64),
         }
+        if rate is not None:
+            e["arrival_rate_per_s"] = rate
+        return e
+
+    for name, arr in rates.items():
+        out["results"][name] = legs(arr)
+    fracs = [float(x) for x in args.capacity_fracs.split(",") if x] if args.mode == "serve-c5" else []
+    if fracs:
+        # capacity = the best served throughput seen at the saturating rates above
+        cap = max(max(e["served_fp32"]["fits_per_s"], e["served_fp32_shortest_first"]["fits_per_s"])
+                  for e in out["results"].values())
+        out["capacity_fits_per_s"] = cap
+        for f in fracs:
+            out["results"][f"{f:g}x capacity"] = legs(_poisson_arrivals(f * cap, len(jobs)), rate=f * cap)
     out["plain_fp64_terms_per_s_measured"] = fp64
     print(json.dumps(out), flush=True)
 

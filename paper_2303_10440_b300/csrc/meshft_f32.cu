@@ -141,6 +141,36 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
     }
 }
 
+// Forward middle-frame value f_m = i (E(d2) - conj E(d1)) / s (both lanes) over one common
+// denominator. With N = d E = (sin d, cos d - 1) and c = d for a gap >= TG, and N = E (Taylor),
+// c = 1 for the (at most one) gap below TG: E(d2) - conj E(d1) = (c1 N2 - c2 conj N1) / (c1 c2), so
+// f_m = i (c1 N2 - c2 conj N1) / (c1 c2 s) takes one reciprocal per lane instead of three. The
+// denominator is >= TG^2 TS where the lane keeps this value (s >= TS); lanes with s < TS are
+// replaced by the series. Returns f_m = -fmr + i fmi.
+__device__ __forceinline__ void fm_closed(F2 d1, F2 d2, F2 s, F2& fmr, F2& fmi) {
+    float s1a, c1a, s1b, c1b, s2a, c2a, s2b, c2b;
+    __sincosf(d1.x, &s1a, &c1a);
+    __sincosf(d1.y, &s1b, &c1b);
+    __sincosf(d2.x, &s2a, &c2a);
+    __sincosf(d2.y, &s2b, &c2b);
+    const bool m1a = d1.x < TG, m1b = d1.y < TG, m2a = d2.x < TG, m2b = d2.y < TG;
+    const F2 dm = mk(fminf(d1.x, d2.x), fminf(d1.y, d2.y));
+    const F2 tm = mul2(dm, dm);
+    F2 pr, pi;
+    taylor2(tm, pr, pi);
+    const F2 one = mk(1.f, 1.f), mone = mk(-1.f, -1.f);
+    const F2 Etx = fma2(tm, pr, one), Ety = mul2(dm, pi);
+    const F2 c1 = sel2(m1a, m1b, one, d1), c2 = sel2(m2a, m2b, one, d2);
+    const F2 N1x = sel2(m1a, m1b, Etx, mk(s1a, s1b)), N1y = sel2(m1a, m1b, Ety, add2(mk(c1a, c1b), mone));
+    const F2 N2x = sel2(m2a, m2b, Etx, mk(s2a, s2b)), N2y = sel2(m2a, m2b, Ety, add2(mk(c2a, c2b), mone));
+    const F2 den = mul2(mul2(c1, c2), s);
+    const F2 R = mk(rcpa(den.x), rcpa(den.y));
+    // c1 N2 - c2 conj N1 = (c1 N2x - c2 N1x) + i (c1 N2y + c2 N1y); times i R
+    const F2 nx = fms2(c1, N2x, mul2(c2, N1x)), ny = fma2(c1, N2y, mul2(c2, N1y));
+    fmr = mul2(ny, R);
+    fmi = mul2(nx, R);
+}
+
 // Middle-frame series for terms whose three phases lie within TS (s < TS). With the nodes
 // (-d1, 0, d2) relative to the middle phase and F(x) = -e^{-ix}, the divided differences are
 // sums over the complete homogeneous symmetric polynomials h_k of the nonzero nodes:
@@ -270,15 +300,12 @@ __device__ __forceinline__ bool fwd_block(const TriF32* __restrict__ tris, int n
             const F2 s = sub2(hi, lo);
             const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
             const F2 phm = add2(ph, mid);
-            Gaps<false> g;
-            gaps2<false>(d1, d2, s, g);
+            F2 fmr, fmi;
+            fm_closed(d1, d2, s, fmr, fmi);
             float sma, cma, smb, cmb;
             __sincosf(phm.x, &sma, &cma);
             __sincosf(phm.y, &smb, &cmb);
             const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
-            // f_m = i (E2 - conj E1) / s = -fmr + i fmi with gx = E2x - E1x, gy = E2y + E1y
-            const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
-            F2 fmr = mul2(gy, g.invs), fmi = mul2(gx, g.invs);
             if (s.x < TS || s.y < TS) {
                 // three phases within TS: the series in the same frame (warp-divergent, rare)
                 F2 sr, si;

@@ -180,6 +180,29 @@ def test_loss_and_grad_matches_oracle(kind, mode, prec, r64, r32):
     assert rel(dpsf.numpy(), dpsf0) < tg
 
 
+@pytest.mark.parametrize("mesh", ["ico0_20", "ico1_80", "soup_130"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_meshes_over_many_chunks(mesh, prec, r64, r32):
+    """Meshes of 20, 80 and 130 triangles on a 64^3 grid: one partial record tile, a part-padding
+    warp, and a triangle block that is almost all padding; the adjoint runs ~500 frequency chunks
+    per triangle block and sums them in the chunk reduction."""
+    grid = synth.Grid(n=(64, 64, 64), h=(0.5, 0.5, 1.0))
+    if mesh == "soup_130":
+        V, F = synth.random_triangles(130, seed=5, extent=6.0, center=grid.center)
+    else:
+        V, F = synth.sphere_mesh(int(mesh[3]), 6.0, grid.center)
+    psf = synth.Psf(sigma=(0.3, 0.3, 0.8), band_tau=1e-3)
+    T = oracle.render(synth.scale_about(V, (1.05, 0.97, 1.0), grid.center), F, grid, psf)["image"]
+    L0, dV0, dpsf0, r0 = oracle.loss_and_grad(V, F, grid, psf, T, "mse")
+    r = r64 if prec == "fp64" else r32
+    L, dV, dpsf, img = r.loss_and_grad(_cuda(V), _cuda(F), grid, psf, _cuda(T), "mse", want_image=True)
+    ti, tl, tg = (1e-10, 1e-10, 1e-9) if prec == "fp64" else (1e-4, 2e-4, 1e-3)
+    assert rel(img.cpu().numpy(), r0["image"]) < ti
+    assert abs(L - L0) <= tl * abs(L0)
+    assert rel(dV.cpu().numpy(), dV0) < tg
+    assert rel(dpsf.numpy(), dpsf0) < tg
+
+
 def test_case1_fp64_matches_oracle(r64):
     case = synth.config_c1()
     T = oracle.render(case.V_true, case.F, case.grid, case.psf)["image"]
