@@ -411,7 +411,8 @@ template <int MODE>
 __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64_t n_t, int64_t n_t_pad,
                                           const FreqPairF32* __restrict__ fr, int f0, int f1, int64_t tblock,
                                           float* __restrict__ out_chunk, int* __restrict__ err,
-                                          FreqPairF32 (*stage)[kAdjPairs], uint64_t* full, uint64_t* empty) {
+                                          FreqPairF32 (*stage)[kAdjPairs], uint64_t* full, uint64_t* empty,
+                                          float* acc_s) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
     constexpr int PAIRS = kAdjPairs;
     const int tid = threadIdx.x;
@@ -421,9 +422,15 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
     // warp branches like its real lanes; a warp of padding only skips the tiles.
     const TriF32 T = tris[t < n_t ? t : tblock * ADJ_THREADS];
     const bool idle = tblock * ADJ_THREADS + (tid & ~31) >= n_t;
-    float tot[NACC], comp[NACC];
+    // edge vectors held once per thread (the record stores each field twice for paired loads from
+    // shared memory; here in registers the pairs are rebuilt at each use: 4-5 registers fewer, ~1%)
+    const float e21[3] = {T.e21x.x, T.e21y.x, T.e21z.x}, e31[3] = {T.e31x.x, T.e31y.x, T.e31z.x};
+    // the triangle's running sums and their compensations live in shared memory (each thread its
+    // own column), touched once per tile: 20-24 registers fewer in the frequency loop
+    float* tot = acc_s + tid;
+    float* comp = acc_s + NACC * ADJ_THREADS + tid;
 #pragma unroll
-    for (int k = 0; k < NACC; ++k) tot[k] = comp[k] = 0.f;
+    for (int k = 0; k < NACC; ++k) tot[k * ADJ_THREADS] = comp[k * ADJ_THREADS] = 0.f;
 
     if (f1 > f0) {
         const auto consume = [&](const FreqPairF32* tile) {
@@ -438,8 +445,8 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
             const uint32_t PB = (uint32_t)R.nB[0] * T.U[0] + (uint32_t)R.nB[1] * T.U[1] + (uint32_t)R.nB[2] * T.U[2];
             const F2 ph = mul2(mk((float)(int32_t)PA, (float)(int32_t)PB), mk(kTwoPiOver2p32, kTwoPiOver2p32));
             const F2 X = R.x, Y = R.y, Z = R.z;
-            const F2 a = fma2(Z, T.e21z, fma2(Y, T.e21y, mul2(X, T.e21x)));
-            const F2 b = fma2(Z, T.e31z, fma2(Y, T.e31y, mul2(X, T.e31x)));
+            const F2 a = fma2(Z, mk(e21[2], e21[2]), fma2(Y, mk(e21[1], e21[1]), mul2(X, mk(e21[0], e21[0]))));
+            const F2 b = fma2(Z, mk(e31[2], e31[2]), fma2(Y, mk(e31[1], e31[1]), mul2(X, mk(e31[0], e31[0]))));
             const Order oA = order3(a.x, b.x), oB = order3(a.y, b.y);
             const F2 lo = mk(oA.lo, oB.lo), hi = mk(oA.hi, oB.hi), mid = mk(oA.mid, oB.mid);
             const F2 s = sub2(hi, lo);
@@ -521,14 +528,19 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
             part[B + 8] = fma2(tv3, Z, part[B + 8]);
             }
             #pragma unroll
-            for (int k = 0; k < NACC; ++k) kahan_add(tot[k], comp[k], part[k].x + part[k].y);
+            for (int k = 0; k < NACC; ++k) {
+                float sk = tot[k * ADJ_THREADS], ck = comp[k * ADJ_THREADS];
+                kahan_add(sk, ck, part[k].x + part[k].y);
+                tot[k * ADJ_THREADS] = sk;
+                comp[k * ADJ_THREADS] = ck;
+            }
         };
         run_tile_pipeline<kAdjStages, kAdjPairs>(fr + (int64_t)f0 * PAIRS, f1 - f0, stage, full, empty, err, consume);
     }
     if (t < n_t_pad) {
         float* out = out_chunk + t;
 #pragma unroll
-        for (int k = 0; k < NACC; ++k) out[(int64_t)k * n_t_pad] = t < n_t ? tot[k] : 0.f;
+        for (int k = 0; k < NACC; ++k) out[(int64_t)k * n_t_pad] = t < n_t ? tot[k * ADJ_THREADS] : 0.f;
     }
     return f1 > f0;
 }
@@ -547,8 +559,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     const int tpc = (n_ftiles + (int)gridDim.y - 1) / (int)gridDim.y;
     const int f0 = blockIdx.y * tpc;
     const int f1 = min(f0 + tpc, n_ftiles);
+    __shared__ float acc_s[2 * NACC * ADJ_THREADS];
     adj_block<MODE>(tris, n_t, n_t_pad, fr, f0, f1, blockIdx.x, partial + (int64_t)blockIdx.y * NACC * n_t_pad, err,
-                    stage, full, empty);
+                    stage, full, empty, acc_s);
 }
 
 // ------------------------------------------------------------------------------------- batched
@@ -596,6 +609,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_batch_f32(const BatchAdjJob
     __shared__ __align__(128) FreqPairF32 stage[kAdjStages][kAdjPairs];
     __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
     __shared__ int s_u;
+    __shared__ float acc_s[2 * NACC_VOL * ADJ_THREADS];
     while (true) {
         if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
         __syncthreads();
@@ -612,9 +626,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_batch_f32(const BatchAdjJob
         float* out = J.partial + (int64_t)U.b * nacc * J.n_t_pad;
         bool used;
         if (J.mode == 0)
-            used = adj_block<0>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty);
+            used = adj_block<0>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty, acc_s);
         else
-            used = adj_block<1>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty);
+            used = adj_block<1>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty, acc_s);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kAdjStages);
         __syncthreads();
