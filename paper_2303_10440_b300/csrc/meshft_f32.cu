@@ -95,18 +95,16 @@ __device__ __forceinline__ float rcpa(float x) {
     return r;
 }
 
-// Gap functions for both lanes of both gaps: E(d1), E(d2) and (adjoint) q(d1), q(d2).
+// Adjoint gap functions for both lanes of both gaps: E(d1), E(d2), q(d1), q(d2) and 1/s.
 // Since s = d1 + d2 >= TS >= 2 TG here, at most one gap per lane is below TG, so a single
 // Taylor evaluation on min(d1, d2) serves whichever gap needs it.
 static_assert(MathCfg<float>::TS >= 2.0f * MathCfg<float>::TG, "one Taylor evaluation per term needs TS >= 2 TG");
-template <bool ADJ>
 struct Gaps {
     F2 E1x, E1y, E2x, E2y;
     F2 q1x, q1y, q2x, q2y;
     F2 invs;
 };
-template <bool ADJ>
-__device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
+__device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps& g) {
     float s1a, c1a, s1b, c1b, s2a, c2a, s2b, c2b;
     __sincosf(d1.x, &s1a, &c1a);
     __sincosf(d1.y, &s1b, &c1b);
@@ -131,7 +129,7 @@ __device__ __forceinline__ void gaps2(F2 d1, F2 d2, F2 s, Gaps<ADJ>& g) {
     g.E1y = sel2(m1a, m1b, Ety, E1yd);
     g.E2x = sel2(m2a, m2b, Etx, E2xd);
     g.E2y = sel2(m2a, m2b, Ety, E2yd);
-    if (ADJ) {
+    {
         // Taylor: Re q = d pr, Im q = pi ; direct: q = (E - 1)/d
         const F2 qtx = mul2(dm, pr);
         g.q1x = sel2(m1a, m1b, qtx, mul2(add2(E1xd, mone), inv1));
@@ -454,8 +452,8 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
             {
                 const F2 d1 = sub2(mid, lo), d2 = sub2(hi, mid);
                 const F2 phm = add2(ph, mid);
-                Gaps<true> g;
-                gaps2<true>(d1, d2, s, g);
+                Gaps g;
+                gaps2(d1, d2, s, g);
                 float sma, cma, smb, cmb;
                 __sincosf(phm.x, &sma, &cma);
                 __sincosf(phm.y, &smb, &cmb);
