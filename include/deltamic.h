@@ -82,7 +82,9 @@ typedef struct {
     int32_t precision;     /* DM_FP64 or DM_FP32_MIXED */
     int32_t device;        /* CUDA device ordinal */
     int32_t deterministic; /* reductions are always deterministic; kept for ABI growth */
-    int32_t reserved;
+    int32_t no_graphs;     /* 0: dm_fit / dm_fit_resume capture one optimisation step as a CUDA graph
+                            * and replay it; 1: enqueue every step's kernels one by one. Results are
+                            * bitwise identical either way. */
 } dm_options;
 
 typedef struct {

@@ -32,7 +32,7 @@ OPTIMIZERS = {"adam": 0, "large_steps": 1}
 
 
 class dm_options(ctypes.Structure):
-    _fields_ = [("precision", c_i32), ("device", c_i32), ("deterministic", c_i32), ("reserved", c_i32)]
+    _fields_ = [("precision", c_i32), ("device", c_i32), ("deterministic", c_i32), ("no_graphs", c_i32)]
 
 
 class dm_grid(ctypes.Structure):

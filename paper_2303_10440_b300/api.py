@@ -84,12 +84,15 @@ class Renderer:
     precision: "fp32" (FP32 mixed path: float images) or "fp64" (plain FP64 path).
     """
 
-    def __init__(self, precision: str = "fp32", device: int = 0):
+    def __init__(self, precision: str = "fp32", device: int = 0, graphs: bool = True):
+        """graphs: fits replay one captured CUDA graph per optimisation step (False: enqueue each step's
+        kernels one by one; the results are bitwise the same)."""
         self.lib = _lib.load()
         self.precision = precision
         self.real = torch.float32 if precision == "fp32" else torch.float64
         self.cplx = torch.complex64 if precision == "fp32" else torch.complex128
-        opt = _lib.dm_options(_lib.DM_FP32_MIXED if precision == "fp32" else _lib.DM_FP64, int(device), 1, 0)
+        opt = _lib.dm_options(_lib.DM_FP32_MIXED if precision == "fp32" else _lib.DM_FP64, int(device), 1,
+                              0 if graphs else 1)
         h = ctypes.c_void_p()
         st = self.lib.dm_create(ctypes.byref(h), ctypes.byref(opt))
         if st != _lib.DM_OK:

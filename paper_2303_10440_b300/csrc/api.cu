@@ -146,6 +146,7 @@ dm_status dm_create(dm_ctx** out, const dm_options* opt) {
         }
         ctx->precision = opt->precision;
         ctx->device = opt->device;
+        ctx->graphs = opt->no_graphs == 0;
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ctx->device < 0 || ctx->device >= ndev) {
@@ -173,6 +174,7 @@ dm_status dm_destroy(dm_ctx* ctx) {
     if (ctx->d_err) cudaFree(ctx->d_err);
     for (auto& kv : ctx->tw32) cudaFree(kv.second);
     for (auto& kv : ctx->tw64) cudaFree(kv.second);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
     for (auto& p : ctx->pending) {
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
@@ -605,12 +607,14 @@ dm_status dm_fit_resume(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* 
     const int64_t nV = 3 * mesh->n_v;
     A.take<double>(2 * nV + 8);  // Adam moments of V and sigma
     A.take<double>(opt->steps);
+    A.take<int64_t>(1);
     if ((s = ensure_ws(ctx, A.off + 256)) != DM_OK) return s;
     A.base = ctx->ws;
     A.off = 0;
     layout(z, A, b, true, !F_dev, W_host, !T_dev, false);
     double* mom = A.take<double>(2 * nV + 8);
     double* hist = A.take<double>(opt->steps);
+    int64_t* d_step = A.take<int64_t>(1);  // Adam step t of the running iteration
     double *mV = mom, *vV = mom + nV, *ms = mom + 2 * nV, *vs = ms + 4;
 
     // the fit owns a device copy of V
@@ -650,20 +654,48 @@ dm_status dm_fit_resume(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* 
     out.image = nullptr;
     out.dV = b.dV;
     out.want_grad = true;
-    for (int it = 0; it < opt->steps; ++it) {
-        if (f64)
-            s = pipeline<double>(ctx, z, b, in, psf_io, grid, JOB_LOSS, out, st, true);
-        else
-            s = pipeline<float>(ctx, z, b, in, psf_io, grid, JOB_LOSS, out, st, true);
-        if (s != DM_OK) return s;
-        CK(cudaMemcpyAsync(hist + it, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToDevice, st));
-        Stage sg(ctx, DM_STAGE_ADAM, st);
-        LAUNCH(1, launch_adam(b.V, b.dV, mV, vV, nV, opt->lr_vertex, opt->beta1, opt->beta2, opt->eps,
-                              step0 + it + 1, st));
+    const int64_t t_first = step0 + 1;
+    CK(cudaMemcpyAsync(d_step, &t_first, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    // One optimisation step, identical on every iteration: the Adam step t lives on the device and
+    // the closing tick stores the loss at hist[t - step0 - 1] and advances t.
+    const auto fit_step = [&](cudaStream_t q) -> dm_status {
+        const dm_status r = f64 ? pipeline<double>(ctx, z, b, in, psf_io, grid, JOB_LOSS, out, q, true)
+                                : pipeline<float>(ctx, z, b, in, psf_io, grid, JOB_LOSS, out, q, true);
+        if (r != DM_OK) return r;
+        Stage sg(ctx, DM_STAGE_ADAM, q);
+        LAUNCH(1, launch_adam_dev_step(b.V, b.dV, mV, vV, nV, opt->lr_vertex, opt->beta1, opt->beta2, opt->eps,
+                                       d_step, q));
         if (opt->lr_psf > 0)
-            LAUNCH(1, launch_adam(b.d_params, b.d_params + 24, ms, vs, 3, opt->lr_psf, opt->beta1, opt->beta2,
-                                  opt->eps, step0 + it + 1, st));
+            LAUNCH(1, launch_adam_dev_step(b.d_params, b.d_params + 24, ms, vs, 3, opt->lr_psf, opt->beta1,
+                                           opt->beta2, opt->eps, d_step, q));
+        LAUNCH(1, launch_fit_tick(hist, b.d_params + 17, d_step, step0, q));
+        return DM_OK;
+    };
+    // The first step runs directly: it also creates the FFT tables and raises kernel attributes,
+    // which a capture must not do.
+    if ((s = fit_step(st)) != DM_OK) return s;
+    int it = 1;
+    if (ctx->graphs && !ctx->prof && opt->steps >= 3) {
+        cudaGraphExec_t ge = nullptr;
+        const int64_t l0 = g_launches;
+        if (capture_graph(ctx, fit_step, &ge)) {
+            const int64_t per = g_launches - l0;
+            g_launches = l0;
+            for (; it < opt->steps; ++it) {
+                const cudaError_t le = cudaGraphLaunch(ge, st);
+                if (le != cudaSuccess) {
+                    cudaGraphExecDestroy(ge);
+                    return fail(ctx, DM_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(le));
+                }
+                g_launches += per;
+            }
+            cudaGraphExecDestroy(ge);  // freed once the launches in flight complete
+        } else {
+            g_launches = l0;  // the capture failed; the remaining steps run directly
+        }
     }
+    for (; it < opt->steps; ++it)
+        if ((s = fit_step(st)) != DM_OK) return s;
     CK(cudaMemcpyAsync(V_io, b.V, nV * sizeof(double), cudaMemcpyDefault, st));
     double sig[3];
     CK(cudaMemcpyAsync(sig, b.d_params, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));

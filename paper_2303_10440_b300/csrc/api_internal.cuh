@@ -30,6 +30,8 @@ struct dm_ctx {
     char* ws = nullptr;
     size_t ws_cap = 0;
     std::map<int, void*> tw32, tw64;  // FFT twiddle tables per length
+    bool graphs = true;               // replay captured fit steps (dm_options.no_graphs == 0)
+    cudaStream_t cap = nullptr;       // stream used only to capture graphs (nothing runs on it)
     // stage timing
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -96,6 +98,39 @@ struct Stage {
         }
     }
 };
+
+// Captures body(stream) into an executable CUDA graph on the context's capture stream, in thread-
+// local capture mode (other threads' CUDA calls are unaffected); nothing runs during the capture.
+// Returns false, leaving no error state behind, when the capture or the instantiation fails; the
+// caller then runs the body directly.
+template <class Body>
+bool capture_graph(dm_ctx* ctx, const Body& body, cudaGraphExec_t* exec) {
+    *exec = nullptr;
+    if (!ctx->cap && cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cap = nullptr;
+        return false;
+    }
+    if (cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const std::string err0 = ctx->err;
+    const dm_status bs = body(ctx->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &g);
+    bool ok = bs == DM_OK && ce == cudaSuccess && g != nullptr;
+    if (ok && cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+        ok = false;
+        *exec = nullptr;
+    }
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        ctx->err = err0;
+    }
+    return ok;
+}
 
 struct DeviceGuard {
     int prev = -1;

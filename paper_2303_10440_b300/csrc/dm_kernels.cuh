@@ -238,6 +238,8 @@ cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_
                         double eps, int64_t step, cudaStream_t st);
 cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1,
                                  double b2, double eps, const int64_t* d_step, cudaStream_t st);
+// hist[*d_step - step0 - 1] = *d_loss; ++*d_step (one thread)
+cudaError_t launch_fit_tick(double* hist, const double* d_loss, int64_t* d_step, int64_t step0, cudaStream_t st);
 
 // FFT (own radix-2/3/4/5 Stockham in shared memory).
 struct FFTAxis {

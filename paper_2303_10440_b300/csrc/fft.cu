@@ -8,6 +8,7 @@
 // the Hermitian-completed line (real parts of the self-conjugate n_z = 0 and
 // Nyquist coefficients) before a complex inverse transform; the z pass of the
 // forward keeps the first Nz/2+1 outputs. All transforms are unnormalised.
+#include <atomic>
 #include <cmath>
 
 #include "dm_kernels.cuh"
@@ -260,10 +261,23 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* s
     }
 }
 
-template <class R>
-cudaError_t set_smem(const void* fn, size_t bytes) {
+// Raises kernel FN's dynamic shared-memory limit to the device's opt-in maximum, once per device,
+// so that later launches (also those captured into a CUDA graph) need no attribute call.
+template <auto FN>
+cudaError_t set_smem(size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    static std::atomic<int> raised[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && raised[dev].load() != 0) return cudaSuccess;
+    int max_smem = 0;
+    if ((e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    if (bytes > (size_t)max_smem) return cudaErrorInvalidValue;
+    if ((e = cudaFuncSetAttribute((const void*)FN, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem)) != cudaSuccess)
+        return e;
+    if (dev < 64) raised[dev].store(1);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -297,15 +311,15 @@ cudaError_t run_pass(PassKind kind, const void* src, void* dst, const FFTAxis& a
     const size_t sm = fft_smem_bytes(N, sizeof(Cx<R>));
     cudaError_t e;
     if (kind == PASS_STRIDED) {
-        if ((e = set_smem<R>((const void*)k_fft_strided<R, NC>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem<k_fft_strided<R, NC>>(sm)) != cudaSuccess) return e;
         const int64_t blocks = outer * ((inner + nl - 1) / nl);
         k_fft_strided<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((Cx<R>*)dst, ax, inner, dir);
     } else if (kind == PASS_Z_C2R) {
-        if ((e = set_smem<R>((const void*)k_fft_z_c2r<R, NC>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem<k_fft_z_c2r<R, NC>>(sm)) != cudaSuccess) return e;
         const int64_t blocks = (outer + nl - 1) / nl;
         k_fft_z_c2r<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const Cx<R>*)src, (R*)dst, ax, Nzh, outer);
     } else {
-        if ((e = set_smem<R>((const void*)k_fft_z_r2c<R, NC>, sm)) != cudaSuccess) return e;
+        if ((e = set_smem<k_fft_z_r2c<R, NC>>(sm)) != cudaSuccess) return e;
         const int64_t blocks = (outer + nl - 1) / nl;
         k_fft_z_r2c<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const R*)src, (Cx<R>*)dst, ax, Nzh, outer);
     }

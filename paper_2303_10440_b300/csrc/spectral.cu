@@ -593,6 +593,17 @@ __global__ void __launch_bounds__(NT) k_adam(double* __restrict__ p, const doubl
     p[i] -= lr * mh / (sqrt(vh) + eps);
 }
 
+// End of one fit step: hist[t - step0 - 1] = loss of the step, then t += 1 (t: the Adam step on the
+// device, so that one captured step replays unchanged).
+__global__ void k_fit_tick(double* __restrict__ hist, const double* __restrict__ d_loss, int64_t* __restrict__ d_step,
+                           int64_t step0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int64_t t = *d_step;
+        hist[t - step0 - 1] = *d_loss;
+        *d_step = t + 1;
+    }
+}
+
 __global__ void k_set_params(double* dst, Params16 p, int n) {
     if (threadIdx.x < n) dst[threadIdx.x] = p.v[threadIdx.x];
 }
@@ -760,6 +771,11 @@ cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_
 cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1,
                                  double b2, double eps, const int64_t* d_step, cudaStream_t st) {
     k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, 0, d_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit_tick(double* hist, const double* d_loss, int64_t* d_step, int64_t step0, cudaStream_t st) {
+    k_fit_tick<<<1, 32, 0, st>>>(hist, d_loss, d_step, step0);
     return cudaGetLastError();
 }
 
