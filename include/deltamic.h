@@ -367,6 +367,8 @@ typedef struct {
     int32_t optimizer;     /* vertex optimiser: DM_OPT_ADAM or DM_OPT_LARGE_STEPS (uniform Adam on
                               u = (1 + lambda L) v, FP32 smoothing solves, tolerance 1e-6) */
     double lambda;         /* large-steps smoothing weight (<= 0: 50) */
+    double lr_decay;       /* step t (from 1, continuing across resume) uses fit.lr_vertex * lr_decay^(t-1)
+                              and likewise lr_psf; 0 or 1: constant rates; otherwise in (0, 1) */
     const dm_fit_state* resume; /* NULL, or the state of a preempted job (copied at submit): V is then
                               that job's vertices and fit.steps the steps still to take */
 } dm_job;

@@ -117,6 +117,7 @@ class dm_job(ctypes.Structure):
         ("label", c_i32),
         ("optimizer", c_i32),
         ("lam", c_f64),
+        ("lr_decay", c_f64),
         ("resume", ctypes.POINTER(dm_fit_state)),
     ]
 

@@ -91,6 +91,7 @@ struct SJob {
     int label = DM_SURFACE;
     int optimizer = DM_OPT_ADAM;
     double lambda = 50.0;
+    double lr_decay = 1.0;  // per-step factor on the learning rates
     int state = DM_JOB_QUEUED;
     int steps_done = 0;
     double terms_step = 0;  // triangle-frequency terms of one step (triangles x half-spectrum size)
@@ -457,23 +458,25 @@ bool iterate(dm_server* S, bool sync) {
         ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, js) ==
               cudaSuccess;
         const dm_fit_options& o = J->fit;
+        const int64_t t = J->step0 + J->steps_done + 1;  // Adam step (bias correction and rate schedule)
+        const double rate = J->lr_decay == 1.0 ? 1.0 : std::pow(J->lr_decay, (double)(t - 1));
         if (J->optimizer == DM_OPT_LARGE_STEPS) {
             // v -= (1 + lambda L)^-1 AdamUniform((1 + lambda L)^-1 dL/dv)
             ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, b.dV, J->gu, nullptr, J->pcg_work, 1e-6, 2000,
                                     J->cg_stats, js) == cudaSuccess;
-            ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
-                                      J->step0 + J->steps_done + 1, J->aup, js) == cudaSuccess;
+            ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex * rate, o.beta1, o.beta2,
+                                      o.eps, t, J->aup, js) == cudaSuccess;
             ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, J->dl, J->wv, b.V, J->pcg_work, 1e-6, 2000,
                                     J->cg_stats, js) == cudaSuccess;
             g_launches += 7;
         } else {
-            ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
-                              J->step0 + J->steps_done + 1, js) == cudaSuccess;
+            ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex * rate, o.beta1, o.beta2, o.eps, t,
+                              js) == cudaSuccess;
             g_launches += 4;
         }
         if (o.lr_psf > 0) {
-            ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
-                              J->step0 + J->steps_done + 1, js) == cudaSuccess;
+            ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf * rate, o.beta1, o.beta2, o.eps,
+                              t, js) == cudaSuccess;
             g_launches += 1;
         }
         // the next iteration's batched launches on the server stream also follow this job's Adam
@@ -723,6 +726,7 @@ dm_status validate_job(const dm_job* j) {
             if (!(j->resume->sigma[a] > 0) || !std::isfinite(j->resume->sigma[a])) return DM_ERR_ARG;
     }
     if (std::isnan(j->lambda)) return DM_ERR_ARG;
+    if (!(j->lr_decay >= 0.0 && j->lr_decay <= 1.0)) return DM_ERR_ARG;
     for (int a = 0; a < 3; ++a) {
         if (!(j->psf.sigma[a] > 0) || !(j->grid.h[a] > 0) || j->grid.n[a] < 1) return DM_ERR_ARG;
         FFTAxis ax;
@@ -816,6 +820,7 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     }
     J->terms_step = (double)job->n_t * (double)job->grid.n[0] * job->grid.n[1] * (job->grid.n[2] / 2 + 1);
     J->lambda = job->lambda > 0 ? job->lambda : 50.0;
+    J->lr_decay = job->lr_decay > 0 ? job->lr_decay : 1.0;
     // a job whose state can never fit the arena is refused now rather than queued forever
     Sizes z = make_sizes(S->ctx, &job->grid, job->n_v, job->n_t, job->psf.band_tau > 0, job->label);
     const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;

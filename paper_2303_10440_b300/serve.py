@@ -53,9 +53,10 @@ class FitServer:
 
     def submit(self, V, F, target, grid, psf, steps: int, lr_vertex: float, lr_psf: float = 0.0, loss: str = "mse",
                label: str = "surface", beta1=0.9, beta2=0.999, eps=1e-20, optimizer: str = "adam",
-               lam: float = 50.0, resume: dict | None = None) -> int:
+               lam: float = 50.0, resume: dict | None = None, lr_decay: float = 1.0) -> int:
         """resume: the state dict of a preempted job (see preempt); V is then that job's vertices and
-        steps the steps still to take."""
+        steps the steps still to take. lr_decay: step t uses lr * lr_decay^(t-1) (t continues across
+        resume)."""
         V = np.ascontiguousarray(V, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.int32)
         T = np.ascontiguousarray(target, dtype=np.float32)
@@ -71,6 +72,7 @@ class FitServer:
         j.label = _lib.DM_VOLUME if label == "volume" else _lib.DM_SURFACE
         j.optimizer = _lib.OPTIMIZERS[optimizer]
         j.lam = float(lam)
+        j.lr_decay = float(lr_decay)
         keep = []
         if resume is not None:
             st = _lib.fit_state_struct(dict(resume), V.shape[0], keep)

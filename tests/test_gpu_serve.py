@@ -225,15 +225,17 @@ def test_shortest_policy_runs_small_jobs_first_with_unchanged_results(setup):
     assert len(rb.loss_history) == 30 and rb.loss_history[-1] < rb.loss_history[0]
 
 
-@pytest.mark.parametrize("optimizer,lr", [("adam", 0.02), ("large_steps", 0.5)])
-def test_preempted_job_resumes_bit_for_bit(setup, optimizer, lr):
+@pytest.mark.parametrize("optimizer,lr,decay", [("adam", 0.02, 1.0), ("large_steps", 0.5, 1.0),
+                                               ("large_steps", 0.5, 0.9)])
+def test_preempted_job_resumes_bit_for_bit(setup, optimizer, lr, decay):
     """Checkpoint / resume in the server: stop a running job, resubmit it with its state, and the result
-    equals the uninterrupted run (vertices and the remaining losses)."""
+    equals the uninterrupted run (vertices and the remaining losses); a decaying rate continues from
+    the checkpoint's step."""
     from paper_2303_10440_b300.serve import FitServer
 
     _, jobs = setup
     steps = 14
-    job = dict(jobs[2], steps=steps, optimizer=optimizer, lr_vertex=lr, lr_psf=0.002)
+    job = dict(jobs[2], steps=steps, optimizer=optimizer, lr_vertex=lr, lr_psf=0.002, lr_decay=decay)
     s0 = FitServer(max_jobs=2)
     i0 = s0.submit(**job)
     assert s0.wait(i0, timeout=300)
@@ -272,3 +274,32 @@ def test_preempting_a_queued_job_returns_its_start_state(setup):
     V, state = out
     assert state["step"] == 0 and np.array_equal(V, jobs[1]["V"])
     assert not np.any(state["m_V"]) and not np.any(state["v_V"])
+
+
+@pytest.mark.parametrize("optimizer,lr", [("adam", 0.02), ("large_steps", 0.5)])
+def test_rate_decay_scales_each_step(setup, optimizer, lr):
+    """Step t of a job with lr_decay g takes the rate lr g^(t-1): the first step equals the constant-rate
+    job's, and the second step's displacement is g times the constant-rate job's second displacement
+    (same point, same moments; Adam's step is linear in the rate, and so is the large-steps smoothing
+    solve up to its stopping rule: relative residual 1e-6 from the previous step's solution, times the
+    smoothing matrix's condition number, ~600 here)."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    g = 0.5
+    base = dict(jobs[1], optimizer=optimizer, lr_vertex=lr)
+    s = FitServer(max_jobs=1)
+
+    def run(**kw):
+        i = s.submit(**dict(base, **kw))
+        assert s.wait(i, timeout=300)
+        return s.result(i).V
+
+    V1, V1d = run(steps=1), run(steps=1, lr_decay=g)
+    V2, V2d = run(steps=2), run(steps=2, lr_decay=g)
+    s.shutdown()
+    assert np.array_equal(V1, V1d)
+    d, dd = V2 - V1, V2d - V1
+    assert np.linalg.norm(d) > 0
+    tol = 1e-12 if optimizer == "adam" else 2e-3
+    assert np.linalg.norm(dd - g * d) <= tol * np.linalg.norm(d)
