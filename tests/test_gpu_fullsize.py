@@ -6,6 +6,8 @@
   evaluate one by one (spectrum and mesh adjoint at the full mesh size).
 * 256x256x128 cell (20480 triangles): sampled spectrum against the oracle, and properties that
   hold at any size (unit total intensity, repeat determinism).
+* The largest serving request (81,920 triangles on 256^3): sampled spectrum and mesh adjoint
+  against the oracle, unit total intensity and repeat determinism of a fit step.
 
 Errors are printed (run with -s to see them).
 """
@@ -107,4 +109,48 @@ def test_c3_properties_and_determinism(renderers):
     T = torch.zeros_like(img)
     a = r32.loss_and_grad(Vd, Fd, case.grid, case.psf, T, "mse")
     b = r32.loss_and_grad(Vd, Fd, case.grid, case.psf, T, "mse")
+    assert a[0] == b[0] and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
+
+
+def _largest_request():
+    grid = synth.Grid(n=(256, 256, 256), h=(0.5, 0.5, 1.0))
+    R = 0.3 * float(min(grid.L))
+    V, F = synth.sh_deformed_sphere(6, R, grid.center, lmax=6, coef_sigma=0.03 * R, seed=10_006)
+    psf = synth.Psf(sigma=(0.2, 0.2, 0.6), band_tau=1e-3)
+    return grid, psf, V, F
+
+
+class _Case:
+    def __init__(self, grid, psf):
+        self.grid, self.psf = grid, psf
+
+
+def test_largest_request_against_the_oracle_on_sampled_frequencies(renderers):
+    r32, r64 = renderers
+    grid, psf, V, F = _largest_request()
+    fn = _sample_band(_Case(grid, psf), 128, seed=8)
+    xi = oracle.wavevectors(fn, grid)
+    Vo = V - np.asarray(grid.origin)
+    ref = oracle.mesh_ft(Vo, F, xi)
+    rng = np.random.default_rng(9)
+    G = (rng.normal(size=len(fn)) + 1j * rng.normal(size=len(fn))) / len(fn)
+    dref = oracle.mesh_ft_adjoint(Vo, F, xi, G)
+    S32 = r32.meshft(_dev(V), _dev(F), grid, _dev(fn)).cpu().numpy()
+    d32 = r32.meshft_adjoint(_dev(V), _dev(F), grid, _dev(fn), _dev(G)).cpu().numpy()
+    e_s, e_d = rel(S32, ref), rel(d32, dref)
+    print(f"\n[81920 triangles, 256^3] FP32 sampled spectrum {e_s:.2e}  adjoint {e_d:.2e}")
+    assert e_s < 1e-5 and e_d < 1e-4
+
+
+def test_largest_request_properties_and_determinism(renderers):
+    r32, _ = renderers
+    grid, psf, V, F = _largest_request()
+    Vd, Fd = _dev(V), _dev(F)
+    img = r32.render(Vd, Fd, grid, psf)
+    total = float(img.double().sum()) * np.prod(grid.h)
+    print(f"\n[81920 triangles, 256^3] total intensity - 1 = {total - 1:.2e}")
+    assert abs(total - 1.0) < 1e-5
+    T = torch.zeros_like(img)
+    a = r32.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
+    b = r32.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
     assert a[0] == b[0] and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
