@@ -458,45 +458,36 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
                 __sincosf(phm.x, &sma, &cma);
                 __sincosf(phm.y, &smb, &cmb);
                 const F2 sm = mk(sma, smb), cm = mk(cma, cmb);
-                // r = -i E - q = (Ey - qx, -Ex - qy)
-                const F2 r1x = sub2(g.E1y, g.q1x), r1y = mk(-g.E1x.x - g.q1y.x, -g.E1x.y - g.q1y.y);
-                const F2 r2x = sub2(g.E2y, g.q2x), r2y = mk(-g.E2x.x - g.q2y.x, -g.E2x.y - g.q2y.y);
-                // f_m = i (E2 - conj E1) invs = (-gy, gx) invs
+                // w = conj(Gw) e^{-i phi_m} = h - i k (h = Gr cm - Gi sm, k = Gr sm + Gi cm) and
+                // Re(w z) = h z.x + k z.y. With s f_m = i (E2 - conj E1) = (-gy, gx) and r = -i E - q,
+                // the unscaled derivatives s D_lo = f_m + i conj r1, s D_mid = i (q2 + conj q1),
+                // s D_hi = i r2 - f_m contract to
+                //   Re(w i conj r1) = k (E1y - q1x) - h (E1x + q1y)
+                //   Re(w i (q2 + conj q1)) = h (q1y - q2y) + k (q1x + q2x)
+                //   Re(w i r2) = h (E2x + q2y) + k (E2y - q2x)
+                const F2 h = fms2(R.Gr, cm, mul2(R.Gi, sm));
+                const F2 k = fma2(R.Gr, sm, mul2(R.Gi, cm));
                 const F2 gx = sub2(g.E2x, g.E1x), gy = add2(g.E2y, g.E1y);
-                F2 mfx = mul2(gy, g.invs);  // -f_m.x
-                F2 fyv = mul2(gx, g.invs);  // f_m.y
-                // unscaled derivatives (times s): D_lo = f + i conj r1, D_mid = i (q2 + conj q1), D_hi = i r2 - f
-                F2 Dlx = sub2(r1y, mfx), Dly = add2(fyv, r1x);
-                F2 Dmx = sub2(g.q1y, g.q2y), Dmy = add2(g.q2x, g.q1x);
-                F2 Dhx = sub2(mfx, r2y), Dhy = sub2(r2x, fyv);
-                F2 inv = g.invs;
+                rf = mul2(fms2(k, gx, mul2(h, gy)), g.invs);  // Re(w f_m)
+                const F2 c1 = fms2(k, sub2(g.E1y, g.q1x), mul2(h, add2(g.E1x, g.q1y)));
+                const F2 cm_ = fma2(h, sub2(g.q1y, g.q2y), mul2(k, add2(g.q1x, g.q2x)));
+                const F2 c2 = fma2(h, add2(g.E2x, g.q2y), mul2(k, sub2(g.E2y, g.q2x)));
+                F2 tlo = mul2(add2(rf, c1), g.invs);
+                F2 tmd = mul2(cm_, g.invs);
+                F2 thi = mul2(sub2(c2, rf), g.invs);
                 if (s.x < TS || s.y < TS) {
                     // three phases within TS: the series in the same frame gives f_m and the true
-                    // derivatives (not times s), so those lanes take scale 1 (warp-divergent, rare)
+                    // derivatives, contracted here for those lanes (warp-divergent, rare)
                     F2 fr, fi, lr, li, mr, mi;
                     series_adj(d1, d2, fr, fi, lr, li, mr, mi);
                     const F2 hr = sub2(sub2(fi, lr), mr);                      // D_hi = -(i f_m + D_lo + D_mid)
                     const F2 hi_ = mk(-fr.x - li.x - mi.x, -fr.y - li.y - mi.y);
                     const bool ta = s.x < TS, tb = s.y < TS;
-                    mfx = sel2(ta, tb, mk(-fr.x, -fr.y), mfx);
-                    fyv = sel2(ta, tb, fi, fyv);
-                    Dlx = sel2(ta, tb, lr, Dlx);
-                    Dly = sel2(ta, tb, li, Dly);
-                    Dmx = sel2(ta, tb, mr, Dmx);
-                    Dmy = sel2(ta, tb, mi, Dmy);
-                    Dhx = sel2(ta, tb, hr, Dhx);
-                    Dhy = sel2(ta, tb, hi_, Dhy);
-                    inv = sel2(ta, tb, mk(1.f, 1.f), inv);
+                    rf = sel2(ta, tb, fma2(h, fr, mul2(k, fi)), rf);
+                    tlo = sel2(ta, tb, fma2(h, lr, mul2(k, li)), tlo);
+                    tmd = sel2(ta, tb, fma2(h, mr, mul2(k, mi)), tmd);
+                    thi = sel2(ta, tb, fma2(h, hr, mul2(k, hi_)), thi);
                 }
-                // conj(Gw) e^{-i phi_m} = h - i k with h = Gr cm - Gi sm, k = Gr sm + Gi cm;
-                // Re((h - i k)(u + i v)) = h u + k v
-                const F2 h = fms2(R.Gr, cm, mul2(R.Gi, sm));
-                const F2 k = fma2(R.Gr, sm, mul2(R.Gi, cm));
-                rf = fms2(k, fyv, mul2(h, mfx));  // h f.x + k f.y with f.x = -mfx
-                const F2 hs = mul2(h, inv), ks = mul2(k, inv);
-                const F2 tlo = fma2(hs, Dlx, mul2(ks, Dly));
-                const F2 tmd = fma2(hs, Dmx, mul2(ks, Dmy));
-                const F2 thi = fma2(hs, Dhx, mul2(ks, Dhy));
                 // vertex 1 = 0, vertex 2 = a, vertex 3 = b
                 const F2 tmn = sel2(oA.lo1, oB.lo1, tmd, tlo), tmx = sel2(oA.hi1, oB.hi1, tmd, thi);
                 tv1 = sel2(oA.lo1, oB.lo1, tlo, sel2(oA.hi1, oB.hi1, thi, tmd));
