@@ -135,12 +135,13 @@ struct BatchUnit {
     int b;  // adjoint: frequency chunk
     int pad;
 };
-cudaError_t launch_fwd_batch_f32(const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
-                                 int* d_err, cudaStream_t st);
-cudaError_t launch_adj_batch_f32(const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
-                                 int* d_err, cudaStream_t st);
-int batch_blocks_per_sm_fwd();
-int batch_blocks_per_sm_adj();
+// One launch per label (mode: DM_SURFACE / DM_VOLUME); every unit's job must have that label.
+cudaError_t launch_fwd_batch_f32(int mode, const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter,
+                                 int grid, int* d_err, cudaStream_t st);
+cudaError_t launch_adj_batch_f32(int mode, const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter,
+                                 int grid, int* d_err, cudaStream_t st);
+int batch_blocks_per_sm_fwd(int mode);
+int batch_blocks_per_sm_adj(int mode);
 constexpr int FWD_BLOCK_FREQS = 2 * FWD_THREADS;  // band frequencies per forward block
 
 // Triangle splits per forward frequency block: about `target` work units over the band's fb blocks,

@@ -561,10 +561,12 @@ __device__ __forceinline__ void inval_barriers(uint64_t* full, uint64_t* empty, 
     }
 }
 
-// Persistent forward over the units of several jobs: each block repeatedly takes the next
-// unit (job, frequency block) from an atomic counter. A unit's result does not depend on
-// which block runs it or on the other jobs in the batch.
-__global__ void __launch_bounds__(FWD_THREADS) k_fwd_batch_f32(const BatchFwdJob* __restrict__ jobs,
+// Persistent forward over the units of several jobs of one label (MODE): each block repeatedly
+// takes the next unit (job, frequency block) from an atomic counter. A unit's result does not
+// depend on which block runs it or on the other jobs in the batch. One instantiation per label
+// keeps each at its own register count (a kernel holding both paths takes the larger).
+template <int MODE>
+__global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_batch_f32(const BatchFwdJob* __restrict__ jobs,
                                                                const BatchUnit* __restrict__ units, int n_units,
                                                                int* __restrict__ counter, int* __restrict__ err) {
     __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
@@ -578,27 +580,24 @@ __global__ void __launch_bounds__(FWD_THREADS) k_fwd_batch_f32(const BatchFwdJob
         if (u >= n_units) break;
         const BatchUnit U = units[u];
         const BatchFwdJob& J = jobs[U.job];
-        bool used;
-        if (J.mode == 0)
-            used = fwd_block<0, false>(J.tris, J.n_tiles, J.last, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
-                                       stage, full, empty);
-        else
-            used = fwd_block<1, false>(J.tris, J.n_tiles, J.last, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol, J.S, err, U.a,
-                                       stage, full, empty);
+        const bool used = fwd_block<MODE, false>(J.tris, J.n_tiles, J.last, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol,
+                                                 J.S, err, U.a, stage, full, empty);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kFwdStages);
         __syncthreads();
     }
 }
 
-// Persistent adjoint over units (job, triangle block, frequency chunk of chunk_tiles tiles).
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_batch_f32(const BatchAdjJob* __restrict__ jobs,
+// Persistent adjoint over units (job, triangle block, frequency chunk of chunk_tiles tiles) of one label.
+template <int MODE>
+__global__ void __launch_bounds__(ADJ_THREADS, MODE == 0 ? 5 : 4) k_adj_batch_f32(const BatchAdjJob* __restrict__ jobs,
                                                                const BatchUnit* __restrict__ units, int n_units,
                                                                int* __restrict__ counter, int* __restrict__ err) {
+    constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
     __shared__ __align__(128) FreqPairF32 stage[kAdjStages][kAdjPairs];
     __shared__ __align__(8) uint64_t full[kAdjStages], empty[kAdjStages];
     __shared__ int s_u;
-    __shared__ float acc_s[2 * NACC_VOL * ADJ_THREADS];
+    __shared__ float acc_s[2 * NACC * ADJ_THREADS];
     while (true) {
         if (threadIdx.x == 0) s_u = atomicAdd(counter, 1);
         __syncthreads();
@@ -611,13 +610,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_batch_f32(const BatchAdjJob
         const int n_ftiles = (int)((M + ADJ_FTILE - 1) / ADJ_FTILE);
         const int f0 = U.b * J.chunk_tiles;
         const int f1 = min(f0 + J.chunk_tiles, n_ftiles);
-        const int nacc = J.mode == 0 ? NACC_SURF : NACC_VOL;
-        float* out = J.partial + (int64_t)U.b * nacc * J.n_t_pad;
-        bool used;
-        if (J.mode == 0)
-            used = adj_block<0>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty, acc_s);
-        else
-            used = adj_block<1>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty, acc_s);
+        float* out = J.partial + (int64_t)U.b * NACC * J.n_t_pad;
+        const bool used = adj_block<MODE>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty,
+                                          acc_s);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kAdjStages);
         __syncthreads();
@@ -683,32 +678,40 @@ cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_
     return cudaGetLastError();
 }
 
-int batch_blocks_per_sm_fwd() {
+int batch_blocks_per_sm_fwd(int mode) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fwd_batch_f32, FWD_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mode == 0 ? k_fwd_batch_f32<0> : k_fwd_batch_f32<1>,
+                                                  FWD_THREADS, 0);
     return n > 0 ? n : 1;
 }
-int batch_blocks_per_sm_adj() {
+int batch_blocks_per_sm_adj(int mode) {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adj_batch_f32, ADJ_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, mode == 0 ? k_adj_batch_f32<0> : k_adj_batch_f32<1>,
+                                                  ADJ_THREADS, 0);
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_fwd_batch_f32(const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
-                                 int* d_err, cudaStream_t st) {
+cudaError_t launch_fwd_batch_f32(int mode, const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter,
+                                 int grid, int* d_err, cudaStream_t st) {
     if (n_units <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_fwd_batch_f32<<<grid, FWD_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
+    if (mode == 0)
+        k_fwd_batch_f32<0><<<grid, FWD_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
+    else
+        k_fwd_batch_f32<1><<<grid, FWD_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_batch_f32(const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter, int grid,
-                                 int* d_err, cudaStream_t st) {
+cudaError_t launch_adj_batch_f32(int mode, const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter,
+                                 int grid, int* d_err, cudaStream_t st) {
     if (n_units <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    k_adj_batch_f32<<<grid, ADJ_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
+    if (mode == 0)
+        k_adj_batch_f32<0><<<grid, ADJ_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
+    else
+        k_adj_batch_f32<1><<<grid, ADJ_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
     return cudaGetLastError();
 }
 

@@ -179,14 +179,15 @@ struct dm_server {
     bool dirty = true;
     std::vector<BatchFwdJob> fj;
     std::vector<BatchAdjJob> aj;
-    std::vector<BatchUnit> uf, ua;
+    std::vector<BatchUnit> uf, ua;   // surface jobs' units first, then volume jobs'
+    size_t nf_surf = 0, na_surf = 0; // how many units of uf / ua belong to surface jobs
     BatchFwdJob* d_fj = nullptr;
     BatchAdjJob* d_aj = nullptr;
     BatchUnit *d_uf = nullptr, *d_ua = nullptr;
     size_t cap_fj = 0, cap_aj = 0, cap_uf = 0, cap_ua = 0;
     int* d_counter = nullptr;
     double* h_loss = nullptr;  // pinned, one per batch slot
-    int grid_fwd = 0, grid_adj = 0;
+    int grid_fwd[2] = {0, 0}, grid_adj[2] = {0, 0};  // persistent grid per label
     std::vector<std::pair<cudaStream_t, cudaEvent_t>> free_streams;  // job streams not in use
     cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr;                  // after each batched launch
     int64_t since_sync = 0;
@@ -331,18 +332,24 @@ bool rebuild_units(dm_server* S) {
         a.partial = (float*)b.adjp;
         order[j] = (int)j;
     }
-    // largest triangle counts first: their forward units cost the most
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return S->run[x]->z.n_t > S->run[y]->z.n_t; });
+    // surface jobs before volume jobs (one launch per label), largest triangle counts first within
+    // each: their forward units cost the most
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const SJob *a = S->run[x], *b = S->run[y];
+        return a->label != b->label ? a->label < b->label : a->z.n_t > b->z.n_t;
+    });
+    S->nf_surf = S->na_surf = 0;
     for (int j : order) {
         const int64_t nb = (S->run[j]->z.nH + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
         for (int64_t k = 0; k < nb; ++k) S->uf.push_back({j, (int)k, 0, 0});
+        if (S->run[j]->label == DM_SURFACE) S->nf_surf = S->uf.size();
     }
     for (int j : order) {
         const Sizes& z = S->run[j]->z;
         const int64_t tb = z.n_t_pad / ADJ_THREADS;
         for (int c = 0; c < z.n_chunks; ++c)
             for (int64_t t = 0; t < tb; ++t) S->ua.push_back({j, (int)t, c, 0});
+        if (S->run[j]->label == DM_SURFACE) S->na_surf = S->ua.size();
     }
     bool ok = grow((void**)&S->d_fj, &S->cap_fj, nj, sizeof(BatchFwdJob)) &&
               grow((void**)&S->d_aj, &S->cap_aj, nj, sizeof(BatchAdjJob)) &&
@@ -398,12 +405,18 @@ bool iterate(dm_server* S, bool sync) {
             ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
         }
     }
-    // persistent grids no larger than the unit lists (a small batch launches no idle blocks)
-    const int gf = (int)std::min<size_t>((size_t)S->grid_fwd, S->uf.size());
-    const int ga = (int)std::min<size_t>((size_t)S->grid_adj, S->ua.size());
-    ok &= launch_fwd_batch_f32(S->d_fj, S->d_uf, (int)S->uf.size(), S->d_counter, gf, ctx->d_err, st) == cudaSuccess;
+    // persistent grids no larger than the unit lists (a small batch launches no idle blocks); one
+    // launch per label present, surface units first
+    const size_t nfl[2] = {S->nf_surf, S->uf.size() - S->nf_surf};
+    const size_t nal[2] = {S->na_surf, S->ua.size() - S->na_surf};
+    for (int m = 0; m < 2; ++m) {
+        if (nfl[m] == 0) continue;
+        const int gf = (int)std::min<size_t>((size_t)S->grid_fwd[m], nfl[m]);
+        ok &= launch_fwd_batch_f32(m, S->d_fj, S->d_uf + (m ? S->nf_surf : 0), (int)nfl[m], S->d_counter, gf,
+                                   ctx->d_err, st) == cudaSuccess;
+        g_launches += 1;
+    }
     ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
-    g_launches += 1;
     // image, loss, adjoint records
     for (SJob* J : S->run) {
         cudaStream_t js = single ? st : J->stream;
@@ -437,9 +450,14 @@ bool iterate(dm_server* S, bool sync) {
             ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
         }
     }
-    ok &= launch_adj_batch_f32(S->d_aj, S->d_ua, (int)S->ua.size(), S->d_counter, ga, ctx->d_err, st) == cudaSuccess;
+    for (int m = 0; m < 2; ++m) {
+        if (nal[m] == 0) continue;
+        const int ga = (int)std::min<size_t>((size_t)S->grid_adj[m], nal[m]);
+        ok &= launch_adj_batch_f32(m, S->d_aj, S->d_ua + (m ? S->na_surf : 0), (int)nal[m], S->d_counter, ga,
+                                   ctx->d_err, st) == cudaSuccess;
+        g_launches += 1;
+    }
     ok &= cudaEventRecord(S->ev_adj, st) == cudaSuccess;
-    g_launches += 1;
     // per-vertex gradients and Adam
     for (size_t j = 0; j < nj; ++j) {
         SJob* J = S->run[j];
@@ -784,8 +802,10 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     }
     S->stats.bytes_total = S->arena.total;
     const int sms = ctx->sm_count;
-    S->grid_fwd = sms * batch_blocks_per_sm_fwd();
-    S->grid_adj = sms * batch_blocks_per_sm_adj();
+    for (int m = 0; m < 2; ++m) {
+        S->grid_fwd[m] = sms * batch_blocks_per_sm_fwd(m);
+        S->grid_adj[m] = sms * batch_blocks_per_sm_adj(m);
+    }
     S->engine = std::thread(engine_main, S);
     *out = S;
     return DM_OK;
