@@ -24,9 +24,10 @@
 // into a ring of shared-memory stages with full/empty mbarriers. FP32 sums within
 // a tile, Kahan across tiles; slices are summed afterwards in FP64 in a fixed order.
 // Adjoint: a thread holds one triangle; the block walks a chunk of the band in
-// tiles of frequency-pair records bulk-copied the same way, keeping the triangle's
-// 10 (surface) or 12 (volume) sums in registers; chunks are summed afterwards in
-// FP64 in a fixed order (deterministic).
+// tiles of frequency-pair records bulk-copied the same way, summing the triangle's
+// 10 (surface) or 12 (volume) terms of a tile in registers and carrying the running
+// sums in shared memory; chunks are summed afterwards in FP64 in a fixed order
+// (deterministic).
 #include "dm_kernels.cuh"
 #include "meshft_math.cuh"
 
@@ -421,10 +422,10 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
     const TriF32 T = tris[t < n_t ? t : tblock * ADJ_THREADS];
     const bool idle = tblock * ADJ_THREADS + (tid & ~31) >= n_t;
     // edge vectors held once per thread (the record stores each field twice for paired loads from
-    // shared memory; here in registers the pairs are rebuilt at each use: 4-5 registers fewer, ~1%)
+    // shared memory; in registers the pairs are rebuilt at each use, which needs fewer registers)
     const float e21[3] = {T.e21x.x, T.e21y.x, T.e21z.x}, e31[3] = {T.e31x.x, T.e31y.x, T.e31z.x};
     // the triangle's running sums and their compensations live in shared memory (each thread its
-    // own column), touched once per tile: 20-24 registers fewer in the frequency loop
+    // own column), touched once per tile, leaving the registers to the frequency loop
     float* tot = acc_s + tid;
     float* comp = acc_s + NACC * ADJ_THREADS + tid;
 #pragma unroll
