@@ -303,3 +303,36 @@ def test_rate_decay_scales_each_step(setup, optimizer, lr):
     assert np.linalg.norm(d) > 0
     tol = 1e-12 if optimizer == "adam" else 2e-3
     assert np.linalg.norm(dd - g * d) <= tol * np.linalg.norm(d)
+
+
+def test_volume_job_in_a_mixed_batch(setup):
+    """A volume-labelled job runs in the batched launches of its own label beside surface jobs: the same
+    result alone and in the mix (bitwise), and the standalone dm_fit's within FP32 tolerance."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    j = jobs[2]
+    # a target without the start's symmetries: Adam's first steps are +-lr on every coordinate, so a
+    # gradient component that vanishes by symmetry would turn rounding differences into full steps
+    R = 0.9 * float(np.linalg.norm(j["V"][0] - np.asarray(j["grid"].center)))
+    Vt, _ = synth.sh_deformed_sphere(3, R, j["grid"].center, lmax=4, coef_sigma=0.05 * R, seed=77)
+    T = r32.render(torch.as_tensor(Vt).cuda(), torch.as_tensor(j["F"]).cuda(), j["grid"], j["psf"],
+                   label="volume").cpu().numpy()
+    vj = dict(j, target=T, label="volume")
+    s1 = FitServer(max_jobs=4)
+    alone = _run(s1, [vj], [0])[0]
+    s1.shutdown()
+    s2 = FitServer(max_jobs=4)
+    mix = _run(s2, [jobs[1], vj, jobs[3]], [0, 1, 2])
+    st = s2.stats()
+    s2.shutdown()
+    assert st["peak_active"] >= 2
+    assert np.array_equal(alone.V, mix[1].V)
+    assert np.array_equal(alone.loss_history, mix[1].loss_history)
+    Vf, sig, hist = r32.fit(torch.as_tensor(j["V"]).cuda(), torch.as_tensor(j["F"]).cuda(), j["grid"], j["psf"],
+                            torch.as_tensor(T).cuda(), steps=STEPS, lr_vertex=j["lr_vertex"], label="volume")
+    Vf = Vf.cpu().numpy()
+    moved = np.linalg.norm(Vf - j["V"])
+    assert moved > 0
+    assert np.linalg.norm(mix[1].V - Vf) < 1e-3 * moved
+    assert np.allclose(mix[1].loss_history, hist.numpy(), rtol=1e-4)
