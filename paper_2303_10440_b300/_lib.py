@@ -118,6 +118,7 @@ class dm_job(ctypes.Structure):
         ("optimizer", c_i32),
         ("lam", c_f64),
         ("lr_decay", c_f64),
+        ("tri_weight", c_p),
         ("resume", ctypes.POINTER(dm_fit_state)),
     ]
 

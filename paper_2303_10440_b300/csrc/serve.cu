@@ -85,6 +85,7 @@ struct SJob {
     std::vector<double> V;
     std::vector<int32_t> F;
     std::vector<float> T;
+    std::vector<float> W;  // per-triangle densities (empty: 1)
     dm_grid grid;
     dm_psf psf;
     dm_fit_options fit;
@@ -139,7 +140,7 @@ int job_chunk_tiles(const Sizes& z, int max_tiles, int sm_count) {
 
 size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, double** mom, double** hist,
                   SJob* J) {
-    layout(z, A, b, true, true, false, true, false);
+    layout(z, A, b, true, true, !J->W.empty(), true, false);
     *mom = A.take<double>(6 * n_v + 8);
     *hist = A.take<double>(steps);
     if (J->optimizer == DM_OPT_LARGE_STEPS) {
@@ -259,6 +260,9 @@ bool setup_job(dm_server* S, SJob* J) {
                   cudaSuccess &&
               cudaMemcpyAsync(b.target, J->T.data(), J->T.size() * sizeof(float), cudaMemcpyHostToDevice, st) ==
                   cudaSuccess &&
+              (J->W.empty() ||
+               cudaMemcpyAsync(b.wts, J->W.data(), J->W.size() * sizeof(float), cudaMemcpyHostToDevice, st) ==
+                   cudaSuccess) &&
               cudaMemsetAsync(mom, 0, (6 * z.n_v + 8) * sizeof(double), st) == cudaSuccess &&
               launch_set_params(b.d_params, psf_params(&J->psf), 9, st) == cudaSuccess &&
               launch_csr(b.F, z.n_t, z.n_v, b.cnt, b.ptr, b.ent, ctx->d_err, st) == cudaSuccess &&
@@ -391,7 +395,7 @@ bool iterate(dm_server* S, bool sync) {
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         int nb = 0;
-        ok &= launch_tri_prep<TriF32>(J->label, b.V, J->z.n_v, b.F, J->z.n_t, nullptr, G, (TriF32*)b.tris,
+        ok &= launch_tri_prep<TriF32>(J->label, b.V, J->z.n_v, b.F, J->z.n_t, b.wts, G, (TriF32*)b.tris,
                                       J->z.n_t_pad, b.partial, &nb, ctx->d_err, js) == cudaSuccess;
         ok &= launch_sum(b.partial, nb, 1, 1, b.d_params + 16, js) == cudaSuccess;
         g_launches += 2;
@@ -468,7 +472,7 @@ bool iterate(dm_server* S, bool sync) {
         const Sizes& z = J->z;
         ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, js) ==
               cudaSuccess;
-        ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, nullptr, G, b.acc, b.d_params + 30, b.contrib, js) ==
+        ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, b.wts, G, b.acc, b.d_params + 30, b.contrib, js) ==
               cudaSuccess;
         ok &= launch_vertex_gather(b.ptr, b.ent, b.contrib, z.n_v, b.dV, js) == cudaSuccess;
         ok &= cudaMemcpyAsync(J->hist + J->steps_done, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToDevice,
@@ -555,6 +559,7 @@ void finish_job(dm_server* S, SJob* J, int state) {
     std::vector<double>().swap(J->V);
     std::vector<int32_t>().swap(J->F);
     std::vector<float>().swap(J->T);
+    std::vector<float>().swap(J->W);
     std::lock_guard<std::mutex> lk(S->mu);
     J->state = state;
     J->t_end = S->now();
@@ -608,6 +613,7 @@ void handle_preempts(dm_server* S) {
         std::vector<double>().swap(J->V);
         std::vector<int32_t>().swap(J->F);
         std::vector<float>().swap(J->T);
+        std::vector<float>().swap(J->W);
         it = S->pending.erase(it);
         any = true;
     }
@@ -745,6 +751,16 @@ dm_status validate_job(const dm_job* j) {
     }
     if (std::isnan(j->lambda)) return DM_ERR_ARG;
     if (!(j->lr_decay >= 0.0 && j->lr_decay <= 1.0)) return DM_ERR_ARG;
+    if (j->tri_weight) {
+        if (j->label != DM_SURFACE) return DM_ERR_ARG;
+        bool any = false;
+        for (int64_t t = 0; t < j->n_t; ++t) {
+            const float w = j->tri_weight[t];
+            if (!(w >= 0.f) || !std::isfinite(w)) return DM_ERR_ARG;
+            any |= w > 0.f;
+        }
+        if (!any) return DM_ERR_ARG;
+    }
     for (int a = 0; a < 3; ++a) {
         if (!(j->psf.sigma[a] > 0) || !(j->grid.h[a] > 0) || j->grid.n[a] < 1) return DM_ERR_ARG;
         FFTAxis ax;
@@ -820,6 +836,7 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     J->F.assign(job->F, job->F + 3 * job->n_t);
     const int64_t N = (int64_t)job->grid.n[0] * job->grid.n[1] * job->grid.n[2];
     J->T.assign(job->target, job->target + N);
+    if (job->tri_weight) J->W.assign(job->tri_weight, job->tri_weight + job->n_t);
     J->grid = job->grid;
     J->psf = job->psf;
     J->fit = job->fit;

@@ -53,10 +53,10 @@ class FitServer:
 
     def submit(self, V, F, target, grid, psf, steps: int, lr_vertex: float, lr_psf: float = 0.0, loss: str = "mse",
                label: str = "surface", beta1=0.9, beta2=0.999, eps=1e-20, optimizer: str = "adam",
-               lam: float = 50.0, resume: dict | None = None, lr_decay: float = 1.0) -> int:
+               lam: float = 50.0, resume: dict | None = None, lr_decay: float = 1.0, weights=None) -> int:
         """resume: the state dict of a preempted job (see preempt); V is then that job's vertices and
         steps the steps still to take. lr_decay: step t uses lr * lr_decay^(t-1) (t continues across
-        resume)."""
+        resume). weights: per-triangle densities (surface label), or None for 1."""
         V = np.ascontiguousarray(V, dtype=np.float64)
         F = np.ascontiguousarray(F, dtype=np.int32)
         T = np.ascontiguousarray(target, dtype=np.float32)
@@ -74,6 +74,12 @@ class FitServer:
         j.lam = float(lam)
         j.lr_decay = float(lr_decay)
         keep = []
+        if weights is not None:
+            W = np.ascontiguousarray(weights, dtype=np.float32)
+            if W.shape != (F.shape[0],):
+                raise ValueError("weights: one value per triangle")
+            keep.append(W)
+            j.tri_weight = W.ctypes.data
         if resume is not None:
             st = _lib.fit_state_struct(dict(resume), V.shape[0], keep)
             keep.append(st)

@@ -53,6 +53,6 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(_lib.dm_fit_options) == 8 + 40
     assert ctypes.sizeof(_lib.dm_stagger_options) == 24 + 56 + 8
     assert ctypes.sizeof(_lib.dm_stagger_stats) == 24
-    assert ctypes.sizeof(_lib.dm_job) == 40 + 64 + 88 + 48 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(_lib.dm_job) == 40 + 64 + 88 + 48 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(_lib.dm_fit_state) == 8 + 72 + 24
     assert ctypes.sizeof(_lib.dm_server_options) == 4 + 4 + 8 + 4 + 4 + 8 + 8

@@ -155,6 +155,11 @@ def test_invalid_jobs_are_refused(setup):
     bad = dict(jobs[1], grid=synth.Grid(n=(14, 14, 14), h=(1, 1, 1)))
     with pytest.raises(RuntimeError, match="DM_ERR_UNSUPPORTED"):
         s.submit(**bad)
+    n_t = jobs[1]["F"].shape[0]
+    for w, kw in ((np.full(n_t, -1.0), {}), (np.zeros(n_t), {}), (np.full(n_t, np.nan), {}),
+                  (np.ones(n_t), {"label": "volume"})):
+        with pytest.raises(RuntimeError, match="DM_ERR_ARG"):
+            s.submit(**dict(jobs[1], weights=w, **kw))
     s.shutdown()
 
 
@@ -336,3 +341,39 @@ def test_volume_job_in_a_mixed_batch(setup):
     assert moved > 0
     assert np.linalg.norm(mix[1].V - Vf) < 1e-3 * moved
     assert np.allclose(mix[1].loss_history, hist.numpy(), rtol=1e-4)
+
+
+def test_weighted_multicell_job_matches_the_standalone_fit(setup):
+    """A two-cell foam with a doubled shared wall (densities 1 and 2, Eq. 13) as one served job:
+    the same result alone and in a mix, and the standalone weighted fit's within FP32 tolerance."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    grid = synth.Grid(n=(32, 32, 24), h=(0.5, 0.5, 1.0))
+    V0, F, rho = synth.box_foam((2, 1, 1), (5.0, 6.0, 6.0), subdiv=2, origin=(3.0, 5.0, 6.0), jitter=0.1, seed=2)
+    Vt = V0 + 0.2 * np.cos(V0[:, [2, 0, 1]] / 2.5)
+    psf = synth.Psf(sigma=(0.4, 0.4, 0.9), band_tau=1e-3)
+    W = rho.astype(np.float32)
+    T = r32.render(torch.as_tensor(Vt).cuda(), torch.as_tensor(F).cuda(), grid, psf,
+                   weights=torch.as_tensor(W).cuda()).cpu().numpy()
+    wj = dict(V=V0, F=F, target=T, grid=grid, psf=psf, steps=STEPS, lr_vertex=0.02, weights=W)
+    s1 = FitServer(max_jobs=4)
+    alone = _run(s1, [wj], [0])[0]
+    s1.shutdown()
+    s2 = FitServer(max_jobs=4)
+    mix = _run(s2, [jobs[1], wj], [0, 1])
+    s2.shutdown()
+    assert np.array_equal(alone.V, mix[1].V)
+    assert np.array_equal(alone.loss_history, mix[1].loss_history)
+    Vf, sig, hist = r32.fit(torch.as_tensor(V0).cuda(), torch.as_tensor(F).cuda(), grid, psf, torch.as_tensor(T).cuda(),
+                            steps=STEPS, lr_vertex=0.02, weights=torch.as_tensor(W).cuda())
+    Vf = Vf.cpu().numpy()
+    moved = np.linalg.norm(Vf - V0)
+    assert moved > 0
+    assert np.linalg.norm(mix[1].V - Vf) < 1e-3 * moved
+    assert np.allclose(mix[1].loss_history, hist.numpy(), rtol=1e-4)
+    # the densities matter: an unweighted job ends elsewhere
+    s3 = FitServer(max_jobs=1)
+    plain = _run(s3, [dict(wj, weights=None)], [0])[0]
+    s3.shutdown()
+    assert np.linalg.norm(plain.V - mix[1].V) > 1e-2 * moved
