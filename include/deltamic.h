@@ -370,7 +370,7 @@ typedef struct {
     double lr_decay;       /* step t (from 1, continuing across resume) uses fit.lr_vertex * lr_decay^(t-1)
                               and likewise lr_psf; 0 or 1: constant rates; otherwise in (0, 1) */
     const float* tri_weight; /* host [n_t] per-triangle densities (copied at submit; surface label only,
-                              finite, >= 0, not all 0), or NULL for density 1 (Sec. 4, Eq. 13) */
+                              finite, >= 0, not all 0), or NULL for density 1 (Sec. 3.3, 4.1) */
     const dm_fit_state* resume; /* NULL, or the state of a preempted job (copied at submit): V is then
                               that job's vertices and fit.steps the steps still to take */
 } dm_job;

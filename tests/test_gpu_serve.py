@@ -344,7 +344,7 @@ def test_volume_job_in_a_mixed_batch(setup):
 
 
 def test_weighted_multicell_job_matches_the_standalone_fit(setup):
-    """A two-cell foam with a doubled shared wall (densities 1 and 2, Eq. 13) as one served job:
+    """A two-cell foam with a doubled shared wall (densities 1 and 2, Sections 3.3 and 4.1) as one served job:
     the same result alone and in a mix, and the standalone weighted fit's within FP32 tolerance."""
     from paper_2303_10440_b300.serve import FitServer
 
