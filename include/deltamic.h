@@ -125,6 +125,14 @@ dm_status dm_workspace_size(const dm_ctx* ctx, const dm_grid* grid, int64_t n_v,
 dm_status dm_reserve(dm_ctx* ctx, size_t bytes);
 /* Synchronise `stream` and report any device-side fault recorded since the last check. */
 dm_status dm_sync(dm_ctx* ctx, void* stream);
+/* Debug check of a mesh (host or device arrays; synchronises): DM_ERR_ARG for a face index outside
+ * [0, n_v), a non-finite vertex or density, or tri_weight with the volume label; DM_ERR_DEGENERATE
+ * for a zero total (weighted) area or a non-positive enclosed volume; DM_ERR_OPEN_MESH when the
+ * volume label's mesh is not closed and consistently oriented (every directed edge p -> q used
+ * once, and q -> p once). The path itself raises DM_ERR_DEGENERATE from the device normaliser:
+ * calls that synchronise (loss and gradients, fits) return it, asynchronous ones (render, stage
+ * calls) at the next dm_sync. The fit server runs this check at submit. */
+dm_status dm_check_mesh(dm_ctx* ctx, const dm_mesh* mesh);
 /* Number of this library's kernels launched since the library was loaded (instrumentation). */
 int64_t dm_kernel_launches(const dm_ctx* ctx);
 
@@ -196,7 +204,8 @@ dm_status dm_r2c(dm_ctx* ctx, const dm_grid* grid, const void* image, void* spec
  * file-scope device array of DM_NOALLOC_SCRATCH_BYTES per device, held until the process exits.
  * Arguments as dm_meshft; S_out is [M] complex float. Every pointer must be device memory of
  * the calling thread's current device. fault_flags (nullable, device int) receives 0, or bit 2
- * for a face index outside [0, n_v), bit 4 for a non-finite vertex (stream ordered).
+ * for a face index outside [0, n_v), bit 4 for a non-finite vertex, bit 8 for a zero total area
+ * or non-positive enclosed volume (stream ordered).
  * Returns DM_ERR_ARG for NULL or host pointers, n_t > DM_NOALLOC_MAX_TRIANGLES or bad sizes;
  * DM_ERR_CUDA if a launch fails. The first call on a device looks up the scratch address
  * (once per device), so make it before any stream capture. All calls on a device share the

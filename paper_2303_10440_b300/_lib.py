@@ -170,6 +170,7 @@ _SIGS = {
     "dm_workspace_size": (c_i32, [c_p, ctypes.POINTER(dm_grid), c_i64, c_i64, ctypes.POINTER(ctypes.c_size_t)]),
     "dm_reserve": (c_i32, [c_p, ctypes.c_size_t]),
     "dm_sync": (c_i32, [c_p, c_p]),
+    "dm_check_mesh": (c_i32, [c_p, c_p]),
     "dm_kernel_launches": (c_i64, [c_p]),
     "dm_profile_enable": (c_i32, [c_p, c_i32]),
     "dm_profile_read": (c_i32, [c_p, c_p, c_p]),

@@ -153,6 +153,13 @@ class Renderer:
         return V.device if isinstance(V, torch.Tensor) else torch.device("cpu")
 
     # ------------------------------------------------------------------ renderer
+    def check_mesh(self, V, F, label="surface", weights=None):
+        """Debug check of a mesh (dm_check_mesh): raises DeltaMicError (DM_ERR_ARG, DM_ERR_DEGENERATE or
+        DM_ERR_OPEN_MESH) for bad indices or values, a zero area / non-positive volume, or a volume-label
+        mesh that is not closed and consistently oriented."""
+        m, keep = self._mesh(V, F, label, weights, self._dev(V))  # host arrays stay on the host
+        self._check(self.lib.dm_check_mesh(self.ctx, ctypes.byref(m)), "dm_check_mesh")
+
     def render(self, V, F, grid, psf, label="surface", weights=None, out=None, stream=None):
         dev = self._dev(V)
         m, keep = self._mesh(V, F, label, weights, dev)

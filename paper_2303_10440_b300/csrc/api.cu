@@ -392,7 +392,7 @@ dm_status raw_common(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* grid, cons
     else
         LAUNCH(1, launch_tri_prep<TriF32>(mesh->label, *V, mesh->n_v, *F, mesh->n_t, *W, G, (TriF32*)b.tris, n_t_pad,
                                           b.partial, &nb, ctx->d_err, st));
-    LAUNCH(1, launch_sum(b.partial, nb, 1, 1, b.d_params + 16, st));
+    LAUNCH(1, launch_norm_sum(b.partial, nb, b.d_params + 16, ctx->d_err, st));
     return DM_OK;
 }
 

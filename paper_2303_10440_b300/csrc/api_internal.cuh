@@ -17,6 +17,10 @@
 
 namespace dm {
 extern std::atomic<int64_t> g_launches;  // kernels launched by this library (instrumentation)
+// Host-side mesh validation (mesh_check.cu): DM_OK, DM_ERR_ARG, DM_ERR_DEGENERATE or, for the volume
+// label, DM_ERR_OPEN_MESH; *why receives the reason.
+dm_status check_mesh_host(const double* V, int64_t n_v, const int32_t* F, int64_t n_t, const float* W, int label,
+                          std::string* why);
 }
 using namespace dm;
 
@@ -195,6 +199,8 @@ dm_status check_dev_err(dm_ctx* ctx, cudaStream_t st) {
         if (h & ERR_BAD_INDEX) return fail(ctx, DM_ERR_ARG, "face index outside [0, n_v)");
         if (h & ERR_NONFINITE) return fail(ctx, DM_ERR_ARG, "non-finite vertex position");
         if (h & ERR_TIMEOUT) return fail(ctx, DM_ERR_TIMEOUT, "a bounded device wait expired");
+        if (h & ERR_DEGENERATE)
+            return fail(ctx, DM_ERR_DEGENERATE, "zero total (weighted) area, or non-positive enclosed volume");
     }
     return DM_OK;
 }
@@ -425,7 +431,7 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
         int nb = 0;
         LAUNCH(1, launch_tri_prep<TriRec>(mode, in.V, in.n_v, in.F, in.n_t, in.wts, G, (TriRec*)b.tris, z.n_t_pad,
                                           b.partial, &nb, ctx->d_err, st));
-        LAUNCH(1, launch_sum(b.partial, nb, 1, 1, d_norm, st));
+        LAUNCH(1, launch_norm_sum(b.partial, nb, d_norm, ctx->d_err, st));
     }
 
     // narrow band

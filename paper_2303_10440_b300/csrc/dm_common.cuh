@@ -12,6 +12,7 @@ enum : int {
     ERR_TIMEOUT = 1,     // a bounded wait on an mbarrier expired
     ERR_BAD_INDEX = 2,   // a face index outside [0, n_v)
     ERR_NONFINITE = 4,   // NaN/Inf in vertex positions
+    ERR_DEGENERATE = 8,  // normaliser (total weighted area, or enclosed volume) not > 0
 };
 
 template <class R>

@@ -170,6 +170,9 @@ cudaError_t launch_tri_prep(int mode, const double* V, int64_t n_v, const int32_
 
 // Deterministic sum of `n` doubles into out[0] (one block).
 cudaError_t launch_sum(const double* x, int64_t n, int stride, int count, double* out, cudaStream_t st);
+// The mesh normaliser (sum of the triangle-record partials): as launch_sum, and ERR_DEGENERATE in
+// d_err when it is not > 0 (zero total weighted area, non-positive enclosed volume).
+cudaError_t launch_norm_sum(const double* x, int64_t n, double* out, int* d_err, cudaStream_t st);
 
 // Narrow band: writes indices of H with h_hat > tau into idx (ordered), size into dM.
 cudaError_t launch_band(const double* d_psf, int psf_kind, double tau, int Nx, int Ny, int Nz, const Geom& g,

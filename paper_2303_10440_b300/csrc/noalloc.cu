@@ -126,7 +126,7 @@ extern "C" dm_status dm_meshft_noalloc(const dm_mesh* mesh, const dm_grid* grid,
     int nb = 0;
     cudaError_t e = launch_tri_prep<TriF32>(mesh->label, mesh->V, mesh->n_v, mesh->F, mesh->n_t, mesh->tri_weight, g,
                                             rec, n_t_pad, partial, &nb, d_err, st);
-    if (e == cudaSuccess) e = launch_sum(partial, nb, 1, 1, d_norm, st);
+    if (e == cudaSuccess) e = launch_norm_sum(partial, nb, d_norm, d_err, st);
     if (e == cudaSuccess) e = launch_fwd_f32(mesh->label, rec, mesh->n_t, fs, g, d_norm, (float2*)S_out, nullptr, 0, d_err, st);
     if (e == cudaSuccess && fault_flags) e = cudaMemcpyAsync(fault_flags, d_err, sizeof(int), cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) {

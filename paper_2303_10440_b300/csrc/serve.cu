@@ -831,6 +831,8 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     if (!S || !job_id) return DM_ERR_ARG;
     dm_status s = validate_job(job);
     if (s != DM_OK) return s;
+    std::string why;  // degenerate or (volume label) open meshes are refused here, not mid-batch
+    if ((s = check_mesh_host(job->V, job->n_v, job->F, job->n_t, job->tri_weight, job->label, &why)) != DM_OK) return s;
     SJob* J = new SJob();
     J->V.assign(job->V, job->V + 3 * job->n_v);
     J->F.assign(job->F, job->F + 3 * job->n_t);

@@ -118,14 +118,18 @@ __global__ void __launch_bounds__(NT) k_tri_prep(int mode, const double* __restr
 }
 
 // out[k] = sum_{b < n} x[b * count + k]  (one block per k, fixed order)
+// err_nonpos (nullable): ERR_DEGENERATE is raised there when a sum is not > 0 (zero, negative, NaN).
 __global__ void __launch_bounds__(1024) k_sum(const double* __restrict__ x, int64_t n, int count,
-                                              double* __restrict__ out) {
+                                              double* __restrict__ out, int* __restrict__ err_nonpos) {
     __shared__ double scratch[32];
     const int k = blockIdx.x;
     double s = 0.0;
     for (int64_t b = threadIdx.x; b < n; b += 1024) s += x[b * count + k];
     s = block_sum<1024>(s, scratch);
-    if (threadIdx.x == 0) out[k] = s;
+    if (threadIdx.x == 0) {
+        out[k] = s;
+        if (err_nonpos && !(s > 0.0)) atomicOr(err_nonpos, ERR_DEGENERATE);
+    }
 }
 
 // ---------------------------------------------------------------- narrow band
@@ -633,7 +637,12 @@ template cudaError_t launch_tri_prep<TriF64>(int, const double*, int64_t, const 
 
 cudaError_t launch_sum(const double* x, int64_t n, int stride, int count, double* out, cudaStream_t st) {
     (void)stride;
-    k_sum<<<count, 1024, 0, st>>>(x, n, count, out);
+    k_sum<<<count, 1024, 0, st>>>(x, n, count, out, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_norm_sum(const double* x, int64_t n, double* out, int* d_err, cudaStream_t st) {
+    k_sum<<<1, 1024, 0, st>>>(x, n, 1, out, d_err);
     return cudaGetLastError();
 }
 

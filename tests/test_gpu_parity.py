@@ -263,6 +263,50 @@ def test_argument_errors_are_reported(r32):
     assert torch.isfinite(img).all()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_degenerate_and_open_meshes_are_reported(prec, r64, r32):
+    """Zero total area and non-positive enclosed volume are reported by the render calls themselves
+    (DM_ERR_DEGENERATE, from the device normaliser); dm_check_mesh also finds volume-label meshes that
+    are not closed and consistently oriented (DM_ERR_OPEN_MESH)."""
+    from paper_2303_10440_b300 import DeltaMicError
+
+    r = r64 if prec == "fp64" else r32
+    grid, psf, V, F, T = _case_small()
+    Td = _cuda(T)
+    flat = np.repeat(V[:1], len(V), axis=0)  # every vertex at one point: zero area, zero volume
+    with pytest.raises(DeltaMicError, match="DM_ERR_DEGENERATE"):
+        r.loss_and_grad(_cuda(flat), _cuda(F), grid, psf, Td, "mse")
+    with pytest.raises(DeltaMicError, match="DM_ERR_DEGENERATE"):  # inward: negative volume
+        r.loss_and_grad(_cuda(V), _cuda(F[:, ::-1].copy()), grid, psf, Td, "mse", label="volume")
+    with pytest.raises(DeltaMicError, match="DM_ERR_DEGENERATE"):
+        r.loss_and_grad(_cuda(V), _cuda(F), grid, psf, Td, "mse",
+                        weights=torch.zeros(len(F), dtype=torch.float32).cuda())
+    # an asynchronous call reports it at the next synchronisation
+    r.render(_cuda(flat), _cuda(F), grid, psf)
+    with pytest.raises(DeltaMicError, match="DM_ERR_DEGENERATE"):
+        r.sync()
+    img = r.render(_cuda(V), _cuda(F), grid, psf)  # the context stays usable
+    r.sync()
+    assert torch.isfinite(img).all()
+    # the debug check, on host and on device arrays
+    for dev in (False, True):
+        cv = (lambda x: _cuda(x)) if dev else (lambda x: x)
+        r.check_mesh(cv(V), cv(F), label="volume")
+        r.check_mesh(cv(V), cv(F[:-1].copy()), label="surface")  # an open surface is fine
+        with pytest.raises(DeltaMicError, match="DM_ERR_OPEN_MESH"):
+            r.check_mesh(cv(V), cv(F[:-1].copy()), label="volume")  # one face missing
+        flipped = F.copy()
+        flipped[0] = flipped[0, ::-1]
+        with pytest.raises(DeltaMicError, match="DM_ERR_OPEN_MESH"):
+            r.check_mesh(cv(V), cv(flipped), label="volume")  # one face turned inward
+        with pytest.raises(DeltaMicError, match="DM_ERR_DEGENERATE"):
+            r.check_mesh(cv(V), cv(F[:, ::-1].copy()), label="volume")
+        bad = F.copy()
+        bad[0, 0] = -1
+        with pytest.raises(DeltaMicError, match="DM_ERR_ARG"):
+            r.check_mesh(cv(V), cv(bad))
+
+
 @pytest.mark.parametrize("wkind", ["interface", "random"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_weighted_density_matches_oracle(wkind, prec, r64, r32):

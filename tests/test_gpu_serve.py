@@ -160,6 +160,11 @@ def test_invalid_jobs_are_refused(setup):
                   (np.ones(n_t), {"label": "volume"})):
         with pytest.raises(RuntimeError, match="DM_ERR_ARG"):
             s.submit(**dict(jobs[1], weights=w, **kw))
+    # degenerate and (volume label) open meshes are refused at submit, not in a running batch
+    with pytest.raises(RuntimeError, match="DM_ERR_DEGENERATE"):
+        s.submit(**dict(jobs[1], V=np.repeat(jobs[1]["V"][:1], len(jobs[1]["V"]), axis=0)))
+    with pytest.raises(RuntimeError, match="DM_ERR_OPEN_MESH"):
+        s.submit(**dict(jobs[1], F=jobs[1]["F"][:-1].copy(), label="volume"))
     s.shutdown()
 
 
