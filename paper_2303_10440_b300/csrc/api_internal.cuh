@@ -294,6 +294,7 @@ struct Sizes {
     int64_t nH, N, n_v, n_t, n_t_pad, M_max, M_pad;
     int n_chunks, nacc;
     bool band;  // narrow band active (tau > 0)
+    bool fwd_split = true;  // room for the forward's triangle-split partial spectra (not in served jobs)
 };
 
 struct Bufs {
@@ -301,7 +302,7 @@ struct Bufs {
     double* partial;   // block partials (norm / loss / gather)
     void* tris;
     void* S;
-    void* S_part;  // FP32 forward: partial spectra of triangle splits (small bands)
+    void* S_part;  // FP32 forward: partial spectra of its triangle splits
     void* spec;
     void* image;
     void* resid;
@@ -330,7 +331,8 @@ size_t layout(const Sizes& z, Arena& A, Bufs& b, bool stageV, bool stageF, bool 
     b.partial = A.take<double>(nparts);
     b.tris = A.take<char>(z.n_t_pad * (z.f64 ? sizeof(TriF64) : sizeof(TriF32)));
     b.S = A.take<char>(z.M_max * 2 * R);
-    b.S_part = z.f64 ? nullptr : A.take<char>(fwd_partial_elems(z.M_max, z.sm_count) * sizeof(float2));
+    b.S_part = z.f64 || !z.fwd_split ? nullptr
+                                     : A.take<char>(fwd_partial_elems(z.M_max, z.sm_count) * sizeof(float2));
     b.spec = A.take<char>(z.nH * 2 * R);
     b.image = A.take<char>(z.N * R);
     b.resid = A.take<char>(z.N * R);

@@ -622,7 +622,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, MODE == 0 ? 5 : 4) k_adj_batch_f3
 
 }  // namespace
 
-int fwd_target_units(int sm_count) { return 8 * sm_count; }
+// Work units of the forward: at least ~112 per SM (28 per resident block). Units are equal in cost
+// and handed out as blocks free up, so the SMs finish within about one unit of each other: with
+// 8 units per SM the last, partly filled round of blocks cost 6% of the 128^3 forward; 56 and 112
+// per SM took it from 11.9 to 11.1 and 11.05 ms (224 was slower again: each unit then covers few
+// triangle tiles). The triangle splits this makes are summed in FP64 in a fixed order.
+int fwd_target_units(int sm_count) { return 112 * sm_count; }
 
 size_t fwd_partial_elems(int64_t M_max, int sm_count) {
     const int64_t fb = (M_max + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
@@ -661,7 +666,11 @@ cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t, const Freq
 int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count) {
     const int64_t tblocks = (n_t + ADJ_THREADS - 1) / ADJ_THREADS;
     const int64_t ftiles = (M_max + ADJ_FTILE - 1) / ADJ_FTILE;
-    const int64_t target = (int64_t)sm_count * 8;  // enough resident blocks to fill every SM
+    // ~128 (triangle block, frequency chunk) units per SM, so that the SMs finish within a small
+    // fraction of the launch of each other (8 per SM left 10% of the 128^3 adjoint in the last,
+    // partly filled round of blocks: 20.9 -> 18.3 ms at 128 per SM); the chunks' partial sums are
+    // added afterwards in a fixed order
+    const int64_t target = (int64_t)sm_count * 128;
     int64_t c = (target + tblocks - 1) / tblocks;
     if (c < 1) c = 1;
     if (c > ftiles) c = ftiles;

@@ -218,6 +218,7 @@ bool setup_job(dm_server* S, SJob* J) {
     dm_ctx* ctx = S->ctx;
     Sizes z = make_sizes(ctx, &J->grid, (int64_t)J->V.size() / 3, (int64_t)J->F.size() / 3, J->psf.band_tau > 0,
                          J->label);
+    z.fwd_split = false;  // the batched forward takes whole triangle lists
     const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
     J->chunk_tiles = job_chunk_tiles(z, S->chunk_tiles, ctx->sm_count);
     z.n_chunks = (int)((ftiles + J->chunk_tiles - 1) / J->chunk_tiles);  // fixed per job
@@ -862,6 +863,7 @@ dm_status dm_server_submit(dm_server* S, const dm_job* job, int64_t* job_id) {
     J->lr_decay = job->lr_decay > 0 ? job->lr_decay : 1.0;
     // a job whose state can never fit the arena is refused now rather than queued forever
     Sizes z = make_sizes(S->ctx, &job->grid, job->n_v, job->n_t, job->psf.band_tau > 0, job->label);
+    z.fwd_split = false;
     const int64_t ftiles = (z.M_max + ADJ_FTILE - 1) / ADJ_FTILE;
     const int ct = job_chunk_tiles(z, S->chunk_tiles, S->ctx->sm_count);
     z.n_chunks = (int)((ftiles + ct - 1) / ct);
