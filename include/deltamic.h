@@ -356,7 +356,7 @@ typedef struct {
     int32_t max_jobs;      /* jobs resident on the device at once (batch slots), >= 1 */
     size_t memory_bytes;   /* device arena for job state (0: half of the free device memory) */
     int32_t chunk_tiles;   /* most adjoint frequency tiles (256 frequencies) per work unit (0: 1024); each
-                              job uses fewer so that it alone yields ~8 units per SM */
+                              job uses fewer so that it alone yields ~64 units per SM */
     int32_t policy;        /* DM_SCHED_FIFO or DM_SCHED_SHORTEST */
     double batch_terms;    /* DM_SCHED_SHORTEST: most triangle-frequency terms per step that one iteration
                               takes on (jobs in policy order; the first always runs); <= 0: no limit */
