@@ -480,7 +480,7 @@ dm_status dm_meshft_adjoint(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* gri
     } else {
         LAUNCH(1, launch_adj_f32(mesh->label, (const TriF32*)b.tris, mesh->n_t, n_t_pad, (const FreqF32*)b.fr, nullptr,
                                  M, (float*)b.adjp, nc, ctx->d_err, st));
-        LAUNCH(1, launch_reduce_chunks<float>((const float*)b.adjp, nc, nacc, mesh->n_t, n_t_pad, b.acc, st));
+        LAUNCH(1, launch_reduce_chunks<float>((const float*)b.adjp, nc, nacc, mesh->n_t, n_t_pad, b.acc, st, nullptr, M));
     }
     LAUNCH(1, launch_assemble(mesh->label, V, F, mesh->n_t, mesh->n_v, W, G, b.acc, b.d_params + 30, b.contrib, st));
     LAUNCH(4, launch_csr(F, mesh->n_t, mesh->n_v, b.cnt, b.ptr, b.ent, ctx->d_err, st));

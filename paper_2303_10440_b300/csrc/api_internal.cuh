@@ -513,7 +513,8 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
     const int64_t tpad = sizeof(R) == 4 ? z.n_t_pad : z.n_t;
     {
         Stage sg(ctx, DM_STAGE_REDUCE, st);
-        LAUNCH(1, launch_reduce_chunks<R>((const R*)b.adjp, z.n_chunks, z.nacc, z.n_t, tpad, b.acc, st));
+        LAUNCH(1, launch_reduce_chunks<R>((const R*)b.adjp, z.n_chunks, z.nacc, z.n_t, tpad, b.acc, st,
+                                          sizeof(R) == 4 ? fs.dM : nullptr, sizeof(R) == 4 ? z.M_max : -1));
     }
     (void)d_coef;
     Stage sg(ctx, DM_STAGE_ASSEMBLE, st);

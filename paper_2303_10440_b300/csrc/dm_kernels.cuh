@@ -200,10 +200,12 @@ template <class R, class FR>
 cudaError_t launch_prep_raw(int mode, const Cx<R>* G, const int32_t* nlist, int64_t M, const Geom& g, FR* fr,
                             int64_t M_pad, double* partial, int* n_blocks_out, cudaStream_t st);
 
-// Sum per-chunk partial accumulators: acc[t][k] = sum_c partial[c][k][t].
+// Sum per-chunk partial accumulators: acc[t][k] = sum_c partial[c][k][t]. M_max >= 0 (FP32 single-job
+// adjoint): only the chunks that hold band tiles are read (the band size *dM, or M_max when dM is
+// NULL); M_max < 0: every chunk.
 template <class R>
 cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const int64_t* dM = nullptr, int64_t M_max = -1);
 
 // Per-corner gradient contributions, then the per-vertex gather through the vertex star.
 cudaError_t launch_assemble(int mode, const double* V, const int32_t* F, int64_t n_t, int64_t n_v, const float* wts,

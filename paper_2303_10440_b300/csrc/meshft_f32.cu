@@ -358,7 +358,7 @@ __device__ __forceinline__ void fwd_units(const FreqSrc& fs, int n_tiles, int ta
                                           int& splits) {
     M = fs.dM ? *fs.dM : fs.M;
     fb = (M + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
-    splits = fwd_splits(fb, n_tiles, target);
+    splits = fwd_splits(fb, (n_tiles + 3) / 4, target);  // at least ~4 triangle tiles per split
 }
 
 template <int MODE, bool EXPLICIT>
@@ -411,7 +411,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
                                           const FreqPairF32* __restrict__ fr, int f0, int f1, int64_t tblock,
                                           float* __restrict__ out_chunk, int* __restrict__ err,
                                           FreqPairF32 (*stage)[kAdjPairs], uint64_t* full, uint64_t* empty,
-                                          float* acc_s) {
+                                          float* acc_s, bool write_empty) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
     constexpr int PAIRS = kAdjPairs;
     const int tid = threadIdx.x;
@@ -527,7 +527,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
         };
         run_tile_pipeline<kAdjStages, kAdjPairs>(fr + (int64_t)f0 * PAIRS, f1 - f0, stage, full, empty, err, consume);
     }
-    if (t < n_t_pad) {
+    if (t < n_t_pad && (f1 > f0 || write_empty)) {
         float* out = out_chunk + t;
 #pragma unroll
         for (int k = 0; k < NACC; ++k) out[(int64_t)k * n_t_pad] = t < n_t ? tot[k * ADJ_THREADS] : 0.f;
@@ -550,8 +550,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     const int f0 = blockIdx.y * tpc;
     const int f1 = min(f0 + tpc, n_ftiles);
     __shared__ float acc_s[2 * NACC * ADJ_THREADS];
+    // a chunk past the band's last tile writes nothing: the chunk reduction leaves such chunks out
     adj_block<MODE>(tris, n_t, n_t_pad, fr, f0, f1, blockIdx.x, partial + (int64_t)blockIdx.y * NACC * n_t_pad, err,
-                    stage, full, empty, acc_s);
+                    stage, full, empty, acc_s, false);
 }
 
 // ------------------------------------------------------------------------------------- batched
@@ -613,7 +614,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, MODE == 0 ? 5 : 4) k_adj_batch_f3
         const int f1 = min(f0 + J.chunk_tiles, n_ftiles);
         float* out = J.partial + (int64_t)U.b * NACC * J.n_t_pad;
         const bool used = adj_block<MODE>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty,
-                                          acc_s);
+                                          acc_s, true);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kAdjStages);
         __syncthreads();

@@ -404,14 +404,24 @@ __global__ void __launch_bounds__(NT) k_prep_raw(int mode, const Cx<R>* __restri
 // acc[t][k] = sum over chunks c of partial[c][k][t]. A block covers 32 triangles (lanes) of one
 // accumulator k (blockIdx.y) with RC_WARPS warps: warp w adds the chunks c = w, w + RC_WARPS, ... in
 // that order into four interleaved sums, and warp 0 adds the warps' sums in warp order. The order is
-// fixed by (n_chunks, RC_WARPS) alone, so the result is reproducible, and the chunk loop runs
-// RC_WARPS x 4 loads deep instead of one chain per triangle (a small mesh has ~8 x SMs chunks).
+// fixed by the chunk count alone, so the result is reproducible, and the chunk loop runs
+// RC_WARPS x 4 loads deep instead of one chain per triangle (a small mesh has thousands of chunks).
+// M_max >= 0: the chunks cut the band's ADJ_FTILE tiles (the device count *dM when given, else
+// M_max) into n_chunks runs of ceil(tiles / n_chunks); chunks past the last tile hold no sums (the
+// adjoint does not write them) and are left out.
 constexpr int RC_WARPS = 16;
 template <class R>
 __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __restrict__ partial, int n_chunks, int nacc,
                                                                  int64_t n_t, int64_t n_t_pad,
-                                                                 double* __restrict__ acc) {
+                                                                 double* __restrict__ acc,
+                                                                 const int64_t* __restrict__ dM, int64_t M_max) {
     __shared__ double sh[RC_WARPS][32];
+    if (M_max >= 0) {
+        const int64_t M = dM ? *dM : M_max;
+        const int64_t tiles = (M + ADJ_FTILE - 1) / ADJ_FTILE;
+        const int64_t tpc = (tiles + n_chunks - 1) / n_chunks;
+        n_chunks = tpc > 0 ? (int)min((int64_t)n_chunks, (tiles + tpc - 1) / tpc) : 0;
+    }
     const int lane = threadIdx.x, w = threadIdx.y;
     const int64_t t = (int64_t)blockIdx.x * 32 + lane;
     const int k = (int)blockIdx.y;
@@ -733,14 +743,16 @@ template cudaError_t launch_prep_raw<double, FreqF64>(int, const Cx<double>*, co
 
 template <class R>
 cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const int64_t* dM, int64_t M_max) {
     if (n_t <= 0 || nacc <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((n_t + 31) / 32), (unsigned)nacc), block(32, RC_WARPS);
-    k_reduce_chunks<R><<<grid, block, 0, st>>>(partial, n_chunks, nacc, n_t, n_t_pad, acc);
+    k_reduce_chunks<R><<<grid, block, 0, st>>>(partial, n_chunks, nacc, n_t, n_t_pad, acc, dM, M_max);
     return cudaGetLastError();
 }
-template cudaError_t launch_reduce_chunks<float>(const float*, int, int, int64_t, int64_t, double*, cudaStream_t);
-template cudaError_t launch_reduce_chunks<double>(const double*, int, int, int64_t, int64_t, double*, cudaStream_t);
+template cudaError_t launch_reduce_chunks<float>(const float*, int, int, int64_t, int64_t, double*, cudaStream_t,
+                                                 const int64_t*, int64_t);
+template cudaError_t launch_reduce_chunks<double>(const double*, int, int, int64_t, int64_t, double*, cudaStream_t,
+                                                  const int64_t*, int64_t);
 
 cudaError_t launch_assemble(int mode, const double* V, const int32_t* F, int64_t n_t, int64_t n_v, const float* wts,
                             const Geom& g, const double* acc, const double* d_coef, double* contrib, cudaStream_t st) {
