@@ -104,6 +104,8 @@ struct Geom {
 cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, float2* S, float2* S_part, int sm_count, int* d_err, cudaStream_t st);
 size_t fwd_partial_elems(int64_t M_max, int sm_count);
+// Work units the forward aims for on sm_count SMs (frequency blocks x triangle splits).
+int fwd_target_units(int sm_count);
 cudaError_t launch_adj_f32(int mode, const TriF32* tris, int64_t n_t, int64_t n_t_pad, const FreqF32* fr,
                            const int64_t* dM, int64_t M_max, float* partial, int n_chunks, int* d_err, cudaStream_t st);
 int adj_chunks_f32(int64_t n_t, int64_t M_max, int sm_count);
@@ -118,6 +120,8 @@ struct BatchFwdJob {
     float tp[3];
     const double* d_vol;
     float2* S;
+    int splits;      // triangle splits per frequency block (fixed per job); > 1: partial spectra in S_part
+    float2* S_part;  // [splits][M] with M the job's band size on the device
 };
 struct BatchAdjJob {
     const TriF32* tris;
@@ -136,10 +140,15 @@ struct BatchUnit {
     int pad;
 };
 // One launch per label (mode: DM_SURFACE / DM_VOLUME); every unit's job must have that label.
+// Forward units are (job, frequency block, triangle split); a job with splits > 1 needs
+// launch_fwd_reduce_splits afterwards.
 cudaError_t launch_fwd_batch_f32(int mode, const BatchFwdJob* jobs, const BatchUnit* units, int n_units, int* counter,
                                  int grid, int* d_err, cudaStream_t st);
 cudaError_t launch_adj_batch_f32(int mode, const BatchAdjJob* jobs, const BatchUnit* units, int n_units, int* counter,
                                  int grid, int* d_err, cudaStream_t st);
+// S[m] = sum over the `splits` partial spectra in S_part (fixed order, FP64), m < the band size.
+cudaError_t launch_fwd_reduce_splits(const FreqSrc& fs, int splits, const float2* S_part, float2* S, int sm_count,
+                                     cudaStream_t st);
 int batch_blocks_per_sm_fwd(int mode);
 int batch_blocks_per_sm_adj(int mode);
 constexpr int FWD_BLOCK_FREQS = 2 * FWD_THREADS;  // band frequencies per forward block

@@ -384,11 +384,13 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_f32(const TriF32* __rest
 }
 
 // S[m] = sum over the triangle splits of the partial spectra (fixed order, FP64); nothing when unsplit.
-__global__ void __launch_bounds__(256) k_fwd_reduce(FreqSrc fs, int n_tiles, int target,
+// fixed_splits > 0: that many splits (a served job's own count) instead of the band-derived one.
+__global__ void __launch_bounds__(256) k_fwd_reduce(FreqSrc fs, int n_tiles, int target, int fixed_splits,
                                                     const float2* __restrict__ S_part, float2* __restrict__ S) {
     int64_t M, fb;
     int splits;
     fwd_units(fs, n_tiles, target, M, fb, splits);
+    if (fixed_splits > 0) splits = fixed_splits;
     if (splits == 1) return;
     for (int64_t m = (int64_t)blockIdx.x * 256 + threadIdx.x; m < M; m += (int64_t)gridDim.x * 256) {
         double sx = 0.0, sy = 0.0;
@@ -582,8 +584,12 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_batch_f32(const BatchFwd
         if (u >= n_units) break;
         const BatchUnit U = units[u];
         const BatchFwdJob& J = jobs[U.job];
-        const bool used = fwd_block<MODE, false>(J.tris, J.n_tiles, J.last, J.fs, J.tp[0], J.tp[1], J.tp[2], J.d_vol,
-                                                 J.S, err, U.a, stage, full, empty);
+        const int t0 = (int)((int64_t)J.n_tiles * U.b / J.splits), t1 = (int)((int64_t)J.n_tiles * (U.b + 1) / J.splits);
+        float2* out = J.S;
+        if (J.splits > 1) out = J.S_part + (int64_t)U.b * (J.fs.dM ? *J.fs.dM : J.fs.M);
+        const bool used = fwd_block<MODE, false>(J.tris + (int64_t)t0 * kFwdTile, t1 - t0,
+                                                 t1 == J.n_tiles ? J.last : kFwdTile, J.fs, J.tp[0], J.tp[1], J.tp[2],
+                                                 J.d_vol, out, err, U.a, stage, full, empty, U.b == 0);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kFwdStages);
         __syncthreads();
@@ -660,7 +666,7 @@ cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t, const Freq
     if (mode == 1 && ex)
         k_fwd_f32<1, true><<<grid, FWD_THREADS, 0, st>>>(tris, n_tiles, last, fs, tpx, tpy, tpz, d_vol, S, S_part,
                                                          target, d_err);
-    if (S_part) k_fwd_reduce<<<4 * sm_count, 256, 0, st>>>(fs, n_tiles, target, S_part, S);
+    if (S_part) k_fwd_reduce<<<4 * sm_count, 256, 0, st>>>(fs, n_tiles, target, 0, S_part, S);
     return cudaGetLastError();
 }
 
@@ -711,6 +717,13 @@ cudaError_t launch_fwd_batch_f32(int mode, const BatchFwdJob* jobs, const BatchU
         k_fwd_batch_f32<0><<<grid, FWD_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
     else
         k_fwd_batch_f32<1><<<grid, FWD_THREADS, 0, st>>>(jobs, units, n_units, counter, d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_reduce_splits(const FreqSrc& fs, int splits, const float2* S_part, float2* S, int sm_count,
+                                     cudaStream_t st) {
+    if (splits <= 1) return cudaSuccess;
+    k_fwd_reduce<<<4 * sm_count, 256, 0, st>>>(fs, 1, 0, splits, S_part, S);
     return cudaGetLastError();
 }
 

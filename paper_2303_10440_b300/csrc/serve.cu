@@ -93,6 +93,8 @@ struct SJob {
     int optimizer = DM_OPT_ADAM;
     double lambda = 50.0;
     double lr_decay = 1.0;  // per-step factor on the learning rates
+    int fsplits = 1;                 // triangle splits of the batched forward (fixed by the job's sizes)
+    float2* S_part = nullptr;        // [fsplits][M] partial spectra when fsplits > 1
     int state = DM_JOB_QUEUED;
     int steps_done = 0;
     double terms_step = 0;  // triangle-frequency terms of one step (triangles x half-spectrum size)
@@ -143,6 +145,12 @@ int job_chunk_tiles(const Sizes& z, int max_tiles, int sm_count) {
 size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, double** mom, double** hist,
                   SJob* J) {
     layout(z, A, b, true, true, !J->W.empty(), true, false);
+    // forward units: (frequency block, triangle split), the split count chosen as for a single fit
+    // (about 112 units per SM for the job alone, about four tiles per split) from the job's own sizes
+    const int64_t fb = (z.M_max + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
+    const int n_tiles = (int)((z.n_t + FWD_REC_TILE - 1) / FWD_REC_TILE);
+    J->fsplits = fwd_splits(fb, (n_tiles + 3) / 4, fwd_target_units(z.sm_count));
+    J->S_part = J->fsplits > 1 ? A.take<float2>((size_t)J->fsplits * z.M_max) : nullptr;
     *mom = A.take<double>(6 * n_v + 8);
     *hist = A.take<double>(steps);
     if (J->optimizer == DM_OPT_LARGE_STEPS) {
@@ -327,6 +335,8 @@ bool rebuild_units(dm_server* S) {
         for (int a = 0; a < 3; ++a) f.tp[a] = (float)(2.0 * M_PI / G.L[a]);
         f.d_vol = b.d_params + 16;
         f.S = (float2*)b.S;
+        f.splits = J->fsplits;
+        f.S_part = J->S_part;
         BatchAdjJob& a = S->aj[j];
         a.tris = (const TriF32*)b.tris;
         a.n_t = z.n_t;
@@ -348,7 +358,8 @@ bool rebuild_units(dm_server* S) {
     S->nf_surf = S->na_surf = 0;
     for (int j : order) {
         const int64_t nb = (S->run[j]->z.nH + FWD_BLOCK_FREQS - 1) / FWD_BLOCK_FREQS;
-        for (int64_t k = 0; k < nb; ++k) S->uf.push_back({j, (int)k, 0, 0});
+        for (int64_t k = 0; k < nb; ++k)
+            for (int sp = 0; sp < S->run[j]->fsplits; ++sp) S->uf.push_back({j, (int)k, sp, 0});
         if (S->run[j]->label == DM_SURFACE) S->nf_surf = S->uf.size();
     }
     for (int j : order) {
@@ -439,6 +450,8 @@ bool iterate(dm_server* S, bool sync) {
         fs.set_dims(J->grid.n[0], J->grid.n[1], J->grid.n[2]);
         const int* n = J->grid.n;
         int nl = 0, ng = 0;
+        ok &= launch_fwd_reduce_splits(fs, J->fsplits, J->S_part, (float2*)b.S, ctx->sm_count, js) == cudaSuccess;
+        if (J->fsplits > 1) g_launches += 1;
         ok &= launch_scatter<float>((const Cx<float>*)b.S, fs, b.d_params, J->psf.kind, b.d_params + 16, G,
                                     (Cx<float>*)b.spec, z.band, js) == cudaSuccess;
         ok &= launch_c2r<float>((const Cx<float>*)b.spec, (Cx<float>*)b.spec, (float*)b.image, n[0], n[1], n[2], J->ax,
