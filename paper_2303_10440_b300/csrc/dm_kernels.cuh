@@ -97,9 +97,10 @@ struct Geom {
 
 // ---------------------------------------------------------------- launchers (return cudaGetLastError())
 // Mesh transform (FP32 mixed path).
-// S_part (nullable): room for fwd_partial_elems(fs.M, sm_count) partial spectra; when given, a band with
-// fewer than about 8 x SMs frequency blocks splits the triangle list over several blocks and the
-// partial spectra are summed in a fixed order; when NULL every block takes the whole triangle list.
+// S_part (nullable): room for fwd_partial_elems(fs.M, sm_count) partial spectra; when given, the
+// triangle list of each frequency block is split so that the launch has about fwd_target_units
+// units (at least ~4 triangle tiles per split) and the partial spectra are summed in a fixed order;
+// when NULL every block takes the whole triangle list.
 // n_t: real triangles; the records are padded with zeros to whole 64-record tiles.
 cudaError_t launch_fwd_f32(int mode, const TriF32* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, float2* S, float2* S_part, int sm_count, int* d_err, cudaStream_t st);
