@@ -212,7 +212,7 @@ cudaError_t launch_prep_raw(int mode, const Cx<R>* G, const int32_t* nlist, int6
 
 // Sum per-chunk partial accumulators: acc[t][k] = sum_c partial[c][k][t]. M_max >= 0 (FP32 single-job
 // adjoint): only the chunks that hold band tiles are read (the band size *dM, or M_max when dM is
-// NULL); M_max < 0: every chunk.
+// NULL; the others hold zeros); M_max < 0: every chunk.
 template <class R>
 cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
                                  cudaStream_t st, const int64_t* dM = nullptr, int64_t M_max = -1);

@@ -413,7 +413,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
                                           const FreqPairF32* __restrict__ fr, int f0, int f1, int64_t tblock,
                                           float* __restrict__ out_chunk, int* __restrict__ err,
                                           FreqPairF32 (*stage)[kAdjPairs], uint64_t* full, uint64_t* empty,
-                                          float* acc_s, bool write_empty) {
+                                          float* acc_s) {
     constexpr int NACC = MODE == 0 ? NACC_SURF : NACC_VOL;
     constexpr int PAIRS = kAdjPairs;
     const int tid = threadIdx.x;
@@ -529,7 +529,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
         };
         run_tile_pipeline<kAdjStages, kAdjPairs>(fr + (int64_t)f0 * PAIRS, f1 - f0, stage, full, empty, err, consume);
     }
-    if (t < n_t_pad && (f1 > f0 || write_empty)) {
+    if (t < n_t_pad) {
         float* out = out_chunk + t;
 #pragma unroll
         for (int k = 0; k < NACC; ++k) out[(int64_t)k * n_t_pad] = t < n_t ? tot[k * ADJ_THREADS] : 0.f;
@@ -538,7 +538,7 @@ __device__ __forceinline__ bool adj_block(const TriF32* __restrict__ tris, int64
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restrict__ tris, int64_t n_t,
+__global__ void __launch_bounds__(ADJ_THREADS, MODE == 0 ? 5 : 4) k_adj_f32(const TriF32* __restrict__ tris, int64_t n_t,
                                                          int64_t n_t_pad, const FreqPairF32* __restrict__ fr,
                                                          const int64_t* __restrict__ dM, int64_t M_max,
                                                          float* __restrict__ partial, int* __restrict__ err) {
@@ -552,9 +552,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_f32(const TriF32* __restric
     const int f0 = blockIdx.y * tpc;
     const int f1 = min(f0 + tpc, n_ftiles);
     __shared__ float acc_s[2 * NACC * ADJ_THREADS];
-    // a chunk past the band's last tile writes nothing: the chunk reduction leaves such chunks out
+    // a chunk past the band's last tile writes zeros, which the chunk reduction leaves out
     adj_block<MODE>(tris, n_t, n_t_pad, fr, f0, f1, blockIdx.x, partial + (int64_t)blockIdx.y * NACC * n_t_pad, err,
-                    stage, full, empty, acc_s, false);
+                    stage, full, empty, acc_s);
 }
 
 // ------------------------------------------------------------------------------------- batched
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, MODE == 0 ? 5 : 4) k_adj_batch_f3
         const int f1 = min(f0 + J.chunk_tiles, n_ftiles);
         float* out = J.partial + (int64_t)U.b * NACC * J.n_t_pad;
         const bool used = adj_block<MODE>(J.tris, J.n_t, J.n_t_pad, J.fr, f0, f1, U.a, out, err, stage, full, empty,
-                                          acc_s, true);
+                                          acc_s);
         __syncthreads();
         if (used && threadIdx.x == 0) inval_barriers(full, empty, kAdjStages);
         __syncthreads();

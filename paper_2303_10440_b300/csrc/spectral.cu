@@ -407,8 +407,8 @@ __global__ void __launch_bounds__(NT) k_prep_raw(int mode, const Cx<R>* __restri
 // fixed by the chunk count alone, so the result is reproducible, and the chunk loop runs
 // RC_WARPS x 4 loads deep instead of one chain per triangle (a small mesh has thousands of chunks).
 // M_max >= 0: the chunks cut the band's ADJ_FTILE tiles (the device count *dM when given, else
-// M_max) into n_chunks runs of ceil(tiles / n_chunks); chunks past the last tile hold no sums (the
-// adjoint does not write them) and are left out.
+// M_max) into n_chunks runs of ceil(tiles / n_chunks); chunks past the last tile hold zeros and are
+// left out.
 constexpr int RC_WARPS = 16;
 template <class R>
 __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __restrict__ partial, int n_chunks, int nacc,
