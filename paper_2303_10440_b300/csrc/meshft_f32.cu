@@ -570,7 +570,7 @@ __device__ __forceinline__ void inval_barriers(uint64_t* full, uint64_t* empty, 
 // depend on which block runs it or on the other jobs in the batch. One instantiation per label
 // keeps each at its own register count (a kernel holding both paths takes the larger).
 template <int MODE>
-__global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_batch_f32(const BatchFwdJob* __restrict__ jobs,
+__global__ void __launch_bounds__(FWD_THREADS, MODE == 0 ? 4 : 3) k_fwd_batch_f32(const BatchFwdJob* __restrict__ jobs,
                                                                const BatchUnit* __restrict__ units, int n_units,
                                                                int* __restrict__ counter, int* __restrict__ err) {
     __shared__ __align__(128) TriF32 stage[kFwdStages][kFwdTile];
