@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 path's step beside the FP32 one")
     p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger", "robust", "fft", "scaling", "mufu"],
                    default="step",
                    help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
@@ -517,12 +518,38 @@ def run_ours(args):
         out["e2e"] = e2e_through_host_buffers(r, case, grid, psf, T, terms_step, args, dev, world)
     if not args.no_serve:
         out["serving"] = serving_leg(args, dev)
+    if rank == 0 and args.precision == "fp32" and not args.no_fp64:
+        out["fp64_plain"] = fp64_plain_step(case, grid, psf, T, terms_step, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(case)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def fp64_plain_step(case, grid, psf, T_dev, terms_step, dev):
+    """The plain FP64 path beside the FP32 one: the same fit step (dm_loss_and_grad on device
+    buffers) in an FP64 context, one warm-up and one CUDA-event-timed step."""
+    import torch
+
+    from paper_2303_10440_b300 import Renderer
+
+    r64 = Renderer("fp64", device=dev.index or 0)
+    Vd = torch.as_tensor(case.V_init).to(dev)
+    Fd = torch.as_tensor(case.F).to(dev)
+    T64 = T_dev.double()
+    r64.loss_and_grad(Vd, Fd, grid, psf, T64, "mse")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record()
+    r64.loss_and_grad(Vd, Fd, grid, psf, T64, "mse")
+    b.record()
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b)
+    r64.close()
+    return {"value": terms_step / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 1,
+            "note": "same workload and step through the FP64 context (plain path); FP64 rate-bound on B300"}
 
 
 def e2e_through_host_buffers(r, case, grid, psf, T_dev, terms_step, args, dev, world):
