@@ -19,10 +19,11 @@
 // comes from exact integer reduction (n . U mod 2^32) and the offset from the
 // FP32 edge projections.
 //
-// Forward: a thread holds two band frequencies in registers; the block walks the
-// triangle list (or, for a small band, a slice of it) in tiles bulk-copied (TMA)
-// into a ring of shared-memory stages with full/empty mbarriers. FP32 sums within
-// a tile, Kahan across tiles; slices are summed afterwards in FP64 in a fixed order.
+// Forward: a thread holds two band frequencies in registers; the block walks a slice
+// of the triangle list (slices sized so that the launch has ~112 units per SM) in
+// tiles bulk-copied (TMA) into a ring of shared-memory stages with full/empty
+// mbarriers. FP32 sums within a tile, Kahan across tiles; slices are summed
+// afterwards in FP64 in a fixed order.
 // Adjoint: a thread holds one triangle; the block walks a chunk of the band in
 // tiles of frequency-pair records bulk-copied the same way, summing the triangle's
 // 10 (surface) or 12 (volume) terms of a tile in registers and carrying the running
