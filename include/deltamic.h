@@ -125,7 +125,8 @@ dm_status dm_workspace_size(const dm_ctx* ctx, const dm_grid* grid, int64_t n_v,
 dm_status dm_reserve(dm_ctx* ctx, size_t bytes);
 /* Synchronise `stream` and report any device-side fault recorded since the last check. */
 dm_status dm_sync(dm_ctx* ctx, void* stream);
-/* Debug check of a mesh (host or device arrays; synchronises): DM_ERR_ARG for a face index outside
+/* Debug check of a mesh (host or device arrays; synchronises; ctx may be NULL for host arrays, and
+ * then no GPU is needed): DM_ERR_ARG for a face index outside
  * [0, n_v), a non-finite vertex or density, or tri_weight with the volume label; DM_ERR_DEGENERATE
  * for a zero total (weighted) area or a non-positive enclosed volume; DM_ERR_OPEN_MESH when the
  * volume label's mesh is not closed and consistently oriented (every directed edge p -> q used

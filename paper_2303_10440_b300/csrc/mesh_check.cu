@@ -92,10 +92,16 @@ extern "C" {
 
 dm_status dm_check_mesh(dm_ctx* ctx, const dm_mesh* mesh) {
     using namespace dm;
-    if (!ctx || !mesh) return DM_ERR_ARG;
-    ctx->err.clear();
+    if (!mesh) return DM_ERR_ARG;
+    if (ctx) ctx->err.clear();
     if (!mesh->V || !mesh->F || mesh->n_v < 3 || mesh->n_t < 1)
         return fail(ctx, DM_ERR_ARG, "mesh: V and F required, n_v >= 3, n_t >= 1");
+    if (!ctx) {
+        // no context: host arrays only, and no CUDA call beyond the pointer checks
+        std::string why;
+        if (is_device_ptr(mesh->V) || is_device_ptr(mesh->F) || is_device_ptr(mesh->tri_weight)) return DM_ERR_ARG;
+        return check_mesh_host(mesh->V, mesh->n_v, mesh->F, mesh->n_t, mesh->tri_weight, mesh->label, &why);
+    }
     DeviceGuard dg(ctx->device);
     // device arrays are copied to the host (a debug call: it synchronises)
     std::vector<double> hV;
