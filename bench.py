@@ -923,8 +923,14 @@ def run_scaling_mode(args):
     def step_ms(V, F, grid, psf, reps=5):
         Vd, Fd = torch.as_tensor(V).to(dev), torch.as_tensor(F).to(dev)
         T = r.render(Vd * 1.01, Fd, grid, psf)
-        for _ in range(2):
+        # warm up for at least ~0.2 s of calls: a tiny case would otherwise be timed while the
+        # clocks are still rising after the CPU oracle's run
+        t_end = time.perf_counter() + 0.2
+        n_warm = 0
+        while n_warm < 2 or time.perf_counter() < t_end:
             r.loss_and_grad(Vd, Fd, grid, psf, T, "mse")
+            n_warm += 1
+        torch.cuda.synchronize()
         ts = []
         for _ in range(reps):
             flush.fill_(0.0)
