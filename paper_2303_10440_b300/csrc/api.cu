@@ -310,6 +310,7 @@ struct RawBufs {
     void* fr;
     void* adjp;
     double* acc;
+    double* red;
     double* contrib;
     int32_t* cnt;
     int32_t* ptr;
@@ -338,6 +339,7 @@ size_t raw_layout(const dm_ctx* ctx, int64_t n_v, int64_t n_t, int64_t M, int la
     b.fr = A.take<char>(M_pad * (f64 ? sizeof(FreqF64) : sizeof(FreqPairF32) / 2));
     b.adjp = A.take<char>((size_t)nc * nacc * n_t_pad * R);
     b.acc = A.take<double>(n_t * nacc);
+    b.red = A.take<double>(reduce_scratch_elems(ctx->sm_count));
     b.contrib = A.take<double>(9 * n_t);
     b.cnt = A.take<int32_t>(n_v);
     b.ptr = A.take<int32_t>(n_v + 1);
@@ -476,11 +478,13 @@ dm_status dm_meshft_adjoint(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* gri
     if (f64) {
         LAUNCH(1, launch_adj_f64(mesh->label, (const TriF64*)b.tris, mesh->n_t, (const FreqF64*)b.fr, nullptr, M,
                                  (double*)b.adjp, nc, st));
-        LAUNCH(1, launch_reduce_chunks<double>((const double*)b.adjp, nc, nacc, mesh->n_t, mesh->n_t, b.acc, st));
+        LAUNCH(1, launch_reduce_chunks<double>((const double*)b.adjp, nc, nacc, mesh->n_t, mesh->n_t, b.acc, st, nullptr,
+                                               -1, b.red, ctx->sm_count));
     } else {
         LAUNCH(1, launch_adj_f32(mesh->label, (const TriF32*)b.tris, mesh->n_t, n_t_pad, (const FreqF32*)b.fr, nullptr,
                                  M, (float*)b.adjp, nc, ctx->d_err, st));
-        LAUNCH(1, launch_reduce_chunks<float>((const float*)b.adjp, nc, nacc, mesh->n_t, n_t_pad, b.acc, st, nullptr, M));
+        LAUNCH(1, launch_reduce_chunks<float>((const float*)b.adjp, nc, nacc, mesh->n_t, n_t_pad, b.acc, st, nullptr, M,
+                                              b.red, ctx->sm_count));
     }
     LAUNCH(1, launch_assemble(mesh->label, V, F, mesh->n_t, mesh->n_v, W, G, b.acc, b.d_params + 30, b.contrib, st));
     LAUNCH(4, launch_csr(F, mesh->n_t, mesh->n_v, b.cnt, b.ptr, b.ent, ctx->d_err, st));

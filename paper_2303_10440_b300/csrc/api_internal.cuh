@@ -309,6 +309,7 @@ struct Bufs {
     void* fr;
     void* adjp;
     double* acc;
+    double* red;  // chunk-reduction slices (reduce_scratch_elems)
     double* contrib;
     int32_t* cnt;
     int32_t* ptr;
@@ -339,6 +340,7 @@ size_t layout(const Sizes& z, Arena& A, Bufs& b, bool stageV, bool stageF, bool 
     b.fr = A.take<char>(z.M_pad * (z.f64 ? sizeof(FreqF64) : sizeof(FreqPairF32) / 2));
     b.adjp = A.take<char>((size_t)z.n_chunks * z.nacc * z.n_t_pad * R);
     b.acc = A.take<double>(z.n_t * z.nacc);
+    b.red = A.take<double>(reduce_scratch_elems(z.sm_count));
     b.contrib = A.take<double>(z.n_t * 9);
     b.cnt = A.take<int32_t>(z.n_v);
     b.ptr = A.take<int32_t>(z.n_v + 1);
@@ -514,7 +516,8 @@ dm_status pipeline(dm_ctx* ctx, const Sizes& z, Bufs& b, const Inputs& in, const
     {
         Stage sg(ctx, DM_STAGE_REDUCE, st);
         LAUNCH(1, launch_reduce_chunks<R>((const R*)b.adjp, z.n_chunks, z.nacc, z.n_t, tpad, b.acc, st,
-                                          sizeof(R) == 4 ? fs.dM : nullptr, sizeof(R) == 4 ? z.M_max : -1));
+                                          sizeof(R) == 4 ? fs.dM : nullptr, sizeof(R) == 4 ? z.M_max : -1, b.red,
+                                          z.sm_count));
     }
     (void)d_coef;
     Stage sg(ctx, DM_STAGE_ASSEMBLE, st);

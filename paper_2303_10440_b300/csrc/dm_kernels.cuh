@@ -213,9 +213,13 @@ cudaError_t launch_prep_raw(int mode, const Cx<R>* G, const int32_t* nlist, int6
 // Sum per-chunk partial accumulators: acc[t][k] = sum_c partial[c][k][t]. M_max >= 0 (FP32 single-job
 // adjoint): only the chunks that hold band tiles are read (the band size *dM, or M_max when dM is
 // NULL; the others hold zeros); M_max < 0: every chunk.
+// scratch (nullable): reduce_scratch_elems(sm_count) doubles; with it a mesh of few triangles splits the
+// chunks into slices summed in a second, fixed-order pass (enough blocks for every SM).
 template <class R>
 cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
-                                 cudaStream_t st, const int64_t* dM = nullptr, int64_t M_max = -1);
+                                 cudaStream_t st, const int64_t* dM = nullptr, int64_t M_max = -1,
+                                 double* scratch = nullptr, int sm_count = 0);
+size_t reduce_scratch_elems(int sm_count);
 
 // Per-corner gradient contributions, then the per-vertex gather through the vertex star.
 cudaError_t launch_assemble(int mode, const double* V, const int32_t* F, int64_t n_t, int64_t n_v, const float* wts,

@@ -486,7 +486,8 @@ bool iterate(dm_server* S, bool sync) {
         const Geom G = make_geom(&J->grid);
         const Bufs& b = J->b;
         const Sizes& z = J->z;
-        ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, js) ==
+        ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, js,
+                                          nullptr, -1, b.red, ctx->sm_count) ==
               cudaSuccess;
         ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, b.wts, G, b.acc, b.d_params + 30, b.contrib, js) ==
               cudaSuccess;

@@ -232,38 +232,71 @@ __global__ void __launch_bounds__(NT) k_band_write(BandArgs b, const int64_t* __
 }
 
 // ---------------------------------------------------------------- transfer function and image
+// Per-thread running sum in the path's precision: FP32 with a Kahan compensation in the FP32 path
+// (B300's FP64 adds run at a small fraction of its FP32 rate, and these kernels add one term per
+// element), plain FP64 in the FP64 path; blocks then combine the per-thread sums in FP64.
+template <class R>
+struct TSum;
+template <>
+struct TSum<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+template <>
+struct TSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+
+// Wavevector component of integer frequency n in the path's precision.
+template <class R>
+__device__ __forceinline__ R wave(int n, R tp) {
+    return (R)n * tp;
+}
+
 template <class R>
 __global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, FreqSrc fs, const double* __restrict__ psf,
                                                 int kind, const double* __restrict__ d_norm, double tpx, double tpy,
                                                 double tpz, double inv_VL, Cx<R>* __restrict__ spec) {
+    __shared__ R s_scale;  // one FP64 division per block, not per frequency
+    if (threadIdx.x == 0) s_scale = (R)(inv_VL / *d_norm);
+    __syncthreads();
     const int64_t M = fs.dM ? *fs.dM : fs.M;
     const int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (m >= M) return;
     const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
     int nx, ny, nz;
     decode_h(idx, fs, nx, ny, nz);
-    const R hh = otf_r<R>(psf, kind, nx * tpx, ny * tpy, nz * tpz);
-    const R sc = hh * (R)(inv_VL / *d_norm);
+    const R hh = otf_r<R>(psf, kind, (double)wave<R>(nx, (R)tpx), (double)wave<R>(ny, (R)tpy),
+                          (double)wave<R>(nz, (R)tpz));
+    const R sc = hh * s_scale;
     const Cx<R> s = S[m];
     spec[idx] = Cx<R>{s.x * sc, s.y * sc};
 }
 
 template <class R>
 __global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* __restrict__ T, int64_t n, int kind,
-                                             R* __restrict__ resid, double* __restrict__ partial) {
+                                             R* __restrict__ resid, double* __restrict__ partial, double inv_n) {
     __shared__ double scratch[32];
-    // per voxel in the path's precision R, the sum in FP64
-    double l = 0.0;
-    const double inv_n = 1.0 / (double)n;
+    // per voxel in the path's precision R, per-thread sums as TSum, the block sum in FP64
+    TSum<R> lsum;
     const R s = kind == 1 ? (R)(2.0 * inv_n) : (R)2;
     for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
         const R t = T[j];
         const R d = I[j] - t;
         const R w = kind == 2 ? t : (R)1;
         const R wd = w * d;
-        l += (double)(wd * d);
+        lsum.add(wd * d);
         resid[j] = s * wd;
     }
+    double l = lsum.get();
     if (kind == 1) l *= inv_n;
     l = block_sum<NT>(l, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = l;
@@ -311,11 +344,15 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
     // Per frequency in the path's precision R; the sums over frequencies in FP64. Grid-stride over
     // the padded band, so each block reduces its partial sums once.
     __shared__ double scratch[32];
+    __shared__ R s_rin;  // one FP64 division per block
+    if (threadIdx.x == 0) s_rin = (R)(1.0 / *d_norm);
+    __syncthreads();
     const int64_t M = fs.dM ? *fs.dM : fs.M;
-    const R rin = (R)(1.0 / *d_norm);
+    const R rin = s_rin;
     const R cvl = (R)inv_VL;
     const R s0 = (R)psf[0], s1 = (R)psf[1], s2 = (R)psf[2];
-    double part[7] = {0, 0, 0, 0, 0, 0, 0};
+    const R tx = (R)tpx, ty = (R)tpy, tz = (R)tpz;
+    TSum<R> part[7];
     for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M_pad; m += (int64_t)gridDim.x * NT) {
         if (m >= M) {
             set_rec(fr, m, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
@@ -324,8 +361,8 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
         const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
         int nx, ny, nz;
         decode_h(idx, fs, nx, ny, nz);
-        const double xd = nx * tpx, yd = ny * tpy, zd = nz * tpz;
-        const R x = (R)xd, y = (R)yd, z = (R)zd;
+        const R x = wave<R>(nx, tx), y = wave<R>(ny, ty), z = wave<R>(nz, tz);
+        const double xd = (double)x, yd = (double)y, zd = (double)z;
         const R c = (nz == 0 || 2 * nz == fs.Nz) ? (R)1 : (R)2;
         const Cx<R> F = spec[idx];
         const R Gx = c * cvl * F.x, Gy = c * cvl * F.y;  // dL/dX
@@ -334,24 +371,24 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
         const R ux = Sm.x * rin, uy = Sm.y * rin;  // u_hat
         const R g = (Gx * ux + Gy * uy) * hh;      // Re(conj(G) X)
         if (kind == 0) {
-            part[0] += (double)(-g * s0 * x * x);
-            part[1] += (double)(-g * s1 * y * y);
-            part[2] += (double)(-g * s2 * z * z);
+            part[0].add(-g * s0 * x * x);
+            part[1].add(-g * s1 * y * y);
+            part[2].add(-g * s2 * z * z);
         } else {
             const R hg = (R)-0.5 * g;
-            part[0] += (double)(hg * x * x);
-            part[1] += (double)(hg * y * y);
-            part[2] += (double)(hg * z * z);
-            part[3] += (double)(-g * x * y);
-            part[4] += (double)(-g * x * z);
-            part[5] += (double)(-g * y * z);
+            part[0].add(hg * x * x);
+            part[1].add(hg * y * y);
+            part[2].add(hg * z * z);
+            part[3].add(-g * x * y);
+            part[4].add(-g * x * z);
+            part[5].add(-g * y * z);
         }
         R Gur = Gx * hh * rin, Gui = Gy * hh * rin;  // dL/du_hat / norm
         const bool zero = nx == 0 && ny == 0 && nz == 0;
         if (zero) {
             Gur = Gui = (R)0;  // u_hat(0) = 1 for every mesh: no gradient through xi = 0
         } else {
-            part[6] += (double)(-(Gur * ux + Gui * uy));  // -cq
+            part[6].add(-(Gur * ux + Gui * uy));  // -cq
         }
         R wr = Gur, wi = Gui;
         if (mode == 1 && !zero) {  // volume: Gw = -i Gu / |xi|^2
@@ -362,7 +399,7 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
         set_rec(fr, m, nx, ny, nz, xd, yd, zd, (double)wr, (double)wi);
     }
     for (int k = 0; k < 7; ++k) {
-        const double v = block_sum<NT>(part[k], scratch);
+        const double v = block_sum<NT>(part[k].get(), scratch);
         if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = v;
     }
     if (threadIdx.x == 0) partial[blockIdx.x * NPART + 7] = 0.0;
@@ -402,10 +439,12 @@ __global__ void __launch_bounds__(NT) k_prep_raw(int mode, const Cx<R>* __restri
 }
 
 // acc[t][k] = sum over chunks c of partial[c][k][t]. A block covers 32 triangles (lanes) of one
-// accumulator k (blockIdx.y) with RC_WARPS warps: warp w adds the chunks c = w, w + RC_WARPS, ... in
-// that order into four interleaved sums, and warp 0 adds the warps' sums in warp order. The order is
-// fixed by the chunk count alone, so the result is reproducible, and the chunk loop runs
-// RC_WARPS x 4 loads deep instead of one chain per triangle (a small mesh has thousands of chunks).
+// accumulator k (blockIdx.y) and one slice of the chunks (blockIdx.z of gridDim.z) with RC_WARPS
+// warps: warp w adds the slice's chunks c = c0 + w, c0 + w + RC_WARPS, ... in that order into four
+// interleaved sums, and warp 0 adds the warps' sums in warp order. With one slice the result goes to
+// acc; with several (few triangles: too few blocks otherwise) each slice's sum goes to
+// out_slices[slice][k][t] and k_reduce_slices adds the slices in order. The order is fixed by the
+// chunk and slice counts alone, so the result is reproducible.
 // M_max >= 0: the chunks cut the band's ADJ_FTILE tiles (the device count *dM when given, else
 // M_max) into n_chunks runs of ceil(tiles / n_chunks); chunks past the last tile hold zeros and are
 // left out.
@@ -414,14 +453,18 @@ template <class R>
 __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __restrict__ partial, int n_chunks, int nacc,
                                                                  int64_t n_t, int64_t n_t_pad,
                                                                  double* __restrict__ acc,
-                                                                 const int64_t* __restrict__ dM, int64_t M_max) {
+                                                                 const int64_t* __restrict__ dM, int64_t M_max,
+                                                                 double* __restrict__ out_slices) {
     __shared__ double sh[RC_WARPS][32];
+    const int slice_len = (n_chunks + (int)gridDim.z - 1) / (int)gridDim.z;
     if (M_max >= 0) {
         const int64_t M = dM ? *dM : M_max;
         const int64_t tiles = (M + ADJ_FTILE - 1) / ADJ_FTILE;
         const int64_t tpc = (tiles + n_chunks - 1) / n_chunks;
         n_chunks = tpc > 0 ? (int)min((int64_t)n_chunks, (tiles + tpc - 1) / tpc) : 0;
     }
+    const int c0 = (int)blockIdx.z * slice_len;
+    const int c1 = min(n_chunks, c0 + slice_len);
     const int lane = threadIdx.x, w = threadIdx.y;
     const int64_t t = (int64_t)blockIdx.x * 32 + lane;
     const int k = (int)blockIdx.y;
@@ -429,14 +472,14 @@ __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __rest
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     if (t < n_t) {
         const R* p = partial + (int64_t)k * n_t_pad + t;
-        int c = w;
-        for (; c + 3 * RC_WARPS < n_chunks; c += 4 * RC_WARPS) {
+        int c = c0 + w;
+        for (; c + 3 * RC_WARPS < c1; c += 4 * RC_WARPS) {
             s0 += (double)p[c * cs];
             s1 += (double)p[(c + RC_WARPS) * cs];
             s2 += (double)p[(c + 2 * RC_WARPS) * cs];
             s3 += (double)p[(c + 3 * RC_WARPS) * cs];
         }
-        for (; c < n_chunks; c += RC_WARPS) s0 += (double)p[c * cs];
+        for (; c < c1; c += RC_WARPS) s0 += (double)p[c * cs];
     }
     sh[w][lane] = (s0 + s1) + (s2 + s3);
     __syncthreads();
@@ -444,8 +487,22 @@ __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __rest
         double r = 0.0;
 #pragma unroll
         for (int i = 0; i < RC_WARPS; ++i) r += sh[i][lane];
-        acc[t * nacc + k] = r;
+        if (gridDim.z == 1)
+            acc[t * nacc + k] = r;
+        else
+            out_slices[((int64_t)blockIdx.z * nacc + k) * n_t + t] = r;
     }
+}
+
+// acc[t][k] = sum over slices s (in order) of slices[s][k][t].
+__global__ void __launch_bounds__(NT) k_reduce_slices(const double* __restrict__ slices, int n_slices, int nacc,
+                                                      int64_t n_t, double* __restrict__ acc) {
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= n_t * nacc) return;
+    const int64_t k = i / n_t, t = i - k * n_t;
+    double r = 0.0;
+    for (int s = 0; s < n_slices; ++s) r += slices[((int64_t)s * nacc + k) * n_t + t];
+    acc[t * nacc + k] = r;
 }
 
 // ---------------------------------------------------------------- gradient assembly
@@ -702,7 +759,7 @@ cudaError_t launch_loss(const R* I, const R* T, int64_t n, int kind, R* resid, d
     int64_t b = nblk(n);
     if (b > 4096) b = 4096;
     *n_blocks_out = (int)b;
-    k_loss<R><<<(unsigned)b, NT, 0, st>>>(I, T, n, kind, resid, partial);
+    k_loss<R><<<(unsigned)b, NT, 0, st>>>(I, T, n, kind, resid, partial, 1.0 / (double)n);
     return cudaGetLastError();
 }
 template cudaError_t launch_loss<float>(const float*, const float*, int64_t, int, float*, double*, int*, cudaStream_t);
@@ -743,16 +800,28 @@ template cudaError_t launch_prep_raw<double, FreqF64>(int, const Cx<double>*, co
 
 template <class R>
 cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64_t n_t, int64_t n_t_pad, double* acc,
-                                 cudaStream_t st, const int64_t* dM, int64_t M_max) {
+                                 cudaStream_t st, const int64_t* dM, int64_t M_max, double* scratch, int sm_count) {
     if (n_t <= 0 || nacc <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((n_t + 31) / 32), (unsigned)nacc), block(32, RC_WARPS);
-    k_reduce_chunks<R><<<grid, block, 0, st>>>(partial, n_chunks, nacc, n_t, n_t_pad, acc, dM, M_max);
+    const int64_t tb = (n_t + 31) / 32;
+    // few triangles: split the chunks into slices so that about 4 blocks per SM run (the scratch
+    // holds reduce_scratch_elems(sm_count) doubles, enough for slices * nacc * n_t at that count)
+    int64_t slices = 1;
+    if (scratch && sm_count > 0 && tb * nacc < 4LL * sm_count) {
+        slices = (4LL * sm_count + tb * nacc - 1) / (tb * nacc);
+        slices = std::min<int64_t>(slices, std::max(1, n_chunks / (4 * RC_WARPS)));
+        if (slices * nacc * n_t > reduce_scratch_elems(sm_count)) slices = 1;
+    }
+    const dim3 grid((unsigned)tb, (unsigned)nacc, (unsigned)slices), block(32, RC_WARPS);
+    k_reduce_chunks<R><<<grid, block, 0, st>>>(partial, n_chunks, nacc, n_t, n_t_pad, acc, dM, M_max, scratch);
+    if (slices > 1) k_reduce_slices<<<nblk(n_t * nacc), NT, 0, st>>>(scratch, (int)slices, nacc, n_t, acc);
     return cudaGetLastError();
 }
 template cudaError_t launch_reduce_chunks<float>(const float*, int, int, int64_t, int64_t, double*, cudaStream_t,
-                                                 const int64_t*, int64_t);
+                                                 const int64_t*, int64_t, double*, int);
 template cudaError_t launch_reduce_chunks<double>(const double*, int, int, int64_t, int64_t, double*, cudaStream_t,
-                                                  const int64_t*, int64_t);
+                                                  const int64_t*, int64_t, double*, int);
+
+size_t reduce_scratch_elems(int sm_count) { return (size_t)256 * (sm_count > 0 ? sm_count : 1); }
 
 cudaError_t launch_assemble(int mode, const double* V, const int32_t* F, int64_t n_t, int64_t n_v, const float* wts,
                             const Geom& g, const double* acc, const double* d_coef, double* contrib, cudaStream_t st) {
