@@ -166,17 +166,39 @@ struct BandArgs {
     int kind;
     double tau;
     double e_max;  // -2 ln tau: h_hat > tau  <=>  xi^T Sigma xi < e_max
+    float e_max_f;  // e_max in FP32
+    float tpf[3];   // tp in FP32
     int Nx, Ny, Nz, Nzh;
     FastDiv div_zh, div_y;
     double tp[3];
     int64_t nH;
 };
 
-// h_hat(xi) > tau, decided on the exponent (no exp) except within rounding of the threshold, where the
-// exp form decides as written.
+// h_hat(xi) > tau, decided on the exponent e = xi^T Sigma xi (no exp). The exponent is first formed in
+// FP32 with a bound on its rounding error (at most a few units in the last place of each of its
+// non-negative magnitude terms, counted with a wide factor); only a frequency whose FP32 exponent
+// lies within that bound of the threshold is decided in FP64, as the FP64 oracle decides it (and,
+// within rounding of the threshold, by the exp form as written). So the band is the oracle's,
+// bit for bit, with FP64 arithmetic on a thin shell of frequencies only.
 __device__ __forceinline__ bool in_band(const BandArgs& b, int64_t idx) {
     int nx, ny, nz;
     decode_h_fast((uint32_t)idx, b.div_zh, b.div_y, b.Nx, b.Ny, nx, ny, nz);
+    const float x = (float)nx * b.tpf[0], y = (float)ny * b.tpf[1], z = (float)nz * b.tpf[2];
+    float e32, mag;
+    if (b.kind == 0) {
+        const float s0 = (float)b.psf[0], s1 = (float)b.psf[1], s2 = (float)b.psf[2];
+        e32 = s0 * s0 * x * x + s1 * s1 * y * y + s2 * s2 * z * z;
+        mag = e32;
+    } else {
+        const double* c = b.psf + 3;
+        const float c0 = (float)c[0], c1 = (float)c[1], c2 = (float)c[2], c3 = (float)c[3], c4 = (float)c[4],
+                    c5 = (float)c[5];
+        e32 = c0 * x * x + c1 * y * y + c2 * z * z + 2.0f * (c3 * x * y + c4 * x * z + c5 * y * z);
+        mag = fabsf(c0) * x * x + fabsf(c1) * y * y + fabsf(c2) * z * z +
+              2.0f * (fabsf(c3 * x * y) + fabsf(c4 * x * z) + fabsf(c5 * y * z));
+    }
+    const float bound = 32.0f * 5.96e-8f * (mag + b.e_max_f);  // 32 units of 2^-24, relative to the magnitudes
+    if (fabsf(e32 - b.e_max_f) > bound) return e32 < b.e_max_f;
     const double e = otf_expo(b.psf, b.kind, nx * b.tp[0], ny * b.tp[1], nz * b.tp[2]);
     if (fabs(e - b.e_max) > 1e-9 * b.e_max) return e < b.e_max;
     return exp(-0.5 * e) > b.tau;
@@ -720,13 +742,17 @@ cudaError_t launch_band(const double* d_psf, int psf_kind, double tau, int Nx, i
     b.kind = psf_kind;
     b.tau = tau;
     b.e_max = -2.0 * log(tau);
+    b.e_max_f = (float)b.e_max;
     b.Nx = Nx;
     b.Ny = Ny;
     b.Nz = Nz;
     b.Nzh = Nz / 2 + 1;
     b.div_zh = make_fastdiv((uint32_t)b.Nzh);
     b.div_y = make_fastdiv((uint32_t)Ny);
-    for (int a = 0; a < 3; ++a) b.tp[a] = 2.0 * M_PI / g.L[a];
+    for (int a = 0; a < 3; ++a) {
+        b.tp[a] = 2.0 * M_PI / g.L[a];
+        b.tpf[a] = (float)b.tp[a];
+    }
     b.nH = (int64_t)Nx * Ny * b.Nzh;
     const unsigned nb = nblk(b.nH);
     k_band_count<<<nb, NT, 0, st>>>(b, block_counts);
