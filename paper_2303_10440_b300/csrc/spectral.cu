@@ -491,19 +491,19 @@ __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __rest
     const int64_t t = (int64_t)blockIdx.x * 32 + lane;
     const int k = (int)blockIdx.y;
     const int64_t cs = (int64_t)nacc * n_t_pad;  // stride between chunks
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    TSum<R> s0, s1, s2, s3;  // per-thread sums in the path's precision (compensated in FP32)
     if (t < n_t) {
         const R* p = partial + (int64_t)k * n_t_pad + t;
         int c = c0 + w;
         for (; c + 3 * RC_WARPS < c1; c += 4 * RC_WARPS) {
-            s0 += (double)p[c * cs];
-            s1 += (double)p[(c + RC_WARPS) * cs];
-            s2 += (double)p[(c + 2 * RC_WARPS) * cs];
-            s3 += (double)p[(c + 3 * RC_WARPS) * cs];
+            s0.add(p[c * cs]);
+            s1.add(p[(c + RC_WARPS) * cs]);
+            s2.add(p[(c + 2 * RC_WARPS) * cs]);
+            s3.add(p[(c + 3 * RC_WARPS) * cs]);
         }
-        for (; c < c1; c += RC_WARPS) s0 += (double)p[c * cs];
+        for (; c < c1; c += RC_WARPS) s0.add(p[c * cs]);
     }
-    sh[w][lane] = (s0 + s1) + (s2 + s3);
+    sh[w][lane] = (s0.get() + s1.get()) + (s2.get() + s3.get());
     __syncthreads();
     if (w == 0 && t < n_t) {
         double r = 0.0;
