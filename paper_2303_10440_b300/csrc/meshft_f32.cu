@@ -23,7 +23,7 @@
 // of the triangle list (slices sized so that the launch has ~112 units per SM) in
 // tiles bulk-copied (TMA) into a ring of shared-memory stages with full/empty
 // mbarriers. FP32 sums within a tile, Kahan across tiles; slices are summed
-// afterwards in FP64 in a fixed order.
+// afterwards in a fixed order (compensated FP32).
 // Adjoint: a thread holds one triangle; the block walks a chunk of the band in
 // tiles of frequency-pair records bulk-copied the same way, summing the triangle's
 // 10 (surface) or 12 (volume) terms of a tile in registers and carrying the running
@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(FWD_THREADS, 4) k_fwd_f32(const TriF32* __rest
                               tpz, d_vol, out, err, b, stage, full, empty, ts == 0);
 }
 
-// S[m] = sum over the triangle splits of the partial spectra (fixed order, FP64); nothing when unsplit.
+// S[m] = sum over the triangle splits of the partial spectra (fixed order, compensated); nothing when
+// unsplit.
 // fixed_splits > 0: that many splits (a served job's own count) instead of the band-derived one.
 __global__ void __launch_bounds__(256) k_fwd_reduce(FreqSrc fs, int n_tiles, int target, int fixed_splits,
                                                     const float2* __restrict__ S_part, float2* __restrict__ S) {
@@ -394,13 +395,14 @@ __global__ void __launch_bounds__(256) k_fwd_reduce(FreqSrc fs, int n_tiles, int
     if (fixed_splits > 0) splits = fixed_splits;
     if (splits == 1) return;
     for (int64_t m = (int64_t)blockIdx.x * 256 + threadIdx.x; m < M; m += (int64_t)gridDim.x * 256) {
-        double sx = 0.0, sy = 0.0;
+        // compensated FP32 sums (B300's FP64 adds are slow); the result is rounded to FP32 anyway
+        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
         for (int ts = 0; ts < splits; ++ts) {
             const float2 v = S_part[(int64_t)ts * M + m];
-            sx += v.x;
-            sy += v.y;
+            kahan_add(sx, cx, v.x);
+            kahan_add(sy, cy, v.y);
         }
-        S[m] = make_float2((float)sx, (float)sy);
+        S[m] = make_float2(sx, sy);
     }
 }
 
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, MODE == 0 ? 5 : 4) k_adj_batch_f3
 // and handed out as blocks free up, so the SMs finish within about one unit of each other: with
 // 8 units per SM the last, partly filled round of blocks cost 6% of the 128^3 forward; 56 and 112
 // per SM took it from 11.9 to 11.1 and 11.05 ms (224 was slower again: each unit then covers few
-// triangle tiles). The triangle splits this makes are summed in FP64 in a fixed order.
+// triangle tiles). The triangle splits this makes are summed in a fixed order.
 int fwd_target_units(int sm_count) { return 112 * sm_count; }
 
 size_t fwd_partial_elems(int64_t M_max, int sm_count) {
