@@ -277,7 +277,6 @@ bool fft_factor(int N, FFTAxis& a);
 size_t fft_smem_bytes(int N, int elem_bytes);
 
 // Small helpers.
-cudaError_t launch_fill_zero_f64(double* p, int64_t n, cudaStream_t st);
 struct Params16 {
     double v[16];
 };

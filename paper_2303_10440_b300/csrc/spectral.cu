@@ -701,11 +701,6 @@ __global__ void k_set_params(double* dst, Params16 p, int n) {
     if (threadIdx.x < n) dst[threadIdx.x] = p.v[threadIdx.x];
 }
 
-__global__ void k_zero_f64(double* p, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (i < n) p[i] = 0.0;
-}
-
 inline unsigned nblk(int64_t n) { return (unsigned)((n + NT - 1) / NT); }
 
 }  // namespace
@@ -897,11 +892,6 @@ cudaError_t launch_fit_tick(double* hist, const double* d_loss, int64_t* d_step,
 
 cudaError_t launch_set_params(double* dst, Params16 p, int n, cudaStream_t st) {
     k_set_params<<<1, 32, 0, st>>>(dst, p, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fill_zero_f64(double* p, int64_t n, cudaStream_t st) {
-    k_zero_f64<<<nblk(n), NT, 0, st>>>(p, n);
     return cudaGetLastError();
 }
 
