@@ -35,7 +35,9 @@ METRIC = "fwd+bwd tri*freq terms/s; served fits/s & p99 vs plain FP64 path at <=
 UNIT = "terms/s"
 # Algorithmic work per (frequency, triangle) term on the FP32 pipe (lane operations) and on
 # the MUFU (sin/cos/rcp) pipe: evaluating Eq. 8 once (forward) and Eq. 8 + Eq. 10 with the
-# contraction into the per-triangle sums (adjoint).
+# contraction into the per-triangle sums (adjoint). These are the method's counts (3 sincos and one
+# common-denominator reciprocal per term), not the kernels' instruction counts: the forward kernel
+# issues exactly these 7 MUFU operations per term, the adjoint 9 (it forms E and q of both gaps).
 OPS_PER_TERM = {"fwd": 45, "adj": 110}
 MUFU_PER_TERM = {"fwd": 7, "adj": 7}
 
