@@ -244,7 +244,7 @@ def test_preempted_job_resumes_bit_for_bit(setup, optimizer, lr, decay):
     from paper_2303_10440_b300.serve import FitServer
 
     _, jobs = setup
-    steps = 14
+    steps = 60  # long enough that the preemption lands while the job still runs, on any host
     job = dict(jobs[2], steps=steps, optimizer=optimizer, lr_vertex=lr, lr_psf=0.002, lr_decay=decay)
     s0 = FitServer(max_jobs=2)
     i0 = s0.submit(**job)
