@@ -362,6 +362,9 @@ typedef struct {
     double batch_terms;    /* DM_SCHED_SHORTEST: most triangle-frequency terms per step that one iteration
                               takes on (jobs in policy order; the first always runs); <= 0: no limit */
     double max_wait_s;     /* a resident job that has not advanced for this long goes first (<= 0: never) */
+    int32_t no_graphs;     /* nonzero: enqueue every iteration directly. Otherwise (the default) the second
+                              iteration over an unchanged set of advanced jobs is captured as a CUDA graph and
+                              replayed until the set changes; results are the same either way */
 } dm_server_options;
 
 typedef struct {
@@ -409,6 +412,7 @@ typedef struct {
     size_t bytes_in_use;   /* arena bytes held by admitted jobs */
     size_t bytes_peak;
     size_t bytes_total;
+    int64_t graph_replays; /* iterations run as one launch of a captured CUDA graph */
 } dm_server_stats;
 
 /* Create a server and start its engine thread. */

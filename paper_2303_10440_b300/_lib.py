@@ -98,7 +98,7 @@ class dm_fit_state(ctypes.Structure):
 
 class dm_server_options(ctypes.Structure):
     _fields_ = [("device", c_i32), ("max_jobs", c_i32), ("memory_bytes", ctypes.c_size_t), ("chunk_tiles", c_i32),
-                ("policy", c_i32), ("batch_terms", c_f64), ("max_wait_s", c_f64)]
+                ("policy", c_i32), ("batch_terms", c_f64), ("max_wait_s", c_f64), ("no_graphs", c_i32)]
 
 
 POLICIES = {"fifo": 0, "shortest": 1}
@@ -131,7 +131,7 @@ class dm_job_status(ctypes.Structure):
 class dm_server_stats(ctypes.Structure):
     _fields_ = [("iterations", c_i64), ("jobs_done", c_i64), ("job_steps", c_i64), ("peak_active", c_i64),
                 ("busy_s", c_f64), ("bytes_in_use", ctypes.c_size_t), ("bytes_peak", ctypes.c_size_t),
-                ("bytes_total", ctypes.c_size_t)]
+                ("bytes_total", ctypes.c_size_t), ("graph_replays", c_i64)]
 
 
 JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "preempted"}

@@ -668,10 +668,10 @@ dm_status dm_fit_resume(dm_ctx* ctx, const dm_mesh* mesh, double* V_io, dm_psf* 
         if (r != DM_OK) return r;
         Stage sg(ctx, DM_STAGE_ADAM, q);
         LAUNCH(1, launch_adam_dev_step(b.V, b.dV, mV, vV, nV, opt->lr_vertex, opt->beta1, opt->beta2, opt->eps,
-                                       d_step, q));
+                                       d_step, 1.0, q));
         if (opt->lr_psf > 0)
             LAUNCH(1, launch_adam_dev_step(b.d_params, b.d_params + 24, ms, vs, 3, opt->lr_psf, opt->beta1,
-                                           opt->beta2, opt->eps, d_step, q));
+                                           opt->beta2, opt->eps, d_step, 1.0, q));
         LAUNCH(1, launch_fit_tick(hist, b.d_params + 17, d_step, step0, q));
         return DM_OK;
     };

@@ -245,19 +245,22 @@ cudaError_t launch_pcg(const int32_t* lptr, const int32_t* lcol, int64_t n_v, do
                        double* sub_into, R* work, double tol, int max_iter, unsigned long long* stats,
                        cudaStream_t st);
 // Uniform Adam: m, v updated; delta = lr m_hat / (sqrt(max v_hat) + eps). part_max holds
-// adam_uniform_partials(n) doubles.
+// adam_uniform_partials(n) doubles. With d_step the step t is read from the device (step ignored), and
+// decay != 1 makes the rate lr decay^(t-1).
 int adam_uniform_partials(int64_t n);
 cudaError_t launch_adam_uniform(const double* g, double* m, double* v, double* delta, int64_t n, double lr, double b1,
-                                double b2, double eps, int64_t step, double* part_max, cudaStream_t st);
+                                double b2, double eps, int64_t step, double* part_max, cudaStream_t st,
+                                const int64_t* d_step = nullptr, double decay = 1.0);
 // Sigma = C C^T into the covariance numbers of the device PSF parameters, and dL/dC from dL/dcov.
 cudaError_t launch_chol_to_cov(const double* C, double* d_psf, cudaStream_t st);
 cudaError_t launch_chol_grad(const double* C, const double* gcov, double* gC, cudaStream_t st);
 
-// Adam update on n doubles.
+// Adam update on n doubles; the _dev_step form reads the step t from the device and takes the rate
+// lr decay^(t-1) (decay 1: constant), so that a captured step replays unchanged.
 cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2,
                         double eps, int64_t step, cudaStream_t st);
 cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1,
-                                 double b2, double eps, const int64_t* d_step, cudaStream_t st);
+                                 double b2, double eps, const int64_t* d_step, double decay, cudaStream_t st);
 // hist[*d_step - step0 - 1] = *d_loss; ++*d_step (one thread)
 cudaError_t launch_fit_tick(double* hist, const double* d_loss, int64_t* d_step, int64_t step0, cudaStream_t st);
 

@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(OT) k_au_moments(const double* __restrict__ g,
 
 __global__ void __launch_bounds__(OT) k_au_step(const double* __restrict__ m, const double* __restrict__ part_max,
                                                 int nb, int64_t n, double lr, double b1, double b2, double eps,
-                                                int64_t step, double* __restrict__ delta) {
+                                                int64_t step, const int64_t* __restrict__ d_step, double decay,
+                                                double* __restrict__ delta) {
     __shared__ double vmax_s;
     if (threadIdx.x < 32) {
         double mx = 0.0;
@@ -246,7 +247,8 @@ __global__ void __launch_bounds__(OT) k_au_step(const double* __restrict__ m, co
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * OT + threadIdx.x;
     if (i >= n) return;
-    const double t = (double)step;
+    const double t = (double)(d_step ? *d_step : step);
+    if (decay != 1.0) lr *= pow(decay, t - 1.0);  // step t takes the rate lr decay^(t-1)
     const double mh = m[i] / (1.0 - pow(b1, t));
     const double vh = vmax_s / (1.0 - pow(b2, t));
     delta[i] = lr * mh / (sqrt(vh) + eps);
@@ -336,10 +338,11 @@ template cudaError_t launch_pcg<double>(const int32_t*, const int32_t*, int64_t,
 int adam_uniform_partials(int64_t n) { return (int)oblk(n); }
 
 cudaError_t launch_adam_uniform(const double* g, double* m, double* v, double* delta, int64_t n, double lr, double b1,
-                                double b2, double eps, int64_t step, double* part_max, cudaStream_t st) {
+                                double b2, double eps, int64_t step, double* part_max, cudaStream_t st,
+                                const int64_t* d_step, double decay) {
     const unsigned nb = oblk(n);
     k_au_moments<<<nb, OT, 0, st>>>(g, m, v, n, b1, b2, part_max);
-    k_au_step<<<nb, OT, 0, st>>>(m, part_max, (int)nb, n, lr, b1, b2, eps, step, delta);
+    k_au_step<<<nb, OT, 0, st>>>(m, part_max, (int)nb, n, lr, b1, b2, eps, step, d_step, decay, delta);
     return cudaGetLastError();
 }
 

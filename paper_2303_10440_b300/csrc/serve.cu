@@ -113,6 +113,8 @@ struct SJob {
     Sizes z;
     Bufs b;
     double *mV = nullptr, *vV = nullptr, *ms = nullptr, *vs = nullptr, *hist = nullptr;
+    int64_t* d_step = nullptr;  // Adam step t of the job's next step (device: a captured iteration replays unchanged)
+    int64_t t_first = 1;        // its value at admission (host source of the upload)
     // large-steps state: Laplacian rows, solver work, warm starts, uniform-Adam step and maxima
     int32_t *lptr = nullptr, *lcol = nullptr;
     float* pcg_work = nullptr;
@@ -153,6 +155,7 @@ size_t job_layout(const Sizes& z, int steps, int64_t n_v, Arena& A, Bufs& b, dou
     J->S_part = J->fsplits > 1 ? A.take<float2>((size_t)J->fsplits * z.M_max) : nullptr;
     *mom = A.take<double>(6 * n_v + 8);
     *hist = A.take<double>(steps);
+    J->d_step = A.take<int64_t>(1);
     if (J->optimizer == DM_OPT_LARGE_STEPS) {
         J->lptr = A.take<int32_t>(n_v + 1);
         J->lcol = A.take<int32_t>(6 * z.n_t);
@@ -202,7 +205,10 @@ struct dm_server {
     std::vector<std::pair<cudaStream_t, cudaEvent_t>> free_streams;  // job streams not in use
     cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr;                  // after each batched launch
     int64_t since_sync = 0;
-    bool prev_single = false;  // the last iteration advanced one job, all on the server stream
+    bool use_graphs = true;              // capture an iteration and replay it while the job set is unchanged
+    cudaGraphExec_t gexec = nullptr;     // the captured iteration of the current job set
+    int64_t graph_launches = 0;          // kernels one replay launches
+    int64_t same_run = 0;                // iterations run over the current job set
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
@@ -250,6 +256,7 @@ bool setup_job(dm_server* S, SJob* J) {
     J->ms = mom + 6 * z.n_v;
     J->vs = J->ms + 4;
     J->hist = hist;
+    J->t_first = J->step0 + 1;
     if (S->free_streams.empty()) {
         cudaStream_t js;
         cudaEvent_t je;
@@ -276,6 +283,7 @@ bool setup_job(dm_server* S, SJob* J) {
                    cudaSuccess) &&
               cudaMemsetAsync(mom, 0, (6 * z.n_v + 8) * sizeof(double), st) == cudaSuccess &&
               launch_set_params(b.d_params, psf_params(&J->psf), 9, st) == cudaSuccess &&
+              cudaMemcpyAsync(J->d_step, &J->t_first, sizeof(int64_t), cudaMemcpyHostToDevice, st) == cudaSuccess &&
               launch_csr(b.F, z.n_t, z.n_v, b.cnt, b.ptr, b.ent, ctx->d_err, st) == cudaSuccess &&
               fft_axes(ctx, J->grid.n, J->ax) == DM_OK;
     g_launches += 5;
@@ -386,23 +394,23 @@ bool rebuild_units(dm_server* S) {
     return ok;
 }
 
-// Enqueue one Adam step of every job in S->run. Each job's own stage kernels run on its stream;
-// the two batched launches run on the server stream after every job's preceding stage (events).
-// Synchronises only when `sync` is set; returns false on a device fault seen at a sync.
-bool iterate(dm_server* S, bool sync) {
+// Enqueue one Adam step of every job in S->run on the server stream: each job's own stage kernels on
+// its stream (forked from the server stream at the start, joined back at the end), the batched
+// launches on the server stream after every job's preceding stage (events). Every value that changes
+// from step to step lives on the device (the Adam step counter), so the same sequence can be captured
+// once and replayed. Adds the kernels it launches to *nl; false if an enqueue failed.
+bool enqueue_step(dm_server* S, int64_t* nl_out) {
     dm_ctx* ctx = S->ctx;
     cudaStream_t st = S->st;
-    if (S->dirty && !rebuild_units(S)) return false;
     const size_t nj = S->run.size();
     // one job: its stage kernels go on the server stream and no events are needed between them
     const bool single = nj == 1;
     bool ok = true;
-    if (!single && S->prev_single) {
-        // the previous iteration ran on the server stream only: the job streams start after it
+    int64_t nlk = 0;
+    if (!single) {
         ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
         for (SJob* J : S->run) ok &= cudaStreamWaitEvent(J->stream, S->ev_fwd, 0) == cudaSuccess;
     }
-    S->prev_single = single;
     // triangle records, normalisers, bands
     for (SJob* J : S->run) {
         cudaStream_t js = single ? st : J->stream;
@@ -412,11 +420,11 @@ bool iterate(dm_server* S, bool sync) {
         ok &= launch_tri_prep<TriF32>(J->label, b.V, J->z.n_v, b.F, J->z.n_t, b.wts, G, (TriF32*)b.tris,
                                       J->z.n_t_pad, b.partial, &nb, ctx->d_err, js) == cudaSuccess;
         ok &= launch_sum(b.partial, nb, 1, 1, b.d_params + 16, js) == cudaSuccess;
-        g_launches += 2;
+        nlk += 2;
         if (J->z.band) {
             ok &= launch_band(b.d_params, J->psf.kind, J->psf.band_tau, J->grid.n[0], J->grid.n[1], J->grid.n[2], G,
                               b.band_idx, b.dM, b.band_counts, js) == cudaSuccess;
-            g_launches += 3;
+            nlk += 3;
         }
         if (!single) {
             ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
@@ -432,7 +440,7 @@ bool iterate(dm_server* S, bool sync) {
         const int gf = (int)std::min<size_t>((size_t)S->grid_fwd[m], nfl[m]);
         ok &= launch_fwd_batch_f32(m, S->d_fj, S->d_uf + (m ? S->nf_surf : 0), (int)nfl[m], S->d_counter, gf,
                                    ctx->d_err, st) == cudaSuccess;
-        g_launches += 1;
+        nlk += 1;
     }
     ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
     // image, loss, adjoint records
@@ -451,7 +459,7 @@ bool iterate(dm_server* S, bool sync) {
         const int* n = J->grid.n;
         int nl = 0, ng = 0;
         ok &= launch_fwd_reduce_splits(fs, J->fsplits, J->S_part, (float2*)b.S, ctx->sm_count, js) == cudaSuccess;
-        if (J->fsplits > 1) g_launches += 1;
+        if (J->fsplits > 1) nlk += 1;
         ok &= launch_scatter<float>((const Cx<float>*)b.S, fs, b.d_params, J->psf.kind, b.d_params + 16, G,
                                     (Cx<float>*)b.spec, z.band, js) == cudaSuccess;
         ok &= launch_c2r<float>((const Cx<float>*)b.spec, (Cx<float>*)b.spec, (float*)b.image, n[0], n[1], n[2], J->ax,
@@ -464,7 +472,7 @@ bool iterate(dm_server* S, bool sync) {
                                             J->psf.kind, b.d_params + 16, G, (FreqF32*)b.fr, z.M_pad, b.partial, &ng,
                                             js) == cudaSuccess;
         ok &= launch_sum(b.partial, ng, 8, 8, b.d_params + 24, js) == cudaSuccess;
-        g_launches += 12;
+        nlk += 12;
         if (!single) {
             ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
             ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
@@ -475,7 +483,7 @@ bool iterate(dm_server* S, bool sync) {
         const int ga = (int)std::min<size_t>((size_t)S->grid_adj[m], nal[m]);
         ok &= launch_adj_batch_f32(m, S->d_aj, S->d_ua + (m ? S->na_surf : 0), (int)nal[m], S->d_counter, ga,
                                    ctx->d_err, st) == cudaSuccess;
-        g_launches += 1;
+        nlk += 1;
     }
     ok &= cudaEventRecord(S->ev_adj, st) == cudaSuccess;
     // per-vertex gradients and Adam
@@ -492,38 +500,95 @@ bool iterate(dm_server* S, bool sync) {
         ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, b.wts, G, b.acc, b.d_params + 30, b.contrib, js) ==
               cudaSuccess;
         ok &= launch_vertex_gather(b.ptr, b.ent, b.contrib, z.n_v, b.dV, js) == cudaSuccess;
-        ok &= cudaMemcpyAsync(J->hist + J->steps_done, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToDevice,
-                              js) == cudaSuccess;
         ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, js) ==
               cudaSuccess;
+        // Adam step t = *J->d_step (bias correction and the rate lr lr_decay^(t-1)); the tick then
+        // stores the step's loss at hist[t - step0 - 1] and advances t
         const dm_fit_options& o = J->fit;
-        const int64_t t = J->step0 + J->steps_done + 1;  // Adam step (bias correction and rate schedule)
-        const double rate = J->lr_decay == 1.0 ? 1.0 : std::pow(J->lr_decay, (double)(t - 1));
         if (J->optimizer == DM_OPT_LARGE_STEPS) {
             // v -= (1 + lambda L)^-1 AdamUniform((1 + lambda L)^-1 dL/dv)
             ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, b.dV, J->gu, nullptr, J->pcg_work, 1e-6, 2000,
                                     J->cg_stats, js) == cudaSuccess;
-            ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex * rate, o.beta1, o.beta2,
-                                      o.eps, t, J->aup, js) == cudaSuccess;
+            ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps, 0,
+                                      J->aup, js, J->d_step, J->lr_decay) == cudaSuccess;
             ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, J->dl, J->wv, b.V, J->pcg_work, 1e-6, 2000,
                                     J->cg_stats, js) == cudaSuccess;
-            g_launches += 7;
+            nlk += 7;
         } else {
-            ok &= launch_adam(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex * rate, o.beta1, o.beta2, o.eps, t,
-                              js) == cudaSuccess;
-            g_launches += 4;
+            ok &= launch_adam_dev_step(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
+                                       J->d_step, J->lr_decay, js) == cudaSuccess;
+            nlk += 4;
         }
         if (o.lr_psf > 0) {
-            ok &= launch_adam(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf * rate, o.beta1, o.beta2, o.eps,
-                              t, js) == cudaSuccess;
-            g_launches += 1;
+            ok &= launch_adam_dev_step(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
+                                       J->d_step, J->lr_decay, js) == cudaSuccess;
+            nlk += 1;
         }
+        ok &= launch_fit_tick(J->hist, b.d_params + 17, J->d_step, J->step0, js) == cudaSuccess;
+        nlk += 1;
         // the next iteration's batched launches on the server stream also follow this job's Adam
         if (!single) {
             ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
             ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
         }
     }
+    *nl_out += nlk;
+    return ok;
+}
+
+// Drop the captured iteration (the set of jobs it advances changed).
+void drop_graph(dm_server* S) {
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);  // freed once its launches in flight complete
+    S->gexec = nullptr;
+    S->same_run = 0;
+}
+
+// One Adam step of every job in S->run. The first iteration after the set of jobs changes runs
+// directly (it uploads the unit tables and raises kernel attributes); the second is captured as a
+// CUDA graph, which later iterations over the same set replay with one launch. Synchronises only
+// when `sync` is set; returns false on a device fault seen at a sync.
+bool iterate(dm_server* S, bool sync) {
+    dm_ctx* ctx = S->ctx;
+    cudaStream_t st = S->st;
+    if (S->dirty) {
+        drop_graph(S);
+        if (!rebuild_units(S)) return false;
+    }
+    const size_t nj = S->run.size();
+    bool ok = true;
+    int64_t nl = 0;
+    if (S->gexec) {
+        ok = cudaGraphLaunch(S->gexec, st) == cudaSuccess;
+        nl = S->graph_launches;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stats.graph_replays += 1;
+    } else if (S->use_graphs && S->same_run >= 1) {
+        cudaGraph_t g = nullptr;
+        bool cap = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (cap) {
+            cap = enqueue_step(S, &nl);
+            cap = cudaStreamEndCapture(st, &g) == cudaSuccess && cap && g != nullptr;
+            cap = cap && cudaGraphInstantiate(&S->gexec, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+        }
+        if (cap) {
+            S->graph_launches = nl;
+            ok = cudaGraphLaunch(S->gexec, st) == cudaSuccess;
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->stats.graph_replays += 1;
+        } else {
+            // the capture failed (nothing of it ran): run this and later iterations directly
+            cudaGetLastError();
+            S->gexec = nullptr;
+            S->use_graphs = false;
+            nl = 0;
+            ok = enqueue_step(S, &nl);
+        }
+    } else {
+        ok = enqueue_step(S, &nl);
+    }
+    g_launches += nl;
+    S->same_run += 1;
     for (size_t j = 0; j < nj; ++j) S->run[j]->steps_done += 1;
     if (sync) {
         ok &= cudaStreamSynchronize(st) == cudaSuccess;
@@ -810,6 +875,7 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     S->policy = opt->policy;
     S->batch_terms = opt->batch_terms;
     S->max_wait_s = opt->max_wait_s;
+    S->use_graphs = opt->no_graphs == 0;
     S->t0 = std::chrono::steady_clock::now();
     memset(&S->stats, 0, sizeof(S->stats));
     DeviceGuard dg(opt->device);
@@ -1009,6 +1075,7 @@ dm_status dm_server_shutdown(dm_server* S) {
     if (S->engine.joinable()) S->engine.join();
     DeviceGuard dg(S->device);
     cudaStreamSynchronize(S->st);
+    if (S->gexec) cudaGraphExecDestroy(S->gexec);
     for (auto& kv : S->jobs) delete kv.second;  // queued, finished and unclaimed jobs
     S->arena.release();
     cudaFree(S->d_fj);

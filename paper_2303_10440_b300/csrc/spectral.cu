@@ -672,10 +672,12 @@ __global__ void __launch_bounds__(NT) k_vertex_gather(const int32_t* __restrict_
 // ---------------------------------------------------------------- Adam
 __global__ void __launch_bounds__(NT) k_adam(double* __restrict__ p, const double* __restrict__ g, double* __restrict__ m,
                                              double* __restrict__ v, int64_t n, double lr, double b1, double b2,
-                                             double eps, int64_t step, const int64_t* __restrict__ d_step) {
+                                             double eps, int64_t step, const int64_t* __restrict__ d_step,
+                                             double decay) {
     const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
     if (i >= n) return;
     const double t = (double)(d_step ? *d_step : step);
+    if (decay != 1.0) lr *= pow(decay, t - 1.0);  // step t takes the rate lr decay^(t-1)
     const double gi = g[i];
     const double mi = b1 * m[i] + (1.0 - b1) * gi;
     const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
@@ -876,12 +878,12 @@ cudaError_t launch_vertex_gather(const int32_t* ptr, const int32_t* ent, const d
 
 cudaError_t launch_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1, double b2,
                         double eps, int64_t step, cudaStream_t st) {
-    k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, step, nullptr);
+    k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, step, nullptr, 1.0);
     return cudaGetLastError();
 }
 cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* v, int64_t n, double lr, double b1,
-                                 double b2, double eps, const int64_t* d_step, cudaStream_t st) {
-    k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, 0, d_step);
+                                 double b2, double eps, const int64_t* d_step, double decay, cudaStream_t st) {
+    k_adam<<<nblk(n), NT, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, 0, d_step, decay);
     return cudaGetLastError();
 }
 

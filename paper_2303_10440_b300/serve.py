@@ -34,13 +34,14 @@ class FitServer:
     """Continuous-batching shape-fit server on one GPU (FP32 mixed path)."""
 
     def __init__(self, device: int = 0, max_jobs: int = 32, memory_bytes: int = 0, chunk_tiles: int = 0,
-                 policy: str = "fifo", batch_terms: float = 0.0, max_wait_s: float = 0.0):
+                 policy: str = "fifo", batch_terms: float = 0.0, max_wait_s: float = 0.0, graphs: bool = True):
         """policy "fifo": arrival order, every resident job advances every iteration; "shortest": the
         jobs with the least remaining work are admitted and advanced first, at most ``batch_terms``
-        triangle-frequency terms per iteration (<= 0: no limit), a job idle for ``max_wait_s`` first."""
+        triangle-frequency terms per iteration (<= 0: no limit), a job idle for ``max_wait_s`` first.
+        graphs: replay an iteration captured as a CUDA graph while the set of advanced jobs is unchanged."""
         self.lib = _lib.load()
         o = _lib.dm_server_options(int(device), int(max_jobs), int(memory_bytes), int(chunk_tiles),
-                                   _lib.POLICIES[policy], float(batch_terms), float(max_wait_s))
+                                   _lib.POLICIES[policy], float(batch_terms), float(max_wait_s), 0 if graphs else 1)
         h = ctypes.c_void_p()
         st = self.lib.dm_server_create(ctypes.byref(h), ctypes.byref(o))
         if st != _lib.DM_OK:

@@ -55,4 +55,5 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(_lib.dm_stagger_stats) == 24
     assert ctypes.sizeof(_lib.dm_job) == 40 + 64 + 88 + 48 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(_lib.dm_fit_state) == 8 + 72 + 24
-    assert ctypes.sizeof(_lib.dm_server_options) == 4 + 4 + 8 + 4 + 4 + 8 + 8
+    assert ctypes.sizeof(_lib.dm_server_options) == 4 + 4 + 8 + 4 + 4 + 8 + 8 + 8  # no_graphs + padding
+    assert ctypes.sizeof(_lib.dm_server_stats) == 4 * 8 + 8 + 3 * 8 + 8

@@ -382,3 +382,38 @@ def test_weighted_multicell_job_matches_the_standalone_fit(setup):
     plain = _run(s3, [dict(wj, weights=None)], [0])[0]
     s3.shutdown()
     assert np.linalg.norm(plain.V - mix[1].V) > 1e-2 * moved
+
+
+def test_graph_replayed_iterations_equal_direct_ones(setup):
+    """While the set of advanced jobs is unchanged the server replays one captured iteration (a CUDA
+    graph; the Adam step and its decayed rate are read on the device): the vertices, sigma and loss
+    histories are bitwise those of a server that enqueues every iteration directly, for a batch (job
+    streams forked and joined inside the graph: Adam, large steps, decay, PSF learning) and for a lone job
+    (all on the server stream)."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    _, jobs = setup
+    mix = [dict(jobs[0]), dict(jobs[1], optimizer="large_steps", lr_vertex=0.5, lr_decay=0.9, lr_psf=0.002),
+           dict(jobs[2], lr_decay=0.95, lr_psf=0.002), dict(jobs[3], steps=9)]
+    lone = [dict(jobs[4], steps=12, lr_psf=0.002, lr_decay=0.97)]
+    for batch in (mix, lone):
+        res, stats = {}, {}
+        for graphs in (True, False):
+            s = FitServer(max_jobs=8, graphs=graphs)
+            res[graphs] = _run(s, batch, list(range(len(batch))))
+            stats[graphs] = s.stats()
+            s.shutdown()
+        assert stats[False]["graph_replays"] == 0
+        # the first iteration over a job set runs directly, the second is captured, the rest replay it
+        # (how often the batch's set changes depends on when the submissions reach the engine)
+        assert stats[True]["graph_replays"] > 0
+        if len(batch) == 1:
+            assert stats[True]["graph_replays"] == stats[True]["iterations"] - 1
+        for k in range(len(batch)):
+            a, b = res[True][k], res[False][k]
+            assert np.array_equal(a.V, b.V)
+            assert np.array_equal(a.sigma, b.sigma)
+            assert np.array_equal(a.loss_history, b.loss_history)
+            assert np.all(np.isfinite(a.loss_history)) and np.all(a.loss_history > 0)  # every step's loss stored
+        print(f"\n[serve] {len(batch)} job(s): graph replays {stats[True]['graph_replays']} of "
+              f"{stats[True]['iterations']} iterations, results bitwise the direct ones")
