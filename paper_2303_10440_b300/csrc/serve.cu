@@ -1,11 +1,13 @@
 // Continuous-batching fit server (include/deltamic.h, "fit server").
 //
 // Engine thread, per iteration:
-//   admit   queued jobs move in (FIFO) while a batch slot and arena room are free; their
-//           mesh, target, PSF parameters, Adam state, vertex star and band live on the device;
-//   step    every active job advances by one Adam step: per-job stage kernels on one stream,
-//           and the two mesh-transform sums of all active jobs as one persistent batched
-//           launch each (work lists of equal-cost units pulled from an atomic counter);
+//   admit   queued jobs move in (in arrival order, or least work first) while a batch slot and
+//           arena room are free; their mesh, target, PSF parameters, optimiser state, vertex star
+//           and band live on the device;
+//   step    the selected resident jobs advance by one optimiser step: per-job stage kernels on
+//           each job's stream, and the two mesh-transform sums of all of them as one persistent
+//           batched launch each per label (work lists of equal-cost units pulled from an atomic
+//           counter); while the selection is unchanged the step replays as a captured CUDA graph;
 //   retire  jobs that reached their step count copy their results to the host and release
 //           their arena block.
 // Arrivals therefore join at the next iteration while earlier jobs are still running, and
