@@ -182,6 +182,39 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
     return r;
 }
 
+// Error-free sum of two floats (Knuth's two-sum): t + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& t, float& e) {
+    t = a + b;
+    const float bp = t - a;
+    e = (a - (t - bp)) + (b - bp);
+}
+
+// Deterministic block sum of per-thread compensated FP32 sums (thread value s - c, the convention of
+// a Kahan sum): within a warp the pairs are combined in FP32 by error-free additions in a fixed
+// butterfly order, the warps' values in FP64. No per-thread FP64 work. `scratch` holds >= 32 doubles;
+// result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum_comp(float s, float c, double* scratch) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        float t, e;
+        two_sum(s, s2, t, e);
+        s = t;
+        c = (c + c2) - e;  // (s1 - c1) + (s2 - c2) = t - ((c1 + c2) - e)
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = (double)s - (double)c;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = lane < NT / 32 ? scratch[lane] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
 // Division by a grid dimension without a run-time divide: for n < 2^32, n / d is the high word of
 // n * m with m = ceil(2^64 / d) (exact, since n (m - 2^64 / d) / 2^64 < 2^-32 < 1 / d).
 struct FastDiv {

@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "dm_kernels.cuh"
 
@@ -139,26 +140,29 @@ __device__ __forceinline__ double otf_expo(const double* psf, int kind, double x
     return c[0] * x * x + c[1] * y * y + c[2] * z * z + 2.0 * (c[3] * x * y + c[4] * x * z + c[5] * y * z);
 }
 
-// h_hat(xi) in the path's precision: FP32 (the FP32 images' own precision) or FP64.
+// h_hat(xi) in FP64 (the FP64 path).
 template <class R>
 __device__ __forceinline__ R otf_r(const double* psf, int kind, double x, double y, double z);
 template <>
-__device__ __forceinline__ float otf_r<float>(const double* psf, int kind, double x, double y, double z) {
-    const float xf = (float)x, yf = (float)y, zf = (float)z;
+__device__ __forceinline__ double otf_r<double>(const double* psf, int kind, double x, double y, double z) {
+    return exp(-0.5 * otf_expo(psf, kind, x, y, z));
+}
+// h_hat(xi) in FP32 (the FP32 images' own precision) from the PSF numbers rounded to FP32 (c[0..2]
+// sigma, c[3..8] covariance, staged once per block): no per-frequency FP64 load or conversion.
+__device__ __forceinline__ float otf_f(const float* c, int kind, float xf, float yf, float zf) {
     float e;
     if (kind == 0) {
-        const float s0 = (float)psf[0], s1 = (float)psf[1], s2 = (float)psf[2];
-        e = s0 * s0 * xf * xf + s1 * s1 * yf * yf + s2 * s2 * zf * zf;
+        e = c[0] * c[0] * xf * xf + c[1] * c[1] * yf * yf + c[2] * c[2] * zf * zf;
     } else {
-        const double* c = psf + 3;
-        e = (float)c[0] * xf * xf + (float)c[1] * yf * yf + (float)c[2] * zf * zf +
-            2.0f * ((float)c[3] * xf * yf + (float)c[4] * xf * zf + (float)c[5] * yf * zf);
+        e = c[3] * xf * xf + c[4] * yf * yf + c[5] * zf * zf +
+            2.0f * (c[6] * xf * yf + c[7] * xf * zf + c[8] * yf * zf);
     }
     return expf(-0.5f * e);
 }
-template <>
-__device__ __forceinline__ double otf_r<double>(const double* psf, int kind, double x, double y, double z) {
-    return exp(-0.5 * otf_expo(psf, kind, x, y, z));
+// The 9 PSF numbers in the path's precision, in shared memory (threads 0..8; a barrier follows).
+template <class R>
+__device__ __forceinline__ void stage_psf(const double* __restrict__ psf, R* c) {
+    if (threadIdx.x < 9) c[threadIdx.x] = (R)psf[threadIdx.x];
 }
 
 struct BandArgs {
@@ -276,6 +280,15 @@ struct TSum<double> {
     __device__ __forceinline__ void add(double v) { s += v; }
     __device__ __forceinline__ double get() const { return s; }
 };
+// Block sum of the threads' TSum values (result valid in thread 0; scratch >= 32 doubles).
+template <int NT>
+__device__ __forceinline__ double block_sum_t(const TSum<float>& p, double* scratch) {
+    return block_sum_comp<NT>(p.s, p.c, scratch);
+}
+template <int NT>
+__device__ __forceinline__ double block_sum_t(const TSum<double>& p, double* scratch) {
+    return block_sum<NT>(p.s, scratch);
+}
 
 // Wavevector component of integer frequency n in the path's precision.
 template <class R>
@@ -288,19 +301,25 @@ __global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, Fre
                                                 int kind, const double* __restrict__ d_norm, double tpx, double tpy,
                                                 double tpz, double inv_VL, Cx<R>* __restrict__ spec) {
     __shared__ R s_scale;  // one FP64 division per block, not per frequency
+    __shared__ R s_c[9];
     if (threadIdx.x == 0) s_scale = (R)(inv_VL / *d_norm);
+    stage_psf(psf, s_c);
     __syncthreads();
     const int64_t M = fs.dM ? *fs.dM : fs.M;
-    const int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x;
-    if (m >= M) return;
-    const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
-    int nx, ny, nz;
-    decode_h(idx, fs, nx, ny, nz);
-    const R hh = otf_r<R>(psf, kind, (double)wave<R>(nx, (R)tpx), (double)wave<R>(ny, (R)tpy),
-                          (double)wave<R>(nz, (R)tpz));
-    const R sc = hh * s_scale;
-    const Cx<R> s = S[m];
-    spec[idx] = Cx<R>{s.x * sc, s.y * sc};
+    // grid-stride, so that the per-block set-up above is paid by few blocks
+    for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M; m += (int64_t)gridDim.x * NT) {
+        const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
+        int nx, ny, nz;
+        decode_h(idx, fs, nx, ny, nz);
+        R hh;
+        if constexpr (std::is_same<R, float>::value)
+            hh = otf_f(s_c, kind, wave<R>(nx, (R)tpx), wave<R>(ny, (R)tpy), wave<R>(nz, (R)tpz));
+        else
+            hh = otf_r<R>(psf, kind, wave<R>(nx, (R)tpx), wave<R>(ny, (R)tpy), wave<R>(nz, (R)tpz));
+        const R sc = hh * s_scale;
+        const Cx<R> s = S[m];
+        spec[idx] = Cx<R>{s.x * sc, s.y * sc};
+    }
 }
 
 template <class R>
@@ -318,9 +337,8 @@ __global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* _
         lsum.add(wd * d);
         resid[j] = s * wd;
     }
-    double l = lsum.get();
+    double l = block_sum_t<NT>(lsum, scratch);
     if (kind == 1) l *= inv_n;
-    l = block_sum<NT>(l, scratch);
     if (threadIdx.x == 0) partial[blockIdx.x] = l;
 }
 
@@ -338,6 +356,20 @@ __device__ __forceinline__ void set_rec(FreqPairF32* fr, int64_t m, int nx, int 
     lane[4] = (float)z;
     lane[6] = (float)gr;
     lane[8] = (float)gi;
+}
+__device__ __forceinline__ void set_rec(FreqPairF32* fr, int64_t m, int nx, int ny, int nz, float x, float y, float z,
+                                        float gr, float gi) {
+    FreqPairF32& r = fr[m >> 1];
+    int32_t* n = (m & 1) ? r.nB : r.nA;
+    n[0] = nx;
+    n[1] = ny;
+    n[2] = nz;
+    float* lane = reinterpret_cast<float*>(&r.x) + (m & 1);
+    lane[0] = x;
+    lane[2] = y;
+    lane[4] = z;
+    lane[6] = gr;
+    lane[8] = gi;
 }
 __device__ __forceinline__ void set_rec(FreqF64* fr, int64_t m, int nx, int ny, int nz, double x, double y, double z,
                                         double gr, double gi) {
@@ -367,12 +399,14 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
     // the padded band, so each block reduces its partial sums once.
     __shared__ double scratch[32];
     __shared__ R s_rin;  // one FP64 division per block
+    __shared__ R s_c[9];
     if (threadIdx.x == 0) s_rin = (R)(1.0 / *d_norm);
+    stage_psf(psf, s_c);
     __syncthreads();
     const int64_t M = fs.dM ? *fs.dM : fs.M;
     const R rin = s_rin;
     const R cvl = (R)inv_VL;
-    const R s0 = (R)psf[0], s1 = (R)psf[1], s2 = (R)psf[2];
+    const R s0 = s_c[0], s1 = s_c[1], s2 = s_c[2];
     const R tx = (R)tpx, ty = (R)tpy, tz = (R)tpz;
     TSum<R> part[7];
     for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M_pad; m += (int64_t)gridDim.x * NT) {
@@ -384,11 +418,14 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
         int nx, ny, nz;
         decode_h(idx, fs, nx, ny, nz);
         const R x = wave<R>(nx, tx), y = wave<R>(ny, ty), z = wave<R>(nz, tz);
-        const double xd = (double)x, yd = (double)y, zd = (double)z;
         const R c = (nz == 0 || 2 * nz == fs.Nz) ? (R)1 : (R)2;
         const Cx<R> F = spec[idx];
         const R Gx = c * cvl * F.x, Gy = c * cvl * F.y;  // dL/dX
-        const R hh = otf_r<R>(psf, kind, xd, yd, zd);
+        R hh;
+        if constexpr (std::is_same<R, float>::value)
+            hh = otf_f(s_c, kind, x, y, z);
+        else
+            hh = otf_r<R>(psf, kind, x, y, z);
         const Cx<R> Sm = S[m];
         const R ux = Sm.x * rin, uy = Sm.y * rin;  // u_hat
         const R g = (Gx * ux + Gy * uy) * hh;      // Re(conj(G) X)
@@ -418,10 +455,10 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
             wr = Gui * ik2;
             wi = -Gur * ik2;
         }
-        set_rec(fr, m, nx, ny, nz, xd, yd, zd, (double)wr, (double)wi);
+        set_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
     }
     for (int k = 0; k < 7; ++k) {
-        const double v = block_sum<NT>(part[k].get(), scratch);
+        const double v = block_sum_t<NT>(part[k], scratch);
         if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = v;
     }
     if (threadIdx.x == 0) partial[blockIdx.x * NPART + 7] = 0.0;
@@ -767,7 +804,8 @@ cudaError_t launch_scatter(const Cx<R>* S, const FreqSrc& fs, const double* d_ps
         if (e != cudaSuccess) return e;
     }
     const double VL = g.L[0] * g.L[1] * g.L[2];
-    k_scatter<R><<<nblk(fs.M), NT, 0, st>>>(S, fs, d_psf, psf_kind, d_norm, 2.0 * M_PI / g.L[0], 2.0 * M_PI / g.L[1],
+    const unsigned nb = (unsigned)std::min<int64_t>(nblk(fs.M), 2048);
+    k_scatter<R><<<nb, NT, 0, st>>>(S, fs, d_psf, psf_kind, d_norm, 2.0 * M_PI / g.L[0], 2.0 * M_PI / g.L[1],
                                             2.0 * M_PI / g.L[2], 1.0 / VL, spec);
     return cudaGetLastError();
 }
