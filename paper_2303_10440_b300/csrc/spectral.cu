@@ -385,6 +385,28 @@ __device__ __forceinline__ void set_rec(FreqF64* fr, int64_t m, int nx, int ny, 
     r.Gi = gi;
     r.pad2 = 0.0;
 }
+// The gather's record writes. FP32: lanes 2k and 2k + 1 of a warp hold frequencies A and B of one
+// pair record and exchange halves, so that each writes 32 contiguous bytes with two 16-byte stores
+// (all 32 lanes must call it). FP64: one record per lane.
+__device__ __forceinline__ void put_rec(FreqPairF32* fr, int64_t m, int nx, int ny, int nz, float x, float y, float z,
+                                        float gr, float gi) {
+    const unsigned full = 0xffffffffu;
+    const int ox = __shfl_xor_sync(full, nx, 1), oy = __shfl_xor_sync(full, ny, 1), oz = __shfl_xor_sync(full, nz, 1);
+    const float px = __shfl_xor_sync(full, x, 1), py = __shfl_xor_sync(full, y, 1), pz = __shfl_xor_sync(full, z, 1);
+    const float pgr = __shfl_xor_sync(full, gr, 1), pgi = __shfl_xor_sync(full, gi, 1);
+    int4* r = reinterpret_cast<int4*>(fr + (m >> 1));
+    if ((m & 1) == 0) {  // A: nA[3], nB[0] | nB[1], nB[2], x.A, x.B
+        r[0] = make_int4(nx, ny, nz, ox);
+        r[1] = make_int4(oy, oz, __float_as_int(x), __float_as_int(px));
+    } else {  // B: y.A, y.B, z.A, z.B | Gr.A, Gr.B, Gi.A, Gi.B
+        r[2] = make_int4(__float_as_int(py), __float_as_int(y), __float_as_int(pz), __float_as_int(z));
+        r[3] = make_int4(__float_as_int(pgr), __float_as_int(gr), __float_as_int(pgi), __float_as_int(gi));
+    }
+}
+__device__ __forceinline__ void put_rec(FreqF64* fr, int64_t m, int nx, int ny, int nz, double x, double y, double z,
+                                        double gr, double gi) {
+    set_rec(fr, m, nx, ny, nz, x, y, z, gr, gi);
+}
 
 // Partials per block: [0..5] dL/dpsf (3 used for kind DIAG), [6] coefficient of d(norm)/dv.
 constexpr int NPART = 8;
@@ -410,52 +432,56 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
     const R tx = (R)tpx, ty = (R)tpy, tz = (R)tpz;
     TSum<R> part[7];
     for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M_pad; m += (int64_t)gridDim.x * NT) {
-        if (m >= M) {
-            set_rec(fr, m, 0, 0, 0, 0.0, 0.0, 0.0, 0.0, 0.0);
-            continue;
+        // padding records (m >= M) are zeros; every lane of a warp runs the same iterations (M_pad
+        // is a multiple of 256), as the paired record write below needs
+        int nx = 0, ny = 0, nz = 0;
+        R x = 0, y = 0, z = 0, wr = 0, wi = 0;
+        if (m < M) {
+            const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
+            decode_h(idx, fs, nx, ny, nz);
+            x = wave<R>(nx, tx);
+            y = wave<R>(ny, ty);
+            z = wave<R>(nz, tz);
+            const R c = (nz == 0 || 2 * nz == fs.Nz) ? (R)1 : (R)2;
+            const Cx<R> F = spec[idx];
+            const R Gx = c * cvl * F.x, Gy = c * cvl * F.y;  // dL/dX
+            R hh;
+            if constexpr (std::is_same<R, float>::value)
+                hh = otf_f(s_c, kind, x, y, z);
+            else
+                hh = otf_r<R>(psf, kind, x, y, z);
+            const Cx<R> Sm = S[m];
+            const R ux = Sm.x * rin, uy = Sm.y * rin;  // u_hat
+            const R g = (Gx * ux + Gy * uy) * hh;      // Re(conj(G) X)
+            if (kind == 0) {
+                part[0].add(-g * s0 * x * x);
+                part[1].add(-g * s1 * y * y);
+                part[2].add(-g * s2 * z * z);
+            } else {
+                const R hg = (R)-0.5 * g;
+                part[0].add(hg * x * x);
+                part[1].add(hg * y * y);
+                part[2].add(hg * z * z);
+                part[3].add(-g * x * y);
+                part[4].add(-g * x * z);
+                part[5].add(-g * y * z);
+            }
+            R Gur = Gx * hh * rin, Gui = Gy * hh * rin;  // dL/du_hat / norm
+            const bool zero = nx == 0 && ny == 0 && nz == 0;
+            if (zero) {
+                Gur = Gui = (R)0;  // u_hat(0) = 1 for every mesh: no gradient through xi = 0
+            } else {
+                part[6].add(-(Gur * ux + Gui * uy));  // -cq
+            }
+            wr = Gur;
+            wi = Gui;
+            if (mode == 1 && !zero) {  // volume: Gw = -i Gu / |xi|^2
+                const R ik2 = (R)1 / (x * x + y * y + z * z);
+                wr = Gui * ik2;
+                wi = -Gur * ik2;
+            }
         }
-        const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
-        int nx, ny, nz;
-        decode_h(idx, fs, nx, ny, nz);
-        const R x = wave<R>(nx, tx), y = wave<R>(ny, ty), z = wave<R>(nz, tz);
-        const R c = (nz == 0 || 2 * nz == fs.Nz) ? (R)1 : (R)2;
-        const Cx<R> F = spec[idx];
-        const R Gx = c * cvl * F.x, Gy = c * cvl * F.y;  // dL/dX
-        R hh;
-        if constexpr (std::is_same<R, float>::value)
-            hh = otf_f(s_c, kind, x, y, z);
-        else
-            hh = otf_r<R>(psf, kind, x, y, z);
-        const Cx<R> Sm = S[m];
-        const R ux = Sm.x * rin, uy = Sm.y * rin;  // u_hat
-        const R g = (Gx * ux + Gy * uy) * hh;      // Re(conj(G) X)
-        if (kind == 0) {
-            part[0].add(-g * s0 * x * x);
-            part[1].add(-g * s1 * y * y);
-            part[2].add(-g * s2 * z * z);
-        } else {
-            const R hg = (R)-0.5 * g;
-            part[0].add(hg * x * x);
-            part[1].add(hg * y * y);
-            part[2].add(hg * z * z);
-            part[3].add(-g * x * y);
-            part[4].add(-g * x * z);
-            part[5].add(-g * y * z);
-        }
-        R Gur = Gx * hh * rin, Gui = Gy * hh * rin;  // dL/du_hat / norm
-        const bool zero = nx == 0 && ny == 0 && nz == 0;
-        if (zero) {
-            Gur = Gui = (R)0;  // u_hat(0) = 1 for every mesh: no gradient through xi = 0
-        } else {
-            part[6].add(-(Gur * ux + Gui * uy));  // -cq
-        }
-        R wr = Gur, wi = Gui;
-        if (mode == 1 && !zero) {  // volume: Gw = -i Gu / |xi|^2
-            const R ik2 = (R)1 / (x * x + y * y + z * z);
-            wr = Gui * ik2;
-            wi = -Gur * ik2;
-        }
-        set_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
+        put_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
     }
     for (int k = 0; k < 7; ++k) {
         const double v = block_sum_t<NT>(part[k], scratch);
@@ -831,6 +857,7 @@ template <class R, class FR>
 cudaError_t launch_gather(int mode, const Cx<R>* spec, const Cx<R>* S, const FreqSrc& fs, const double* d_psf,
                           int psf_kind, const double* d_norm, const Geom& g, FR* fr, int64_t M_pad, double* partial,
                           int* n_blocks_out, cudaStream_t st) {
+    if (M_pad % NT != 0) return cudaErrorInvalidValue;  // whole warps per iteration (paired record writes)
     const unsigned b = (unsigned)std::min<int64_t>(nblk(M_pad), 2048);  // grid-stride: one reduction per block
     *n_blocks_out = (int)b;
     const double VL = g.L[0] * g.L[1] * g.L[2];
