@@ -215,6 +215,35 @@ __device__ __forceinline__ double block_sum_comp(float s, float c, double* scrat
     return r;
 }
 
+// K such block sums at once, with two barriers in all: thread k < K returns sum k (the warps' values
+// added in warp order); other threads return 0. `scratch` holds >= K * NT / 32 doubles.
+template <int NT, int K>
+__device__ __forceinline__ double block_sums_comp(float (&s)[K], float (&c)[K], double* scratch) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, s[k], o), c2 = __shfl_xor_sync(0xffffffffu, c[k], o);
+            float t, e;
+            two_sum(s[k], s2, t, e);
+            s[k] = t;
+            c[k] = (c[k] + c2) - e;
+        }
+    }
+    constexpr int W = NT / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) scratch[k * W + wid] = (double)s[k] - (double)c[k];
+    }
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < K)
+        for (int w = 0; w < W; ++w) r += scratch[threadIdx.x * W + w];
+    return r;
+}
+
 // Division by a grid dimension without a run-time divide: for n < 2^32, n / d is the high word of
 // n * m with m = ceil(2^64 / d) (exact, since n (m - 2^64 / d) / 2^64 < 2^-32 < 1 / d).
 struct FastDiv {

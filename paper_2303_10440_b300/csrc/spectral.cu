@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
                                                double* __restrict__ partial) {
     // Per frequency in the path's precision R; the sums over frequencies in FP64. Grid-stride over
     // the padded band, so each block reduces its partial sums once.
-    __shared__ double scratch[32];
+    __shared__ double scratch[7 * NT / 32];  // >= 32 doubles for the FP64 block sums
     __shared__ R s_rin;  // one FP64 division per block
     __shared__ R s_c[9];
     if (threadIdx.x == 0) s_rin = (R)(1.0 / *d_norm);
@@ -483,9 +483,20 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
         }
         put_rec(fr, m, nx, ny, nz, x, y, z, wr, wi);
     }
-    for (int k = 0; k < 7; ++k) {
-        const double v = block_sum_t<NT>(part[k], scratch);
-        if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = v;
+    if constexpr (std::is_same<R, float>::value) {
+        float ps[7], pc[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            ps[k] = part[k].s;
+            pc[k] = part[k].c;
+        }
+        const double v = block_sums_comp<NT, 7>(ps, pc, scratch);
+        if (threadIdx.x < 7) partial[blockIdx.x * NPART + threadIdx.x] = v;
+    } else {
+        for (int k = 0; k < 7; ++k) {
+            const double v = block_sum_t<NT>(part[k], scratch);
+            if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = v;
+        }
     }
     if (threadIdx.x == 0) partial[blockIdx.x * NPART + 7] = 0.0;
 }
