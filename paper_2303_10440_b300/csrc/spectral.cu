@@ -780,6 +780,27 @@ __global__ void k_set_params(double* dst, Params16 p, int n) {
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + NT - 1) / NT); }
 
+// Blocks of NT threads of kernel FN that the current device holds at once (occupancy x SM count),
+// looked up once per device and kernel.
+template <auto FN>
+cudaError_t one_wave(int* out) {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int w = dev < 64 ? cache[dev].load() : 0;
+    if (w == 0) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, FN, NT, 0);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        w = std::max(1, per_sm) * std::max(1, sms);
+        if (dev < 64) cache[dev].store(w);
+    }
+    *out = w;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 template <class Rec>
@@ -842,7 +863,10 @@ cudaError_t launch_scatter(const Cx<R>* S, const FreqSrc& fs, const double* d_ps
         if (e != cudaSuccess) return e;
     }
     const double VL = g.L[0] * g.L[1] * g.L[2];
-    const unsigned nb = (unsigned)std::min<int64_t>(nblk(fs.M), 2048);
+    int wave = 0;
+    const cudaError_t e = one_wave<k_scatter<R>>(&wave);  // grid-stride over one wave of resident blocks
+    if (e != cudaSuccess) return e;
+    const unsigned nb = (unsigned)std::min<int64_t>(nblk(fs.M), wave);
     k_scatter<R><<<nb, NT, 0, st>>>(S, fs, d_psf, psf_kind, d_norm, 2.0 * M_PI / g.L[0], 2.0 * M_PI / g.L[1],
                                             2.0 * M_PI / g.L[2], 1.0 / VL, spec);
     return cudaGetLastError();
@@ -855,8 +879,10 @@ template cudaError_t launch_scatter<double>(const Cx<double>*, const FreqSrc&, c
 template <class R>
 cudaError_t launch_loss(const R* I, const R* T, int64_t n, int kind, R* resid, double* partial, int* n_blocks_out,
                         cudaStream_t st) {
-    int64_t b = nblk(n);
-    if (b > 4096) b = 4096;
+    int wave = 0;
+    const cudaError_t e = one_wave<k_loss<R>>(&wave);  // grid-stride over one wave of resident blocks
+    if (e != cudaSuccess) return e;
+    const int64_t b = std::min<int64_t>(nblk(n), std::min(wave, 4096));
     *n_blocks_out = (int)b;
     k_loss<R><<<(unsigned)b, NT, 0, st>>>(I, T, n, kind, resid, partial, 1.0 / (double)n);
     return cudaGetLastError();
@@ -872,19 +898,9 @@ cudaError_t launch_gather(int mode, const Cx<R>* spec, const Cx<R>* S, const Fre
     if (M_pad % NT != 0) return cudaErrorInvalidValue;  // whole warps per iteration (paired record writes)
     // grid-stride over one wave of resident blocks: each block's seven reductions are paid once per
     // block slot (at 128^3 with 80 triangles 2048 blocks took 45 us, one wave of 592 27 us)
-    static std::atomic<int> wave_blocks[64];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    int wave = 0;
+    cudaError_t e = one_wave<k_gather<R, FR>>(&wave);
     if (e != cudaSuccess) return e;
-    int wave = dev < 64 ? wave_blocks[dev].load() : 0;
-    if (wave == 0) {
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gather<R, FR>, NT, 0);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        wave = std::max(1, per_sm) * std::max(1, sms);
-        if (dev < 64) wave_blocks[dev].store(wave);
-    }
     const unsigned b = (unsigned)std::min<int64_t>(nblk(M_pad), wave);
     *n_blocks_out = (int)b;
     const double VL = g.L[0] * g.L[1] * g.L[2];
