@@ -98,6 +98,23 @@ def test_adam_uniform_matches_oracle(r64):
         assert rel(m.cpu().numpy(), m0) < 1e-15 and rel(v.cpu().numpy(), v0) < 1e-15
 
 
+def test_adam_matches_oracle(r64, r32):
+    """dm_adam (the fit loop's vertex and PSF optimiser) against the oracle's Adam, step by step."""
+    rng = np.random.default_rng(8)
+    n = 3 * 900
+    for r, tol in ((r64, 1e-14), (r32, 1e-14)):
+        p0, m0, v0 = rng.normal(size=n), np.zeros(n), np.zeros(n)
+        p = torch.as_tensor(p0.copy()).cuda()
+        m, v = torch.zeros(n, dtype=torch.float64).cuda(), torch.zeros(n, dtype=torch.float64).cuda()
+        for t in range(1, 6):
+            g = rng.normal(size=n) * 1e-9
+            d0, m0, v0 = opt.adam(g, m0, v0, t, 0.3, 0.9, 0.999, 1e-20)
+            p0 = p0 - d0
+            r.adam(p, torch.as_tensor(g).cuda(), m, v, t, 0.3, 0.9, 0.999, 1e-20)
+            assert rel(p.cpu().numpy(), p0) < tol
+            assert rel(m.cpu().numpy(), m0) < 1e-15 and rel(v.cpu().numpy(), v0) < 1e-15
+
+
 def _tiny_case():
     grid = synth.Grid(n=(12, 12, 10), h=(1.0, 1.0, 1.5), origin=(0.2, -0.1, 0.3))
     V0, F = synth.sphere_mesh(1, 3.2, grid.center)

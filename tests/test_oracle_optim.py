@@ -2,7 +2,8 @@
 Section 5.2 PSF step).
 
 References: the spectrum of the icosahedron graph, a brute-force dense Laplacian, the closed
-form of uniform Adam under a constant gradient, the dense matrix power (1 + lambda L)^-2,
+forms of uniform and plain Adam under a constant gradient
+and without memory, plain Adam's moments written as explicit weighted sums, the dense matrix power (1 + lambda L)^-2,
 finite differences through Sigma = C C^T, and the invariants of the two sub-problems.
 """
 
@@ -63,6 +64,59 @@ def test_uniform_adam_closed_forms():
     g2 = np.random.default_rng(2).normal(size=(40, 3))
     d, _, _ = opt.adam_uniform(g2, m, v, 7, 0.3, 0.0, 0.0, 0.0)
     assert np.max(np.abs(d - 0.3 * g2 / np.abs(g2).max())) < 1e-14
+
+
+def test_adam_closed_forms():
+    """Plain Adam (Kingma and Ba 2014; the PSF step of Section 5.2 and the plain vertex optimiser)."""
+    g = np.random.default_rng(5).normal(size=(40, 3))
+    m, v = np.zeros_like(g), np.zeros_like(g)
+    # a constant gradient: the bias-corrected moments are exactly g and g^2, so every step is
+    # lr g / (|g| + eps) (a missing or wrong bias correction scales steps 1..5 differently)
+    for t in range(1, 6):
+        d, m, v = opt.adam(g, m, v, t, 0.1, 0.9, 0.999, 1e-3)
+        assert np.max(np.abs(d - 0.1 * g / (np.abs(g) + 1e-3))) < 1e-14
+    # no memory (beta1 = beta2 = 0): the step is lr g / (|g| + eps) whatever the history
+    g2 = np.random.default_rng(6).normal(size=(40, 3))
+    d, _, _ = opt.adam(g2, m, v, 7, 0.3, 0.0, 0.0, 1e-2)
+    assert np.max(np.abs(d - 0.3 * g2 / (np.abs(g2) + 1e-2))) < 1e-14
+    # the first step is lr sign(g) when eps = 0, for any beta
+    d, _, _ = opt.adam(g2, np.zeros_like(g2), np.zeros_like(g2), 1, 0.2, 0.7, 0.95, 0.0)
+    assert np.max(np.abs(d - 0.2 * np.sign(g2))) < 1e-14
+
+
+def test_adam_matches_the_moments_written_as_weighted_sums():
+    """The recursion against the moments' explicit form: m_hat_t = sum_i b1^(t-i) (1 - b1) g_i / (1 - b1^t)
+    (the bias correction makes the weights sum to one), likewise v_hat with g_i^2; also the scale invariance
+    of the step (eps = 0) and Kingma and Ba's bound |step| <= lr (1 - b1) / sqrt(1 - b2) for (1 - b1) >
+    sqrt(1 - b2)."""
+    rng = np.random.default_rng(7)
+    b1, b2, lr, eps = 0.9, 0.999, 0.05, 1e-8
+    gs = [rng.normal(size=(30, 3)) * rng.uniform(0.1, 3.0) for _ in range(9)]
+    m, v = np.zeros((30, 3)), np.zeros((30, 3))
+    for t in range(1, len(gs) + 1):
+        d, m, v = opt.adam(gs[t - 1], m, v, t, lr, b1, b2, eps)
+        w1 = np.array([b1 ** (t - i) * (1 - b1) for i in range(1, t + 1)])
+        w2 = np.array([b2 ** (t - i) * (1 - b2) for i in range(1, t + 1)])
+        assert abs(w1.sum() - (1 - b1**t)) < 1e-15 and abs(w2.sum() - (1 - b2**t)) < 1e-15
+        mh = sum(w * g for w, g in zip(w1, gs[:t])) / w1.sum()
+        vh = sum(w * g * g for w, g in zip(w2, gs[:t])) / w2.sum()
+        ref = lr * mh / (np.sqrt(vh) + eps)
+        assert np.max(np.abs(d - ref)) < 1e-13 * lr
+    # scale invariance with eps = 0: gradients times c > 0 give the same steps
+    m1, v1, m2, v2 = (np.zeros((30, 3)) for _ in range(4))
+    for t, g in enumerate(gs, start=1):
+        d1, m1, v1 = opt.adam(g, m1, v1, t, lr, b1, b2, 0.0)
+        d2, m2, v2 = opt.adam(1e-9 * g, m2, v2, t, lr, b1, b2, 0.0)
+        assert np.max(np.abs(d1 - d2)) < 1e-13 * lr
+    # the step bound, on the worst case for it: one large gradient after many zeros
+    b1, b2 = 0.5, 0.99  # (1 - b1) = 0.5 > sqrt(1 - b2) = 0.1
+    m, v = np.zeros(1), np.zeros(1)
+    steps = []
+    for t in range(1, 60):
+        d, m, v = opt.adam(np.array([1.0 if t == 59 else 0.0]), m, v, t, 1.0, b1, b2, 0.0)
+        steps.append(abs(d[0]) if t == 59 else 0.0)
+    bound = (1 - b1) / np.sqrt(1 - b2)
+    assert steps[-1] <= bound * (1 + 1e-12) and steps[-1] > 0.6 * bound
 
 
 def test_large_steps_without_moments_is_the_printed_update():
