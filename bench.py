@@ -1,13 +1,14 @@
 #!/usr/bin/env python
 """Throughput of one shape-fit step of the mesh-Fourier renderer on one B300.
 
-A step is one pass of the whole hot path on the single-cell workload (icosphere
-level 4 = 5120 triangles, SH l <= 6 deformation, 128^3 grid of (0.5, 0.5, 1) um
-voxels, Gaussian PSF sigma = (0.2, 0.2, 0.6) um, narrow band h_hat > 1e-3):
-narrow band, triangle records, mesh transform over every (band frequency,
-triangle) pair, transfer-function multiply, inverse 3D DFT, MSE loss and
-residual, forward 3D DFT of the residual, dL/dsigma, the adjoint mesh transform,
-per-vertex assembly, and the Adam update of the vertices.
+A step is one pass of the whole hot path on the largest single-fit workload
+(icosphere level 5 = 20480 triangles, SH l <= 10 deformation, 256x256x128 grid of
+(0.5, 0.5, 1) um voxels, Gaussian PSF sigma = (0.25, 0.25, 0.7) um, the whole
+half spectrum of 4,259,840 frequencies): triangle records, mesh transform over
+every (frequency, triangle) pair, transfer-function multiply, inverse 3D DFT, MSE
+loss and residual, forward 3D DFT of the residual, dL/dsigma, the adjoint mesh
+transform, per-vertex assembly, and the Adam update of the vertices.
+`--workload c2` runs the 128^3 single cell (5120 triangles, narrow band h_hat > 1e-3).
 
 Metric: forward + backward (triangle x frequency) terms per second,
 2 * M * n_t / step time. Prints one JSON line (rank 0).
@@ -42,15 +43,43 @@ OPS_PER_TERM = {"fwd": 45, "adj": 110}
 MUFU_PER_TERM = {"fwd": 7, "adj": 7}
 
 
+# DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum + dram__bytes_write.sum from one
+# ncu capture of `python bench.py --workload W --steps 1 --warmup 3 --no-cpu-baseline --no-e2e --no-serve
+# --no-fp64`, one kernel, one launch), keyed by workload and kernel, with the SHA-256 of the mesh-transform
+# sources it was taken on: a capture of other sources is not reported (the traffic is then null).
+MEASURED_TRAFFIC = {}
+TRAFFIC_SOURCES = ("meshft_f32.cu", "meshft_math.cuh", "dm_kernels.cuh", "dm_common.cuh")
+
+
+def kernel_sources_digest() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2303_10440_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, kernel: str) -> dict:
+    m = MEASURED_TRAFFIC.get((workload, kernel))
+    digest = kernel_sources_digest()
+    if not m or m["sources"] != digest:
+        return {"traffic": None, "traffic_note": f"no ncu capture of these kernel sources ({digest}) on this workload"}
+    return {"traffic": m["bytes"], "traffic_unit": "DRAM bytes per launch (ncu dram__bytes_read.sum + "
+            "dram__bytes_write.sum)", "traffic_sources": digest}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["c2", "c3", "c1", "c2s"], default="c2",
-                   help="c2: 128^3 single cell (default); c3: 256x256x128, 20480 triangles; c1: 32^3 icosphere; "
-                   "c2s: the c2 cell on a 64^3 grid of doubled voxels (small profiling case)")
+    p.add_argument("--workload", choices=["c3", "c2", "c1", "c2s", "c3s"], default="c3",
+                   help="c3: 256x256x128, 20480 triangles (default); c2: 128^3 single cell, 5120 triangles; "
+                   "c1: 32^3 icosphere; c2s: the c2 cell on a 64^3 grid of doubled voxels and c3s: the c3 cell on "
+                   "128x128x64 doubled voxels (small profiling cases)")
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
                    help="fp32: the FP32 mixed path (headline); fp64: the plain FP64 path (comparator)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -88,6 +117,11 @@ def make_case(name):
         c = synth.config_c2()
         c.grid = synth.Grid(n=(64, 64, 64), h=(1.0, 1.0, 2.0))
         c.name = "c2s_cell_sh6_64cube_profile"
+        return c
+    if name == "c3s":
+        c = synth.config_c3()
+        c.grid = synth.Grid(n=(128, 128, 64), h=(1.0, 1.0, 2.0))
+        c.name = "c3s_cell_sh10_128x128x64_profile"
         return c
     return synth.config_c1()
 
@@ -190,10 +224,16 @@ def time_oracle_step(case, xi, G):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(case, n_freq=16384):
+def cpu_sample_freqs(case, terms=1.6e8):
+    """Band frequencies of the CPU oracle's sample: about `terms` forward terms (x all triangles), which
+    the FP64 oracle evaluates forward and adjoint in roughly 10-20 s on 16 host cores."""
+    return max(512, int(terms / case.F.shape[0]))
+
+
+def cpu_baseline(case, n_freq=None):
     import oracle
 
-    xi, G, _ = oracle_sample(case, n_freq)
+    xi, G, _ = oracle_sample(case, n_freq or cpu_sample_freqs(case))
     dt = time_oracle_step(case, xi, G)
     terms = 2.0 * len(xi) * case.F.shape[0]
     return {
@@ -213,7 +253,7 @@ def run_reference(args):
     import oracle
 
     case = make_case(args.workload)
-    n_freq = 384
+    n_freq = max(96, int(8e6 / case.F.shape[0]))  # ~0.7 s of oracle work per step
     xi, G, M = oracle_sample(case, n_freq)
     for _ in range(args.warmup):
         time_oracle_step(case, xi, G)
@@ -236,7 +276,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(case, M, "oracle step = sampled band frequencies x all triangles"),
+        "config": workload_config(case, M),
         "cpu_baseline": {
             "value": value,
             "unit": UNIT,
@@ -250,7 +290,11 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def workload_config(case, M, l2):
+L2_NOTE = "flushed (256 MB write) between timed steps, outside the events"
+
+
+def workload_config(case, M, l2=L2_NOTE):
+    """The workload's description; identical in both arms of the benchmark."""
     return {
         "workload": case.name,
         "grid": list(case.grid.n),
@@ -465,9 +509,6 @@ def run_ours(args):
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     value, t_max = whole_job_value(t_ms, terms_step * args.steps, world, dev)
 
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels from
-    # one ncu capture of this command on the 128^3 workload; other workloads were not captured
-    measured_traffic = {("c2", "k_adj_f32"): 34908416 + 41746176, ("c2", "k_fwd_f32"): 4866816 + 9900544}
 
     # roofline of the dominant kernel (event-timed inside the library on this stream)
     dom = max(("fwd", "adj"), key=lambda s: stages[s][0])
@@ -485,8 +526,7 @@ def run_ours(args):
         "peak": peak,
         "unit": "Tops/s",
         "frac": achieved / peak,
-        "traffic": measured_traffic.get((args.workload, kern[dom])),
-        "traffic_unit": "bytes per launch (ncu, profiles/k_adj_f32_k_fwd_f32_c2_128cube.md)",
+        **measured_traffic(args.workload, kern[dom]),
         "ops_per_term": OPS_PER_TERM[dom],
         "mufu_per_term": MUFU_PER_TERM[dom],
         "terms_per_launch": terms_launch,
@@ -510,7 +550,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic",
-        "config": workload_config(case, M, "flushed (256 MB write) between timed steps, outside the events"),
+        "config": workload_config(case, M),
         "roofline": roofline,
         "clocks": clk,
         "gpu_launches": int(launches),
@@ -530,9 +570,12 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def fp64_plain_step(case, grid, psf, T_dev, terms_step, dev):
-    """The plain FP64 path beside the FP32 one: the same fit step (dm_loss_and_grad on device
-    buffers) in an FP64 context, one warm-up and one CUDA-event-timed step."""
+def fp64_plain_step(case, grid, psf, T_dev, terms_step, dev, full_limit=2e10):
+    """The plain FP64 path beside the FP32 one. Up to `full_limit` terms per step: the same fit step
+    (dm_loss_and_grad on device buffers) in an FP64 context, one warm-up and one CUDA-event-timed step.
+    Larger workloads (one FP64 step of the 256x256x128 cell takes over a minute): the two FP64 mesh-transform
+    sums (dm_meshft, dm_meshft_adjoint) over a seeded random 1/16 of the band x all triangles, whose cost is
+    linear in the terms; the stage kernels are < 2% of a step."""
     import torch
 
     from paper_2303_10440_b300 import Renderer
@@ -540,18 +583,46 @@ def fp64_plain_step(case, grid, psf, T_dev, terms_step, dev):
     r64 = Renderer("fp64", device=dev.index or 0)
     Vd = torch.as_tensor(case.V_init).to(dev)
     Fd = torch.as_tensor(case.F).to(dev)
-    T64 = T_dev.double()
-    r64.loss_and_grad(Vd, Fd, grid, psf, T64, "mse")
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if terms_step <= full_limit:
+        T64 = T_dev.double()
+        r64.loss_and_grad(Vd, Fd, grid, psf, T64, "mse")
+        torch.cuda.synchronize(dev)
+        a.record()
+        r64.loss_and_grad(Vd, Fd, grid, psf, T64, "mse")
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        r64.close()
+        return {"value": terms_step / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 1,
+                "note": "same workload and step through the FP64 context (plain path); FP64 rate-bound on B300"}
+    band = r64.band(grid, psf).cpu().numpy()
+    rng = np.random.default_rng(11)
+    sel = np.sort(rng.choice(len(band), size=len(band) // 16, replace=False))
+    nzh = grid.n[2] // 2 + 1
+    idx = band[sel].astype(np.int64)
+    iz, t = idx % nzh, idx // nzh
+    iy, ix = t % grid.n[1], t // grid.n[1]
+    nx = np.where(ix < (grid.n[0] + 1) // 2, ix, ix - grid.n[0])
+    ny = np.where(iy < (grid.n[1] + 1) // 2, iy, iy - grid.n[1])
+    fn = torch.as_tensor(np.stack([nx, ny, iz], axis=1).astype(np.int32)).to(dev)
+    G = torch.randn(len(sel), dtype=torch.complex128, device=dev) / len(sel)
+    r64.meshft(Vd, Fd, grid, fn[:4096])
+    r64.meshft_adjoint(Vd, Fd, grid, fn[:4096], G[:4096])
     torch.cuda.synchronize(dev)
     a.record()
-    r64.loss_and_grad(Vd, Fd, grid, psf, T64, "mse")
+    r64.meshft(Vd, Fd, grid, fn)
+    r64.meshft_adjoint(Vd, Fd, grid, fn, G)
     b.record()
     torch.cuda.synchronize(dev)
     ms = a.elapsed_time(b)
     r64.close()
-    return {"value": terms_step / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": 1,
-            "note": "same workload and step through the FP64 context (plain path); FP64 rate-bound on B300"}
+    terms = 2.0 * len(sel) * case.F.shape[0]
+    return {"value": terms / (ms * 1e-3), "unit": UNIT, "ms_sample": ms, "ms_per_step_extrapolated":
+            ms * terms_step / terms, "steps": 1,
+            "note": f"FP64 context: dm_meshft + dm_meshft_adjoint on a seeded random 1/16 of the band "
+            f"({len(sel)} frequencies) x all {case.F.shape[0]} triangles, CUDA-event timed; the per-step time is "
+            f"extrapolated linearly in terms (FP64 rate-bound on B300)"}
 
 
 def e2e_through_host_buffers(r, case, grid, psf, T_dev, terms_step, args, dev, world):
@@ -985,11 +1056,11 @@ def run_scaling_mode(args):
 def run_mufu_probe(args):
     """Throughput of the MUFU sin/cos and reciprocal instructions the mesh-transform sums use, measured with
     a kernel of independent chains (the XU roofline of the forward sum)."""
-    import torch
+    from paper_2303_10440_b300 import build
 
-    from paper_2303_10440_b300 import _lib
-
-    lib = _lib.load()
+    lib = ctypes.CDLL(build.build_probe())
+    lib.dm_probe_mufu.restype = ctypes.c_int
+    lib.dm_probe_mufu.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]
     res = {}
     for kind, name in ((0, "sincos"), (1, "rcp")):
         ops = ctypes.c_double()

@@ -81,7 +81,6 @@ typedef struct dm_ctx dm_ctx;
 typedef struct {
     int32_t precision;     /* DM_FP64 or DM_FP32_MIXED */
     int32_t device;        /* CUDA device ordinal */
-    int32_t deterministic; /* reductions are always deterministic; kept for ABI growth */
     int32_t no_graphs;     /* 0: dm_fit / dm_fit_resume capture one optimisation step as a CUDA graph
                             * and replay it; 1: enqueue every step's kernels one by one. Results are
                             * bitwise identical either way. */
@@ -159,12 +158,6 @@ dm_status dm_profile_enable(dm_ctx* ctx, int32_t enable);
 /* ms, calls: arrays of DM_NUM_STAGES (either may be NULL). */
 dm_status dm_profile_read(dm_ctx* ctx, double* ms, int64_t* calls);
 
-/* Instrumentation with no counterpart in the paper: the throughput of the MUFU operations the mesh
- * transform spends per term, kind 0 = sin/cos pairs (__sincosf), kind 1 = approximate reciprocals, in
- * operations per second on `device` (a sin/cos pair counts 2). Runs two launches of independent
- * dependency chains on the default stream and synchronises. */
-dm_status dm_probe_mufu(int32_t kind, int32_t device, double* ops_per_s);
-
 /* Failure-detection check with no counterpart in the paper: runs one block whose threads wait on an
  * mbarrier that nothing completes, with the bounded wait the mesh-transform pipelines use, limited to
  * limit_ns (<= 2 s). *status = DM_ERR_TIMEOUT when the wait expired and was reported through the
@@ -208,9 +201,12 @@ dm_status dm_r2c(dm_ctx* ctx, const dm_grid* grid, const void* image, void* spec
  * for a face index outside [0, n_v), bit 4 for a non-finite vertex, bit 8 for a zero total area
  * or non-positive enclosed volume (stream ordered).
  * Returns DM_ERR_ARG for NULL or host pointers, n_t > DM_NOALLOC_MAX_TRIANGLES or bad sizes;
- * DM_ERR_CUDA if a launch fails. The first call on a device looks up the scratch address
- * (once per device), so make it before any stream capture. All calls on a device share the
- * scratch: calls that overlap on the GPU race and must be serialised by the caller. */
+ * DM_ERR_CUDA if a launch fails. The first call on a device is a start-up warm-up: it looks up the
+ * scratch address (once per device) and, with CUDA's lazy module loading, is when the kernels'
+ * modules and the scratch array are placed on the device, so it can still take device memory or
+ * fail under memory pressure; make it at start-up, before any stream capture. Later calls take no
+ * device memory. All calls on a device share the scratch: calls that overlap on the GPU race and
+ * must be serialised by the caller. */
 #define DM_NOALLOC_MAX_TRIANGLES 65536
 #define DM_NOALLOC_SCRATCH_BYTES (8u << 20)
 dm_status dm_meshft_noalloc(const dm_mesh* mesh, const dm_grid* grid, const int32_t* freq_n, int64_t M, void* S_out,

@@ -32,7 +32,7 @@ OPTIMIZERS = {"adam": 0, "large_steps": 1}
 
 
 class dm_options(ctypes.Structure):
-    _fields_ = [("precision", c_i32), ("device", c_i32), ("deterministic", c_i32), ("no_graphs", c_i32)]
+    _fields_ = [("precision", c_i32), ("device", c_i32), ("no_graphs", c_i32)]
 
 
 class dm_grid(ctypes.Structure):
@@ -199,7 +199,6 @@ _SIGS = {
     "dm_server_get_stats": (c_i32, [c_p, ctypes.POINTER(dm_server_stats)]),
     "dm_server_clock": (c_f64, [c_p]),
     "dm_server_shutdown": (c_i32, [c_p]),
-    "dm_probe_mufu": (c_i32, [c_i32, c_i32, ctypes.POINTER(c_f64)]),
     "dm_probe_wait_timeout": (c_i32, [c_i32, ctypes.c_uint64, ctypes.POINTER(c_i32)]),
     "dm_smooth_solve": (c_i32, [c_p, c_p, c_i64, c_i64, c_f64, c_p, c_p, c_f64, c_i32, c_p, c_p]),
     "dm_adam_uniform": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i64, c_f64, c_f64, c_f64, c_f64, c_i64, c_p]),

@@ -91,7 +91,7 @@ class Renderer:
         self.precision = precision
         self.real = torch.float32 if precision == "fp32" else torch.float64
         self.cplx = torch.complex64 if precision == "fp32" else torch.complex128
-        opt = _lib.dm_options(_lib.DM_FP32_MIXED if precision == "fp32" else _lib.DM_FP64, int(device), 1,
+        opt = _lib.dm_options(_lib.DM_FP32_MIXED if precision == "fp32" else _lib.DM_FP64, int(device),
                               0 if graphs else 1)
         h = ctypes.c_void_p()
         st = self.lib.dm_create(ctypes.byref(h), ctypes.byref(opt))

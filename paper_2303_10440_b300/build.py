@@ -10,6 +10,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdeltamic.so")
+# benchmark-only MUFU throughput probe, kept out of the product library
+PROBE_SRC = os.path.join(HERE, "bench_probe", "mufu_probe.cu")
+PROBE_LIB = os.path.join(HERE, "libdm_mufu_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -31,7 +34,19 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in deps())
 
 
+def build_probe(force: bool = False) -> str:
+    """The benchmark-only MUFU probe library (one source file, no dependency on the product library)."""
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_SRC) <= os.path.getmtime(PROBE_LIB):
+        return PROBE_LIB
+    nvcc = os.environ.get("NVCC", "nvcc")
+    tmp = PROBE_LIB + ".tmp"
+    subprocess.run([nvcc, *ARCH, *FLAGS, "-shared", PROBE_SRC, "-o", tmp, "-lcudart"], check=True)
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    build_probe(force)
     if not force and up_to_date():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")

@@ -17,8 +17,10 @@
 //   on the GPU (different streams, or host threads using the same device) race on
 //   it and must be serialised by the caller;
 // * the first call on a device looks up the array's device address with
-//   cudaGetSymbolAddress (once per device); make that first call before any
-//   stream capture.
+//   cudaGetSymbolAddress (once per device); under CUDA's lazy module loading it is
+//   also when the kernels' modules and the array are placed on the device, so it
+//   can still take device memory: make that first call at start-up, as a warm-up,
+//   before any stream capture. Later calls take no device memory.
 #include <mutex>
 
 #include "../../include/deltamic.h"

@@ -865,7 +865,7 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     if (!out || !opt || opt->max_jobs < 1) return DM_ERR_ARG;
     if (opt->policy != DM_SCHED_FIFO && opt->policy != DM_SCHED_SHORTEST) return DM_ERR_ARG;
     *out = nullptr;
-    dm_options o{DM_FP32_MIXED, opt->device, 1, 0};
+    dm_options o{DM_FP32_MIXED, opt->device, 0};
     dm_ctx* ctx = nullptr;
     dm_status s = dm_create(&ctx, &o);
     if (s != DM_OK) return s;

@@ -421,6 +421,7 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
     // Per frequency in the path's precision R; the sums over frequencies in FP64. Grid-stride over
     // the padded band, so each block reduces its partial sums once.
     __shared__ double scratch[7 * NT / 32];  // >= 32 doubles for the FP64 block sums
+    static_assert(7 * NT / 32 >= 32 && NT >= 7, "k_gather's scratch serves block_sum_t (32) and 7 sums");
     __shared__ R s_rin;  // one FP64 division per block
     __shared__ R s_c[9];
     if (threadIdx.x == 0) s_rin = (R)(1.0 / *d_norm);

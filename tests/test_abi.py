@@ -49,7 +49,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(_lib.dm_grid) == 16 + 48
     assert ctypes.sizeof(_lib.dm_psf) == 8 + 24 + 48 + 8
     assert ctypes.sizeof(_lib.dm_mesh) == 48
-    assert ctypes.sizeof(_lib.dm_options) == 16
+    assert ctypes.sizeof(_lib.dm_options) == 12
     assert ctypes.sizeof(_lib.dm_fit_options) == 8 + 40
     assert ctypes.sizeof(_lib.dm_stagger_options) == 24 + 56 + 8
     assert ctypes.sizeof(_lib.dm_stagger_stats) == 24

@@ -5,7 +5,9 @@ running (a server that reserved all of its memory at start-up, or a framework th
 owns every allocation): it takes no context and keeps its scratch in a fixed device
 array. Here it is called twice in a row through the C ABI, on two different meshes
 and frequency lists, and each result is compared with the context-based dm_meshft
-within the FP32 spectrum tolerance of the parity tests.
+within the FP32 spectrum tolerance of the parity tests, and the second with the FP64
+oracle. The first call is the warm-up (it loads the kernels' modules and looks up the
+scratch); the second must leave the device's free memory unchanged.
 """
 
 import ctypes
@@ -14,11 +16,13 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-6  # FP32 spectrum tolerance of tests/test_gpu_parity.py (relative L2)
+TOL_ORACLE = 1e-5  # FP32 spectrum against the FP64 oracle (tests/test_gpu_fullsize.py)
 
 
 def _mesh_struct(_lib, V, F):
@@ -53,25 +57,40 @@ def test_noalloc_matches_meshft_on_two_calls_in_a_row():
         synth.sh_deformed_sphere(2, 4.0, grid.center + 0.7, lmax=3, coef_sigma=0.3, seed=12),
     ]
     rng = np.random.default_rng(3)
+    # every device buffer of both calls exists before the first call, so that nothing but the library
+    # could take device memory between the two calls
+    bufs = []
     for k, (V, F) in enumerate(cases):
         M = 3000 + 517 * k  # ragged: not a multiple of the block size
         n = np.stack([rng.integers(-16, 16, M), rng.integers(-16, 16, M), rng.integers(0, 17, M)], axis=1)
         n[0] = 0
-        Vd = torch.as_tensor(V).to(dev)
-        Fd = torch.as_tensor(F).to(dev)
-        nd = torch.as_tensor(n.astype(np.int32)).to(dev)
-        S = torch.empty(M, dtype=torch.complex64, device=dev)
-        flags = torch.full((1,), -1, dtype=torch.int32, device=dev)
-        m = _mesh_struct(_lib, Vd, Fd)
-        g = _grid_struct(_lib, grid)
-        st = lib.dm_meshft_noalloc(ctypes.byref(m), ctypes.byref(g), nd.data_ptr(), M, S.data_ptr(),
-                                   flags.data_ptr(), torch.cuda.current_stream().cuda_stream)
-        assert st == _lib.DM_OK
-        ref = r.meshft(Vd, Fd, grid, nd)
+        bufs.append(dict(V=V, F=F, n=n.astype(np.int32), M=M, Vd=torch.as_tensor(V).to(dev),
+                         Fd=torch.as_tensor(F).to(dev), nd=torch.as_tensor(n.astype(np.int32)).to(dev),
+                         S=torch.empty(M, dtype=torch.complex64, device=dev),
+                         flags=torch.full((1,), -1, dtype=torch.int32, device=dev)))
+    g = _grid_struct(_lib, grid)
+    stream = torch.cuda.current_stream().cuda_stream
+    free = []
+    for k, b in enumerate(bufs):
+        m = _mesh_struct(_lib, b["Vd"], b["Fd"])
         torch.cuda.synchronize()
-        assert int(flags.item()) == 0
-        err = torch.linalg.norm(S - ref) / torch.linalg.norm(ref)
+        free.append(torch.cuda.mem_get_info(dev)[0])
+        st = lib.dm_meshft_noalloc(ctypes.byref(m), ctypes.byref(g), b["nd"].data_ptr(), b["M"], b["S"].data_ptr(),
+                                   b["flags"].data_ptr(), stream)
+        assert st == _lib.DM_OK
+        torch.cuda.synchronize()
+        free.append(torch.cuda.mem_get_info(dev)[0])
+        assert int(b["flags"].item()) == 0
+    # the second call (after the warm-up call) reserved no device memory
+    assert free[3] == free[2], free
+    for k, b in enumerate(bufs):
+        ref = r.meshft(b["Vd"], b["Fd"], grid, b["nd"])
+        err = torch.linalg.norm(b["S"] - ref) / torch.linalg.norm(ref)
         assert float(err) < TOL, (k, float(err))
+    b = bufs[1]
+    ref = oracle.mesh_ft(b["V"] - np.asarray(grid.origin), b["F"], oracle.wavevectors(b["n"], grid))
+    err = np.linalg.norm(b["S"].cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < TOL_ORACLE, err
     r.close()
 
 
