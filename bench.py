@@ -47,7 +47,10 @@ MUFU_PER_TERM = {"fwd": 7, "adj": 7}
 # ncu capture of `python bench.py --workload W --steps 1 --warmup 3 --no-cpu-baseline --no-e2e --no-serve
 # --no-fp64`, one kernel, one launch), keyed by workload and kernel, with the SHA-256 of the mesh-transform
 # sources it was taken on: a capture of other sources is not reported (the traffic is then null).
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("c3", "k_adj_f32"): {"bytes": 147.49e6 + 72.30e6, "sources": "f20a411847be84cc"},
+    ("c3", "k_fwd_f32"): {"bytes": 2.69e6 + 9.40e6, "sources": "f20a411847be84cc"},
+}
 TRAFFIC_SOURCES = ("meshft_f32.cu", "meshft_math.cuh", "dm_kernels.cuh", "dm_common.cuh")
 
 

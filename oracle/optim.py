@@ -127,8 +127,10 @@ def initial_cov(psf) -> tuple:
 def fit_staggered(V, F, grid, psf, target, rounds: int, shape_steps: int, psf_steps: int, lr_vertex: float,
                   lr_psf: float, lam: float = 50.0, optimizer: str = "large_steps", shape_loss: str = "weighted",
                   psf_loss: str = "l2", beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-20,
-                  mode: str = "surface", weights=None):
-    """The staggered fit. Returns (V, cov, shape_losses, psf_losses); each loss is taken before its step."""
+                  mode: str = "surface", weights=None, trace=None):
+    """The staggered fit. Returns (V, cov, shape_losses, psf_losses); each loss is taken before its step.
+    trace (optional list): receives, for every step, the state it started from and what it evaluated there:
+    dict(kind="shape" | "psf", V, cov, L, grad) with grad = dL/dV or dL/dcov."""
     V = np.array(V, dtype=np.float64)
     n_v = V.shape[0]
     c = cov_to_chol(initial_cov(psf))
@@ -144,6 +146,8 @@ def fit_staggered(V, F, grid, psf, target, rounds: int, shape_steps: int, psf_st
             L, dV, _, _ = _o.loss_and_grad(V, F, grid, _psf_full(chol_to_cov(c), tau), target, shape_loss, mode,
                                            weights=weights)
             hs.append(L)
+            if trace is not None:
+                trace.append(dict(kind="shape", V=V.copy(), cov=chol_to_cov(c), L=L, grad=dV.copy()))
             if optimizer == "large_steps":
                 gu = np.asarray(spla.spsolve(A, dV)).reshape(dV.shape)
                 d, mV, vV = adam_uniform(gu, mV, vV, ts, lr_vertex, beta1, beta2, eps)
@@ -156,6 +160,8 @@ def fit_staggered(V, F, grid, psf, target, rounds: int, shape_steps: int, psf_st
             L, _, dcov, _ = _o.loss_and_grad(V, F, grid, _psf_full(chol_to_cov(c), 0.0), target, psf_loss, mode,
                                              weights=weights)
             hp.append(L)
+            if trace is not None:
+                trace.append(dict(kind="psf", V=V.copy(), cov=chol_to_cov(c), L=L, grad=np.asarray(dcov).copy()))
             d, mC, vC = adam(chol_grad(c, dcov), mC, vC, tp, lr_psf, beta1, beta2, eps)
             c = c - d
     return V, chol_to_cov(c), np.array(hs), np.array(hp)

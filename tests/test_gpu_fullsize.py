@@ -118,7 +118,7 @@ def c3_fp64(renderers):
     img = render(V, sig, Fd, r64, case.grid)
     loss = ((img - T) ** 2).mean()
     loss.backward()
-    return dict(case=case, Fd=Fd, T=T, img=img.detach(), L=float(loss), gV=V.grad.detach().clone(),
+    return dict(case=case, Fd=Fd, T=T, img=img.detach(), L=float(loss.detach()), gV=V.grad.detach().clone(),
                 gs=sig.grad.detach().clone())
 
 
@@ -157,9 +157,11 @@ def test_c3_autograd_matches_central_differences(renderers, c3_fp64):
     triangles around it: S(V') = S(V) - S_star(V) + S_star(V') exactly (up to rounding), the area likewise.
     Directions 2..63 move one random vertex (and, in part, sigma) and are evaluated through that split:
     the FP64 spectrum of the whole mesh once, then the FP64 transforms of the vertex's few triangles,
-    the transfer function, the FP64 inverse DFT and the loss. Directions 0 and 1 move every vertex (the
-    second also sigma) and run through whole FP64 renders. The split is first checked against the
-    autograd forward's image."""
+    the transfer function, the FP64 inverse DFT and the loss. When only a vertex moves, L(+) - L(-) is
+    ~1/n_v of a dense direction's, so I(+) - I(-) is formed from the star's own differences (subtracting
+    two FP64 images of the whole mesh would leave ~1e-4 of it as rounding). Directions 0 and 1 move every
+    vertex (the second also sigma) and run through whole FP64 renders. The split is first checked against
+    the autograd forward's image."""
     from paper_2303_10440_b300 import PSF
 
     _, r64 = renderers
@@ -209,12 +211,21 @@ def test_c3_autograd_matches_central_differences(renderers, c3_fp64):
             Fs = _dev(star)
             S_rest = S_full - r64.meshft(_dev(V0), Fs, grid, fn)
             A_rest = A_full - float(_area(V0, star))
-            I = []
-            for sgn in (1.0, -1.0):
-                Vp = V0.copy()
-                Vp[v] += sgn * h * dv
-                Sp = S_rest + r64.meshft(_dev(Vp), Fs, grid, fn)
-                I.append(image(Sp, A_rest + float(_area(Vp, star)), sig0 + sgn * h * ds))
+            Vs = [V0.copy(), V0.copy()]
+            Vs[0][v] += h * dv
+            Vs[1][v] -= h * dv
+            Ss = [r64.meshft(_dev(x), Fs, grid, fn) for x in Vs]  # the star's spectra at V(+), V(-)
+            As = [float(_area(x, star)) for x in Vs]
+            I = [image(S_rest + Ss[0], A_rest + As[0], sig0 + h * ds), image(S_rest + Ss[1], A_rest + As[1], sig0 - h * ds)]
+            if not ds.any():
+                # one vertex moves: I(+) - I(-) from the star's own differences, without subtracting two images
+                # of the whole mesh: (S_rest + S+)/A+ - (S_rest + S-)/A- = [(S+ - S-) A- + (S_rest + S-)(A_s- - A_s+)]
+                # / (A+ A-), A+- = A_rest + A_s+-, then the same transfer function and inverse DFT (linear)
+                Ap, Am = A_rest + As[0], A_rest + As[1]
+                dX = ((Ss[0] - Ss[1]) * Am + (S_rest + Ss[1]) * (As[1] - As[0])) / (Ap * Am)
+                dI = image(dX, 1.0, sig0)
+                I = [I[0] + I[1] + dI, I[0] + I[1] - dI]  # (dL below uses only I(+) - I(-) and I(+) + I(-))
+                I = [0.5 * x for x in I]
             an = float(gV[v] @ dv + gs @ ds)
             scale = np.linalg.norm(gV[v]) * np.linalg.norm(dv) + np.linalg.norm(gs) * np.linalg.norm(ds)
         fd = dL(I[0], I[1]) / (2 * h)

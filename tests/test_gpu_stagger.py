@@ -126,23 +126,60 @@ def _tiny_case():
 
 
 @pytest.mark.parametrize("optimizer,lr_vertex", [("large_steps", 0.5), ("adam", 0.03)])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_fit_staggered_matches_oracle(optimizer, lr_vertex, prec, r64, r32):
+def test_fit_staggered_matches_oracle(optimizer, lr_vertex, r64):
+    """FP64 path: the whole staggered fit against the oracle's. The per-step gradients agree to ~1e-13; the
+    smoothing filter (1 + lambda L)^-2 can amplify a relative gradient error by up to its condition bound
+    kappa = 1 + 2 lambda (max degree) in the displacement, and Adam divides each coordinate by its own
+    moment, so a coordinate whose gradient is near zero carries a larger relative error: 1e-8 on the
+    displacement and 1e-9 on the covariance and losses leave room for both over 10 steps."""
     grid, V0, F, T = _tiny_case()
     psf0 = synth.Psf(sigma=(1.1, 1.1, 1.3), band_tau=1e-3)
     kw = dict(rounds=2, shape_steps=3, psf_steps=2, lr_vertex=lr_vertex, lr_psf=0.02, optimizer=optimizer)
     V1, cov1, hs1, hp1 = opt.fit_staggered(V0, F, grid, psf0, T, **kw)
-    r = r64 if prec == "fp64" else r32
-    V, psf, hs, hp, cg = r.fit_staggered(torch.as_tensor(V0).cuda(), torch.as_tensor(F).cuda(), grid, psf0,
-                                         torch.as_tensor(T).cuda(), **kw)
-    tv, tc, tl = (1e-8, 1e-9, 1e-9) if prec == "fp64" else (2e-2, 2e-3, 2e-3)
-    assert rel(V.cpu().numpy() - V0, V1 - V0) < tv
-    assert rel(psf.cov, cov1) < tc
-    assert rel(hs.numpy(), hs1) < tl and rel(hp.numpy(), hp1) < tl
+    V, psf, hs, hp, cg = r64.fit_staggered(torch.as_tensor(V0).cuda(), torch.as_tensor(F).cuda(), grid, psf0,
+                                           torch.as_tensor(T).cuda(), **kw)
+    assert rel(V.cpu().numpy() - V0, V1 - V0) < 1e-8
+    assert rel(psf.cov, cov1) < 1e-9
+    assert rel(hs.numpy(), hs1) < 1e-9 and rel(hp.numpy(), hp1) < 1e-9
     if optimizer == "large_steps":
         assert cg["iterations"] > 0 and cg["unconverged"] == 0
     else:
         assert cg["iterations"] == 0
+
+
+@pytest.mark.parametrize("optimizer,lr_vertex", [("large_steps", 0.5), ("adam", 0.03)])
+def test_fit_staggered_fp32_steps_match_oracle(optimizer, lr_vertex, r32):
+    """FP32 path: the parity unit is the step at identical inputs. FP32 and FP64 trajectories separate (Adam
+    divides each coordinate by its own moment, so gradient errors far inside the tolerance flip the steps of
+    coordinates whose gradient is near zero, and the fit amplifies the difference), so each state the oracle's
+    fit passes through is fed to the FP32 path, whose loss and gradient (dL/dV on the narrow band for shape
+    steps, dL/dcov on the whole half spectrum for PSF steps) must match the oracle's there within the path's
+    tolerances: 1e-4 on the loss (the image tolerance), 1e-3 on the gradients. The whole FP32 fit is run too,
+    and must match the oracle's first loss within 1e-4 and lower its PSF loss."""
+    from paper_2303_10440_b300 import PSF
+
+    grid, V0, F, T = _tiny_case()
+    psf0 = synth.Psf(sigma=(1.1, 1.1, 1.3), band_tau=1e-3)
+    kw = dict(rounds=2, shape_steps=3, psf_steps=2, lr_vertex=lr_vertex, lr_psf=0.02, optimizer=optimizer)
+    trace = []
+    opt.fit_staggered(V0, F, grid, psf0, T, trace=trace, **kw)
+    assert len(trace) == 10
+    Fd, Td = torch.as_tensor(F).cuda(), torch.as_tensor(T).cuda().float()
+    errs = []
+    for st in trace:
+        shape = st["kind"] == "shape"
+        psf = PSF(cov=tuple(st["cov"]), band_tau=psf0.band_tau if shape else 0.0)
+        L, dV, dcov, _ = r32.loss_and_grad(torch.as_tensor(st["V"]).cuda(), Fd, grid, psf, Td,
+                                           "weighted" if shape else "l2")
+        g = dV.cpu().numpy() if shape else dcov.numpy()
+        eL, eg = abs(L - st["L"]) / st["L"], rel(g, st["grad"])
+        errs.append((st["kind"], eL, eg))
+        assert eL < 1e-4 and eg < 1e-3, (st["kind"], eL, eg)
+    print(f"\n[FP32 staggered steps vs oracle, {optimizer}] worst loss {max(e[1] for e in errs):.2e}, "
+          f"worst gradient {max(e[2] for e in errs):.2e}")
+    V, psf, hs, hp, cg = r32.fit_staggered(torch.as_tensor(V0).cuda(), Fd, grid, psf0, Td, **kw)
+    assert abs(float(hs[0]) - trace[0]["L"]) < 1e-4 * trace[0]["L"]
+    assert float(hp[-1]) < float(hp[0])
 
 
 @pytest.mark.parametrize("variant", ["volume", "tissue_foam"])
