@@ -165,6 +165,67 @@ __host__ __device__ inline int fwd_splits(int64_t fb, int n_tiles, int target) {
 }
 constexpr int FWD_REC_TILE = 64;                  // triangle records per forward pipeline stage
 
+// ---------------------------------------------------------------- batched stages (fit server)
+// One served job's arguments for the stage kernels that the server runs for every job of an
+// iteration in one launch each (FP32 path). Each stage gives every job a block count fixed by the
+// job's own sizes (and the device), so a job's results do not depend on the other jobs of a launch.
+struct StageJob {
+    int mode, psf_kind, loss_kind;
+    int band;            // narrow band: the half spectrum is zeroed before the scatter
+    int64_t n_v, n_t, n_t_pad, N, nH, M_pad;
+    Geom g;
+    double* V;
+    const int32_t* F;
+    const float* wts;
+    TriF32* tris;
+    double* params;      // [0..8] psf, [16] normaliser, [17] loss, [24..31] gather sums
+    double* partial;     // per-block partial sums of the stage reductions
+    FreqSrc fs;
+    float2* S;
+    const float2* S_part;  // [fsplits][M] partial spectra when fsplits > 1
+    int fsplits;
+    int rc_slices;       // slices of the chunk reduction (> 1: second pass over red)
+    Cx<float>* spec;
+    float* image;
+    const float* target;
+    float* resid;
+    FreqPairF32* fr;
+    const float* adjp;
+    int n_chunks, nacc;
+    double* acc;
+    double* red;
+    double* contrib;
+    const int32_t* ptr;
+    const int32_t* ent;
+    double* dV;
+    int vertex_adam;     // Adam on the vertices in the batched update (large-steps jobs run their own)
+    double *mV, *vV, *ms, *vs, *hist;
+    int64_t* d_step;     // Adam step t of the job's next step
+    int64_t step0;
+    double lr_v, lr_psf, b1, b2, eps, decay;
+};
+
+// Batched stage ids: offsets[s * (nj + 1) + j] is the first block of job j in stage s's launch
+// (offsets[s * (nj + 1) + nj] = the launch's blocks).
+enum BatchStage {
+    BS_PREP, BS_FWDRED, BS_ZERO, BS_SCATTER, BS_LOSS, BS_GATHER, BS_REDUCE, BS_SLICES, BS_ASSEMBLE,
+    BS_VGATHER, BS_ADAM, BS_COUNT
+};
+// Per-job block counts of every batched stage (the single-job launches' counts for the same sizes).
+void batch_stage_blocks(const StageJob& J, int sm_count, int counts[BS_COUNT]);
+// Slices of the chunk reduction of a job (launch_reduce_chunks' choice with the scratch given).
+int reduce_slices_for(int64_t n_t, int nacc, int n_chunks, int sm_count);
+// One launch per stage over the nj jobs of `jobs` (device table); total = offsets[s*(nj+1) + nj].
+cudaError_t launch_batch_stage(int stage, const StageJob* jobs, const int* offsets, int nj, int total, int* d_err,
+                               cudaStream_t st);
+// Sums of the per-block partials of a stage into params: params[dst + k] = sum over the job's blocks b
+// of partial[b * count + k], k < count (one block per (job, k)); flag_err: ERR_DEGENERATE when not > 0.
+cudaError_t launch_batch_sum(const StageJob* jobs, const int* stage_offsets, int nj, int count, int dst, int* flag_err,
+                             cudaStream_t st);
+// End of a step for every job: Adam on sigma (lr_psf > 0) with the step t, hist[t - step0 - 1] = loss,
+// losses[j] = loss, t += 1.
+cudaError_t launch_batch_tick(const StageJob* jobs, int nj, double* losses, cudaStream_t st);
+
 // Mesh transform (FP64 plain path).
 cudaError_t launch_fwd_f64(int mode, const TriF64* tris, int64_t n_t, const FreqSrc& fs, const Geom& g,
                            const double* d_vol, double2* S, cudaStream_t st);
@@ -278,6 +339,22 @@ template <class R>
 cudaError_t launch_r2c(const R* in, Cx<R>* spec_out, int Nx, int Ny, int Nz, const FFTAxis* ax, cudaStream_t st);
 bool fft_factor(int N, FFTAxis& a);
 size_t fft_smem_bytes(int N, int elem_bytes);
+
+// Batched FFT passes over the jobs of one line length: complex strided passes, or the real z passes.
+struct FFTJob {
+    const void* src;
+    void* dst;
+    FFTAxis ax;
+    int64_t inner;  // strided: element stride of the lines; z passes: 0
+    int64_t lines;  // strided: number of outer blocks of lines (the single-job pass's `outer`); z: lines
+    int Nzh;
+};
+enum FFTPassKind { FFT_STRIDED = 0, FFT_Z_C2R = 1, FFT_Z_R2C = 2 };
+// Blocks one job takes in a batched pass (the single-job pass's grid).
+int64_t fft_pass_blocks(int kind, const FFTJob& j);
+cudaError_t launch_fft_batch(int kind, int N, const FFTJob* jobs, const int* offsets, int nj, int total, int dir,
+                             cudaStream_t st);
+
 
 // Small helpers.
 struct Params16 {

@@ -182,8 +182,8 @@ __device__ __forceinline__ Cx<R>* transform_lines(Cx<R>* a, Cx<R>* b, const FFTA
 // Complex transform of all lines along an axis with element stride `inner`:
 // element (o, k, c) at o*N*inner + k*inner + c, lines indexed by (o, c).
 template <class R, int NC>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const FFTAxis ax, int64_t inner,
-                                                             int dir) {
+__device__ __forceinline__ void k_fft_strided_body(Cx<R>* data, const FFTAxis ax, int64_t inner,
+                                                             int dir, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NC ? NC : ax.N;
     const int nl = lines_per_block(N);
@@ -191,8 +191,8 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const 
     Cx<R>* a = (Cx<R>*)smem_raw;
     Cx<R>* b = a + N * LS;
     const int64_t col_blocks = (inner + nl - 1) / nl;
-    const int64_t o = blockIdx.x / col_blocks;
-    const int64_t c0 = (blockIdx.x % col_blocks) * nl;
+    const int64_t o = blk / col_blocks;
+    const int64_t c0 = (blk % col_blocks) * nl;
     const int ncols = (int)min((int64_t)nl, inner - c0);
     Cx<R>* base = data + o * N * inner + c0;
     for (int i = threadIdx.x; i < N * nl; i += blockDim.x) {
@@ -206,11 +206,16 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const 
         if (c < ncols) base[(int64_t)k * inner + c] = res[k * LS + c];
     }
 }
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const FFTAxis ax, int64_t inner,
+                                                             int dir) {
+    k_fft_strided_body<R, NC>(data, ax, inner, dir, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
 
 // Inverse z pass: lines of Nzh complex (contiguous) -> Nz reals (contiguous).
 template <class R, int NC>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R* out, const FFTAxis ax, int Nzh_,
-                                                           int64_t nlines) {
+__device__ __forceinline__ void k_fft_z_c2r_body(const Cx<R>* spec, R* out, const FFTAxis ax, int Nzh_,
+                                                           int64_t nlines, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NC ? NC : ax.N;
     const int Nzh = NC ? NC / 2 + 1 : Nzh_;
@@ -218,7 +223,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R*
     const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
     Cx<R>* b = a + N * LS;
-    const int64_t l0 = (int64_t)blockIdx.x * nl;
+    const int64_t l0 = blk * nl;
     const int nv = (int)min((int64_t)nl, nlines - l0);
     for (int i = threadIdx.x; i < Nzh * nl; i += blockDim.x) {
         const int k = i % Nzh, c = i / Nzh;
@@ -235,11 +240,16 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R*
         if (c < nv) out[(l0 + c) * N + k] = res[k * LS + c].x;
     }
 }
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_c2r(const Cx<R>* spec, R* out, const FFTAxis ax, int Nzh_,
+                                                           int64_t nlines) {
+    k_fft_z_c2r_body<R, NC>(spec, out, ax, Nzh_, nlines, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
 
 // Forward z pass: lines of Nz reals -> first Nzh complex outputs.
 template <class R, int NC>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* spec, const FFTAxis ax, int Nzh_,
-                                                           int64_t nlines) {
+__device__ __forceinline__ void k_fft_z_r2c_body(const R* in, Cx<R>* spec, const FFTAxis ax, int Nzh_,
+                                                           int64_t nlines, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NC ? NC : ax.N;
     const int Nzh = NC ? NC / 2 + 1 : Nzh_;
@@ -247,7 +257,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* s
     const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
     Cx<R>* b = a + N * LS;
-    const int64_t l0 = (int64_t)blockIdx.x * nl;
+    const int64_t l0 = blk * nl;
     const int nv = (int)min((int64_t)nl, nlines - l0);
     for (int i = threadIdx.x; i < N * nl; i += blockDim.x) {
         const int k = i % N, c = i / N;
@@ -259,6 +269,51 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* s
         const int k = i % Nzh, c = i / Nzh;
         if (c < nv) spec[(l0 + c) * Nzh + k] = res[k * LS + c];
     }
+}
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* spec, const FFTAxis ax, int Nzh_,
+                                                           int64_t nlines) {
+    k_fft_z_r2c_body<R, NC>(in, spec, ax, Nzh_, nlines, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
+
+// Batched passes (fit server): the jobs of one line length in one launch; block b belongs to the
+// largest job j with offs[j] <= b, as its block b - offs[j] of its single-job grid.
+struct FFTBlock {
+    int j;
+    int64_t b, nb;
+};
+__device__ __forceinline__ FFTBlock fft_block(const int* __restrict__ offs, int nj) {
+    const int bi = (int)blockIdx.x;
+    int lo = 0, hi = nj;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (offs[mid] <= bi)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return {lo, (int64_t)(bi - offs[lo]), (int64_t)(offs[lo + 1] - offs[lo])};
+}
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) kb_fft_strided(const FFTJob* __restrict__ jobs,
+                                                              const int* __restrict__ offs, int nj, int dir) {
+    const FFTBlock q = fft_block(offs, nj);
+    const FFTJob& J = jobs[q.j];
+    k_fft_strided_body<R, NC>((Cx<R>*)J.dst, J.ax, J.inner, dir, q.b, q.nb);
+}
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) kb_fft_z_c2r(const FFTJob* __restrict__ jobs,
+                                                            const int* __restrict__ offs, int nj) {
+    const FFTBlock q = fft_block(offs, nj);
+    const FFTJob& J = jobs[q.j];
+    k_fft_z_c2r_body<R, NC>((const Cx<R>*)J.src, (R*)J.dst, J.ax, J.Nzh, J.lines, q.b, q.nb);
+}
+template <class R, int NC>
+__global__ void __launch_bounds__(FFT_THREADS) kb_fft_z_r2c(const FFTJob* __restrict__ jobs,
+                                                            const int* __restrict__ offs, int nj) {
+    const FFTBlock q = fft_block(offs, nj);
+    const FFTJob& J = jobs[q.j];
+    k_fft_z_r2c_body<R, NC>((const R*)J.src, (Cx<R>*)J.dst, J.ax, J.Nzh, J.lines, q.b, q.nb);
 }
 
 // Raises kernel FN's dynamic shared-memory limit to the device's opt-in maximum, once per device,
@@ -338,6 +393,45 @@ cudaError_t pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, i
         case 512: return run_pass<R, 512>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         case 1024: return run_pass<R, 1024>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         default: return run_pass<R, 0>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+    }
+}
+
+template <int NC>
+cudaError_t run_batch_pass(int kind, const FFTJob* jobs, const int* offs, int nj, int total, int N, int dir,
+                           cudaStream_t st) {
+    const size_t sm = fft_smem_bytes(N, sizeof(Cx<float>));
+    cudaError_t e;
+    if (kind == FFT_STRIDED) {
+        if ((e = set_smem<kb_fft_strided<float, NC>>(sm)) != cudaSuccess) return e;
+        kb_fft_strided<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj, dir);
+    } else if (kind == FFT_Z_C2R) {
+        if ((e = set_smem<kb_fft_z_c2r<float, NC>>(sm)) != cudaSuccess) return e;
+        kb_fft_z_c2r<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj);
+    } else {
+        if ((e = set_smem<kb_fft_z_r2c<float, NC>>(sm)) != cudaSuccess) return e;
+        kb_fft_z_r2c<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj);
+    }
+    return cudaGetLastError();
+}
+
+int64_t fft_pass_blocks(int kind, const FFTJob& j) {
+    const int nl = lines_per_block(j.ax.N);
+    if (kind == FFT_STRIDED) return j.lines * ((j.inner + nl - 1) / nl);  // lines: the outer count
+    return (j.lines + nl - 1) / nl;
+}
+
+cudaError_t launch_fft_batch(int kind, int N, const FFTJob* jobs, const int* offsets, int nj, int total, int dir,
+                             cudaStream_t st) {
+    if (total <= 0 || nj <= 0) return cudaSuccess;
+    switch (N) {
+        case 16: return run_batch_pass<16>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 32: return run_batch_pass<32>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 64: return run_batch_pass<64>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 128: return run_batch_pass<128>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 256: return run_batch_pass<256>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 512: return run_batch_pass<512>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 1024: return run_batch_pass<1024>(kind, jobs, offsets, nj, total, N, dir, st);
+        default: return run_batch_pass<0>(kind, jobs, offsets, nj, total, N, dir, st);
     }
 }
 

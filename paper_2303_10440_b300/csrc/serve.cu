@@ -203,6 +203,22 @@ struct dm_server {
     size_t cap_fj = 0, cap_aj = 0, cap_uf = 0, cap_ua = 0;
     int* d_counter = nullptr;
     double* h_loss = nullptr;  // pinned, one per batch slot
+    double* d_losses = nullptr;  // device, one per batch slot (written by the batched tick)
+    // batched stage launches: the job table, per-stage block offsets, FFT pass groups
+    std::vector<StageJob> sj;
+    std::vector<int> offs;  // [BS_COUNT][nj + 1]
+    int totals[BS_COUNT] = {0};
+    struct FFTGroup {
+        int kind, N, dir, nj, total;
+        size_t jobs_at, offs_at;  // into fftj / fft_offs
+    };
+    std::vector<FFTGroup> c2r_groups, r2c_groups;  // in launch order (x, y, z passes; z, y, x passes)
+    std::vector<FFTJob> fftj;
+    std::vector<int> fft_offs;
+    StageJob* d_sj = nullptr;
+    int *d_offs = nullptr, *d_fft_offs = nullptr;
+    FFTJob* d_fftj = nullptr;
+    size_t cap_sj = 0, cap_offs = 0, cap_fftj = 0, cap_fft_offs = 0;
     int grid_fwd[2] = {0, 0}, grid_adj[2] = {0, 0};  // persistent grid per label
     std::vector<std::pair<cudaStream_t, cudaEvent_t>> free_streams;  // job streams not in use
     cudaEvent_t ev_fwd = nullptr, ev_adj = nullptr;                  // after each batched launch
@@ -301,6 +317,13 @@ bool setup_job(dm_server* S, SJob* J) {
                  cudaMemcpyAsync(J->wv, J->r_warm.data() + 3 * z.n_v, 3 * z.n_v * sizeof(double),
                                  cudaMemcpyHostToDevice, st) == cudaSuccess;
     }
+    // the band of a job that keeps its PSF is the same at every step: computed once here (a job that
+    // learns sigma recomputes it every step)
+    if (ok && z.band && J->fit.lr_psf <= 0) {
+        ok = launch_band(b.d_params, J->psf.kind, J->psf.band_tau, J->grid.n[0], J->grid.n[1], J->grid.n[2],
+                         make_geom(&J->grid), b.band_idx, b.dM, b.band_counts, st) == cudaSuccess;
+        g_launches += 3;
+    }
     if (ok && J->has_resume) {
         const int64_t nV = 3 * z.n_v;
         ok = cudaMemcpyAsync(J->mV, J->r_mV.data(), nV * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess &&
@@ -318,6 +341,134 @@ bool setup_job(dm_server* S, SJob* J) {
         return false;
     }
     return true;
+}
+
+// The batched stage launches of the jobs in S->run: one StageJob per job (index as in S->run), the
+// per-stage block offsets, and the FFT passes grouped by line length.
+void build_stage_tables(dm_server* S) {
+    const int nj = (int)S->run.size();
+    const int sms = S->ctx->sm_count;
+    S->sj.resize(nj);
+    for (int j = 0; j < nj; ++j) {
+        const SJob* J = S->run[j];
+        const Sizes& z = J->z;
+        const Bufs& b = J->b;
+        StageJob& q = S->sj[j];
+        memset(&q, 0, sizeof(q));
+        q.mode = J->label;
+        q.psf_kind = J->psf.kind;
+        q.loss_kind = J->fit.loss;
+        q.band = z.band ? 1 : 0;
+        q.n_v = z.n_v;
+        q.n_t = z.n_t;
+        q.n_t_pad = z.n_t_pad;
+        q.N = z.N;
+        q.nH = z.nH;
+        q.M_pad = z.M_pad;
+        q.g = make_geom(&J->grid);
+        q.V = b.V;
+        q.F = b.F;
+        q.wts = b.wts;
+        q.tris = (TriF32*)b.tris;
+        q.params = b.d_params;
+        q.partial = b.partial;
+        q.fs = S->fj[j].fs;
+        q.S = (float2*)b.S;
+        q.S_part = J->S_part;
+        q.fsplits = J->fsplits;
+        q.rc_slices = reduce_slices_for(z.n_t, z.nacc, z.n_chunks, sms);
+        q.spec = (Cx<float>*)b.spec;
+        q.image = (float*)b.image;
+        q.target = (const float*)b.target;
+        q.resid = (float*)b.resid;
+        q.fr = (FreqPairF32*)b.fr;
+        q.adjp = (const float*)b.adjp;
+        q.n_chunks = z.n_chunks;
+        q.nacc = z.nacc;
+        q.acc = b.acc;
+        q.red = b.red;
+        q.contrib = b.contrib;
+        q.ptr = b.ptr;
+        q.ent = b.ent;
+        q.dV = b.dV;
+        q.vertex_adam = J->optimizer == DM_OPT_ADAM ? 1 : 0;
+        q.mV = J->mV;
+        q.vV = J->vV;
+        q.ms = J->ms;
+        q.vs = J->vs;
+        q.hist = J->hist;
+        q.d_step = J->d_step;
+        q.step0 = J->step0;
+        q.lr_v = J->fit.lr_vertex;
+        q.lr_psf = J->fit.lr_psf;
+        q.b1 = J->fit.beta1;
+        q.b2 = J->fit.beta2;
+        q.eps = J->fit.eps;
+        q.decay = J->lr_decay;
+    }
+    S->offs.assign((size_t)BS_COUNT * (nj + 1), 0);
+    for (int j = 0; j < nj; ++j) {
+        int c[BS_COUNT];
+        batch_stage_blocks(S->sj[j], sms, c);
+        for (int st = 0; st < BS_COUNT; ++st) {
+            int* o = S->offs.data() + (size_t)st * (nj + 1);
+            o[j + 1] = o[j] + c[st];
+        }
+    }
+    for (int st = 0; st < BS_COUNT; ++st) S->totals[st] = S->offs[(size_t)st * (nj + 1) + nj];
+    // FFT passes: inverse x, y, z (complex, complex, complex-to-real), forward z, y, x; each pass grouped
+    // by line length (one launch per length)
+    S->fftj.clear();
+    S->fft_offs.clear();
+    S->c2r_groups.clear();
+    S->r2c_groups.clear();
+    const auto add_pass = [&](std::vector<dm_server::FFTGroup>& out, int kind, int dir, int axis) {
+        std::map<int, std::vector<FFTJob>> by_n;
+        for (int j = 0; j < nj; ++j) {
+            const SJob* J = S->run[j];
+            const int* n = J->grid.n;
+            if (kind == FFT_STRIDED && n[axis] <= 1) continue;  // a length-1 axis needs no pass
+            const int Nzh = n[2] / 2 + 1;
+            FFTJob f;
+            f.ax = J->ax[axis];
+            f.Nzh = Nzh;
+            if (kind == FFT_STRIDED) {
+                f.src = f.dst = J->b.spec;
+                f.inner = axis == 0 ? (int64_t)n[1] * Nzh : Nzh;
+                f.lines = axis == 0 ? 1 : n[0];
+            } else {
+                f.src = kind == FFT_Z_C2R ? J->b.spec : J->b.resid;
+                f.dst = kind == FFT_Z_C2R ? J->b.image : J->b.spec;
+                f.inner = 0;
+                f.lines = (int64_t)n[0] * n[1];
+            }
+            by_n[f.ax.N].push_back(f);
+        }
+        for (auto& kv : by_n) {
+            dm_server::FFTGroup g;
+            g.kind = kind;
+            g.N = kv.first;
+            g.dir = dir;
+            g.nj = (int)kv.second.size();
+            g.jobs_at = S->fftj.size();
+            g.offs_at = S->fft_offs.size();
+            int total = 0;
+            S->fft_offs.push_back(0);
+            for (const FFTJob& f : kv.second) {
+                S->fftj.push_back(f);
+                total += (int)fft_pass_blocks(kind, f);
+                S->fft_offs.push_back(total);
+            }
+            g.total = total;
+            out.push_back(g);
+        }
+    };
+    add_pass(S->c2r_groups, FFT_STRIDED, +1, 0);
+    add_pass(S->c2r_groups, FFT_STRIDED, +1, 1);
+    add_pass(S->c2r_groups, FFT_Z_C2R, +1, 2);
+    add_pass(S->r2c_groups, FFT_Z_R2C, -1, 2);
+    add_pass(S->r2c_groups, FFT_STRIDED, -1, 1);
+    add_pass(S->r2c_groups, FFT_STRIDED, -1, 0);
 }
 
 bool rebuild_units(dm_server* S) {
@@ -379,10 +530,15 @@ bool rebuild_units(dm_server* S) {
             for (int64_t t = 0; t < tb; ++t) S->ua.push_back({j, (int)t, c, 0});
         if (S->run[j]->label == DM_SURFACE) S->na_surf = S->ua.size();
     }
+    build_stage_tables(S);
     bool ok = grow((void**)&S->d_fj, &S->cap_fj, nj, sizeof(BatchFwdJob)) &&
               grow((void**)&S->d_aj, &S->cap_aj, nj, sizeof(BatchAdjJob)) &&
               grow((void**)&S->d_uf, &S->cap_uf, S->uf.size(), sizeof(BatchUnit)) &&
-              grow((void**)&S->d_ua, &S->cap_ua, S->ua.size(), sizeof(BatchUnit));
+              grow((void**)&S->d_ua, &S->cap_ua, S->ua.size(), sizeof(BatchUnit)) &&
+              grow((void**)&S->d_sj, &S->cap_sj, nj, sizeof(StageJob)) &&
+              grow((void**)&S->d_offs, &S->cap_offs, S->offs.size(), sizeof(int)) &&
+              grow((void**)&S->d_fftj, &S->cap_fftj, std::max<size_t>(1, S->fftj.size()), sizeof(FFTJob)) &&
+              grow((void**)&S->d_fft_offs, &S->cap_fft_offs, std::max<size_t>(1, S->fft_offs.size()), sizeof(int));
     // the tables change only with the set of jobs advanced, so they are uploaded here (stream-ordered
     // after the previous iteration's batched launches) and not every iteration
     cudaStream_t st = S->st;
@@ -392,49 +548,57 @@ bool rebuild_units(dm_server* S) {
                    cudaSuccess;
     ok = ok && cudaMemcpyAsync(S->d_ua, S->ua.data(), S->ua.size() * sizeof(BatchUnit), cudaMemcpyHostToDevice, st) ==
                    cudaSuccess;
+    ok = ok && cudaMemcpyAsync(S->d_sj, S->sj.data(), nj * sizeof(StageJob), cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(S->d_offs, S->offs.data(), S->offs.size() * sizeof(int), cudaMemcpyHostToDevice, st) ==
+                   cudaSuccess;
+    ok = ok && (S->fftj.empty() || cudaMemcpyAsync(S->d_fftj, S->fftj.data(), S->fftj.size() * sizeof(FFTJob),
+                                                   cudaMemcpyHostToDevice, st) == cudaSuccess);
+    ok = ok && (S->fft_offs.empty() || cudaMemcpyAsync(S->d_fft_offs, S->fft_offs.data(),
+                                                       S->fft_offs.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                                       st) == cudaSuccess);
     S->dirty = !ok;
     return ok;
 }
 
-// Enqueue one Adam step of every job in S->run on the server stream: each job's own stage kernels on
-// its stream (forked from the server stream at the start, joined back at the end), the batched
-// launches on the server stream after every job's preceding stage (events). Every value that changes
-// from step to step lives on the device (the Adam step counter), so the same sequence can be captured
-// once and replayed. Adds the kernels it launches to *nl; false if an enqueue failed.
+// Enqueue one optimiser step of every job in S->run on the server stream: each stage of the step is one
+// launch over all jobs (job table, per-job block counts fixed by each job's own sizes), the two
+// mesh-transform sums are the persistent batched launches, and only a large-steps job's smoothing
+// solves and uniform-Adam step run as launches of their own. Every value that changes from step to
+// step lives on the device (the Adam step counters), so the same sequence can be captured once and
+// replayed. Adds the kernels it launches to *nl_out; false if an enqueue failed.
 bool enqueue_step(dm_server* S, int64_t* nl_out) {
     dm_ctx* ctx = S->ctx;
     cudaStream_t st = S->st;
-    const size_t nj = S->run.size();
-    // one job: its stage kernels go on the server stream and no events are needed between them
-    const bool single = nj == 1;
+    const int nj = (int)S->run.size();
     bool ok = true;
     int64_t nlk = 0;
-    if (!single) {
-        ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
-        for (SJob* J : S->run) ok &= cudaStreamWaitEvent(J->stream, S->ev_fwd, 0) == cudaSuccess;
-    }
-    // triangle records, normalisers, bands
+    const auto stage = [&](int s) {
+        if (S->totals[s] <= 0) return;
+        ok &= launch_batch_stage(s, S->d_sj, S->d_offs, nj, S->totals[s], ctx->d_err, st) == cudaSuccess;
+        nlk += 1;
+    };
+    const auto stage_sum = [&](int s, int count, int dst) {
+        ok &= launch_batch_sum(S->d_sj, S->d_offs + (size_t)s * (nj + 1), nj, count, dst, nullptr, st) == cudaSuccess;
+        nlk += 1;
+    };
+    const auto fft = [&](const std::vector<dm_server::FFTGroup>& groups) {
+        for (const auto& g : groups) {
+            ok &= launch_fft_batch(g.kind, g.N, S->d_fftj + g.jobs_at, S->d_fft_offs + g.offs_at, g.nj, g.total, g.dir,
+                                   st) == cudaSuccess;
+            nlk += 1;
+        }
+    };
+    // triangle records and normalisers; the bands of jobs that learn sigma
+    stage(BS_PREP);
+    stage_sum(BS_PREP, 1, 16);
     for (SJob* J : S->run) {
-        cudaStream_t js = single ? st : J->stream;
-        const Geom G = make_geom(&J->grid);
-        const Bufs& b = J->b;
-        int nb = 0;
-        ok &= launch_tri_prep<TriF32>(J->label, b.V, J->z.n_v, b.F, J->z.n_t, b.wts, G, (TriF32*)b.tris,
-                                      J->z.n_t_pad, b.partial, &nb, ctx->d_err, js) == cudaSuccess;
-        ok &= launch_sum(b.partial, nb, 1, 1, b.d_params + 16, js) == cudaSuccess;
-        nlk += 2;
-        if (J->z.band) {
-            ok &= launch_band(b.d_params, J->psf.kind, J->psf.band_tau, J->grid.n[0], J->grid.n[1], J->grid.n[2], G,
-                              b.band_idx, b.dM, b.band_counts, js) == cudaSuccess;
-            nlk += 3;
-        }
-        if (!single) {
-            ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
-            ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
-        }
+        if (!J->z.band || J->fit.lr_psf <= 0) continue;
+        ok &= launch_band(J->b.d_params, J->psf.kind, J->psf.band_tau, J->grid.n[0], J->grid.n[1], J->grid.n[2],
+                          make_geom(&J->grid), J->b.band_idx, J->b.dM, J->b.band_counts, st) == cudaSuccess;
+        nlk += 3;
     }
-    // persistent grids no larger than the unit lists (a small batch launches no idle blocks); one
-    // launch per label present, surface units first
+    // mesh-transform sums: one persistent launch per label present, surface units first (grids no
+    // larger than the unit lists, so a small batch launches no idle blocks)
     const size_t nfl[2] = {S->nf_surf, S->uf.size() - S->nf_surf};
     const size_t nal[2] = {S->na_surf, S->ua.size() - S->na_surf};
     for (int m = 0; m < 2; ++m) {
@@ -444,42 +608,16 @@ bool enqueue_step(dm_server* S, int64_t* nl_out) {
                                    ctx->d_err, st) == cudaSuccess;
         nlk += 1;
     }
-    ok &= cudaEventRecord(S->ev_fwd, st) == cudaSuccess;
+    stage(BS_FWDRED);
     // image, loss, adjoint records
-    for (SJob* J : S->run) {
-        cudaStream_t js = single ? st : J->stream;
-        if (!single) ok &= cudaStreamWaitEvent(js, S->ev_fwd, 0) == cudaSuccess;
-        const Geom G = make_geom(&J->grid);
-        const Bufs& b = J->b;
-        const Sizes& z = J->z;
-        FreqSrc fs;
-        fs.nlist = nullptr;
-        fs.idx = z.band ? b.band_idx : nullptr;
-        fs.dM = z.band ? b.dM : nullptr;
-        fs.M = z.nH;
-        fs.set_dims(J->grid.n[0], J->grid.n[1], J->grid.n[2]);
-        const int* n = J->grid.n;
-        int nl = 0, ng = 0;
-        ok &= launch_fwd_reduce_splits(fs, J->fsplits, J->S_part, (float2*)b.S, ctx->sm_count, js) == cudaSuccess;
-        if (J->fsplits > 1) nlk += 1;
-        ok &= launch_scatter<float>((const Cx<float>*)b.S, fs, b.d_params, J->psf.kind, b.d_params + 16, G,
-                                    (Cx<float>*)b.spec, z.band, js) == cudaSuccess;
-        ok &= launch_c2r<float>((const Cx<float>*)b.spec, (Cx<float>*)b.spec, (float*)b.image, n[0], n[1], n[2], J->ax,
-                                js) == cudaSuccess;
-        ok &= launch_loss<float>((const float*)b.image, (const float*)b.target, z.N, J->fit.loss, (float*)b.resid,
-                                 b.partial, &nl, js) == cudaSuccess;
-        ok &= launch_sum(b.partial, nl, 1, 1, b.d_params + 17, js) == cudaSuccess;
-        ok &= launch_r2c<float>((const float*)b.resid, (Cx<float>*)b.spec, n[0], n[1], n[2], J->ax, js) == cudaSuccess;
-        ok &= launch_gather<float, FreqF32>(J->label, (const Cx<float>*)b.spec, (const Cx<float>*)b.S, fs, b.d_params,
-                                            J->psf.kind, b.d_params + 16, G, (FreqF32*)b.fr, z.M_pad, b.partial, &ng,
-                                            js) == cudaSuccess;
-        ok &= launch_sum(b.partial, ng, 8, 8, b.d_params + 24, js) == cudaSuccess;
-        nlk += 12;
-        if (!single) {
-            ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
-            ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
-        }
-    }
+    stage(BS_ZERO);
+    stage(BS_SCATTER);
+    fft(S->c2r_groups);
+    stage(BS_LOSS);
+    stage_sum(BS_LOSS, 1, 17);
+    fft(S->r2c_groups);
+    stage(BS_GATHER);
+    stage_sum(BS_GATHER, 8, 24);
     for (int m = 0; m < 2; ++m) {
         if (nal[m] == 0) continue;
         const int ga = (int)std::min<size_t>((size_t)S->grid_adj[m], nal[m]);
@@ -487,53 +625,29 @@ bool enqueue_step(dm_server* S, int64_t* nl_out) {
                                    ctx->d_err, st) == cudaSuccess;
         nlk += 1;
     }
-    ok &= cudaEventRecord(S->ev_adj, st) == cudaSuccess;
-    // per-vertex gradients and Adam
-    for (size_t j = 0; j < nj; ++j) {
-        SJob* J = S->run[j];
-        cudaStream_t js = single ? st : J->stream;
-        if (!single) ok &= cudaStreamWaitEvent(js, S->ev_adj, 0) == cudaSuccess;
-        const Geom G = make_geom(&J->grid);
-        const Bufs& b = J->b;
-        const Sizes& z = J->z;
-        ok &= launch_reduce_chunks<float>((const float*)b.adjp, z.n_chunks, z.nacc, z.n_t, z.n_t_pad, b.acc, js,
-                                          nullptr, -1, b.red, ctx->sm_count) ==
-              cudaSuccess;
-        ok &= launch_assemble(J->label, b.V, b.F, z.n_t, z.n_v, b.wts, G, b.acc, b.d_params + 30, b.contrib, js) ==
-              cudaSuccess;
-        ok &= launch_vertex_gather(b.ptr, b.ent, b.contrib, z.n_v, b.dV, js) == cudaSuccess;
-        ok &= cudaMemcpyAsync(S->h_loss + j, b.d_params + 17, sizeof(double), cudaMemcpyDeviceToHost, js) ==
-              cudaSuccess;
-        // Adam step t = *J->d_step (bias correction and the rate lr lr_decay^(t-1)); the tick then
-        // stores the step's loss at hist[t - step0 - 1] and advances t
+    // per-vertex gradients and the update
+    stage(BS_REDUCE);
+    stage(BS_SLICES);
+    stage(BS_ASSEMBLE);
+    stage(BS_VGATHER);
+    stage(BS_ADAM);
+    for (SJob* J : S->run) {
+        if (J->optimizer != DM_OPT_LARGE_STEPS) continue;
+        // v -= (1 + lambda L)^-1 AdamUniform((1 + lambda L)^-1 dL/dv), step t = *J->d_step
         const dm_fit_options& o = J->fit;
-        if (J->optimizer == DM_OPT_LARGE_STEPS) {
-            // v -= (1 + lambda L)^-1 AdamUniform((1 + lambda L)^-1 dL/dv)
-            ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, b.dV, J->gu, nullptr, J->pcg_work, 1e-6, 2000,
-                                    J->cg_stats, js) == cudaSuccess;
-            ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps, 0,
-                                      J->aup, js, J->d_step, J->lr_decay) == cudaSuccess;
-            ok &= launch_pcg<float>(J->lptr, J->lcol, z.n_v, J->lambda, J->dl, J->wv, b.V, J->pcg_work, 1e-6, 2000,
-                                    J->cg_stats, js) == cudaSuccess;
-            nlk += 7;
-        } else {
-            ok &= launch_adam_dev_step(b.V, b.dV, J->mV, J->vV, 3 * z.n_v, o.lr_vertex, o.beta1, o.beta2, o.eps,
-                                       J->d_step, J->lr_decay, js) == cudaSuccess;
-            nlk += 4;
-        }
-        if (o.lr_psf > 0) {
-            ok &= launch_adam_dev_step(b.d_params, b.d_params + 24, J->ms, J->vs, 3, o.lr_psf, o.beta1, o.beta2, o.eps,
-                                       J->d_step, J->lr_decay, js) == cudaSuccess;
-            nlk += 1;
-        }
-        ok &= launch_fit_tick(J->hist, b.d_params + 17, J->d_step, J->step0, js) == cudaSuccess;
-        nlk += 1;
-        // the next iteration's batched launches on the server stream also follow this job's Adam
-        if (!single) {
-            ok &= cudaEventRecord(J->ev, js) == cudaSuccess;
-            ok &= cudaStreamWaitEvent(st, J->ev, 0) == cudaSuccess;
-        }
+        const int64_t n_v = J->z.n_v;
+        ok &= launch_pcg<float>(J->lptr, J->lcol, n_v, J->lambda, J->b.dV, J->gu, nullptr, J->pcg_work, 1e-6, 2000,
+                                J->cg_stats, st) == cudaSuccess;
+        ok &= launch_adam_uniform(J->gu, J->mV, J->vV, J->dl, 3 * n_v, o.lr_vertex, o.beta1, o.beta2, o.eps, 0, J->aup,
+                                  st, J->d_step, J->lr_decay) == cudaSuccess;
+        ok &= launch_pcg<float>(J->lptr, J->lcol, n_v, J->lambda, J->dl, J->wv, J->b.V, J->pcg_work, 1e-6, 2000,
+                                J->cg_stats, st) == cudaSuccess;
+        nlk += 4;
     }
+    // sigma (lr_psf > 0), the loss history and the step counters; the losses to the host
+    ok &= launch_batch_tick(S->d_sj, nj, S->d_losses, st) == cudaSuccess;
+    ok &= cudaMemcpyAsync(S->h_loss, S->d_losses, nj * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    nlk += 1;
     *nl_out += nlk;
     return ok;
 }
@@ -890,6 +1004,7 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
     bool ok = S->arena.init(bytes) && cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) == cudaSuccess &&
               cudaMalloc(&S->d_counter, sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&S->h_loss, sizeof(double) * (size_t)S->max_jobs) == cudaSuccess &&
+              cudaMalloc(&S->d_losses, sizeof(double) * (size_t)S->max_jobs) == cudaSuccess &&
               cudaEventCreateWithFlags(&S->ev_fwd, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&S->ev_adj, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
@@ -897,6 +1012,7 @@ dm_status dm_server_create(dm_server** out, const dm_server_options* opt) {
         S->arena.release();
         if (S->st) cudaStreamDestroy(S->st);
         if (S->d_counter) cudaFree(S->d_counter);
+        if (S->d_losses) cudaFree(S->d_losses);
         dm_destroy(ctx);
         delete S;
         return DM_ERR_OOM;
@@ -1085,6 +1201,11 @@ dm_status dm_server_shutdown(dm_server* S) {
     cudaFree(S->d_uf);
     cudaFree(S->d_ua);
     cudaFree(S->d_counter);
+    cudaFree(S->d_losses);
+    cudaFree(S->d_sj);
+    cudaFree(S->d_offs);
+    cudaFree(S->d_fftj);
+    cudaFree(S->d_fft_offs);
     cudaFreeHost(S->h_loss);
     for (auto& p : S->free_streams) {
         cudaStreamDestroy(p.first);

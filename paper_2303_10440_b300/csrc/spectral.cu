@@ -58,12 +58,12 @@ __device__ __forceinline__ void store_rec(TriF64& r, const double* v1, const dou
 }
 
 template <class Rec>
-__global__ void __launch_bounds__(NT) k_tri_prep(int mode, const double* __restrict__ V, int64_t n_v,
+__device__ __forceinline__ void k_tri_prep_body(int mode, const double* __restrict__ V, int64_t n_v,
                                                  const int32_t* __restrict__ F, int64_t n_t,
                                                  const float* __restrict__ wts, Geom g, Rec* __restrict__ rec,
-                                                 int64_t n_t_pad, double* __restrict__ partial, int* err) {
+                                                 int64_t n_t_pad, double* __restrict__ partial, int* err, int64_t blk, int64_t nblk) {
     __shared__ double scratch[32];
-    const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t t = blk * NT + threadIdx.x;
     double contrib = 0.0;
     if (t < n_t_pad) {
         Rec r;
@@ -116,15 +116,21 @@ __global__ void __launch_bounds__(NT) k_tri_prep(int mode, const double* __restr
         rec[t] = r;
     }
     const double s = block_sum<NT>(contrib, scratch);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[blk] = s;
+}
+template <class Rec>
+__global__ void __launch_bounds__(NT) k_tri_prep(int mode, const double* __restrict__ V, int64_t n_v,
+                                                 const int32_t* __restrict__ F, int64_t n_t,
+                                                 const float* __restrict__ wts, Geom g, Rec* __restrict__ rec,
+                                                 int64_t n_t_pad, double* __restrict__ partial, int* err) {
+    k_tri_prep_body<Rec>(mode, V, n_v, F, n_t, wts, g, rec, n_t_pad, partial, err, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
 // out[k] = sum_{b < n} x[b * count + k]  (one block per k, fixed order)
 // err_nonpos (nullable): ERR_DEGENERATE is raised there when a sum is not > 0 (zero, negative, NaN).
-__global__ void __launch_bounds__(1024) k_sum(const double* __restrict__ x, int64_t n, int count,
-                                              double* __restrict__ out, int* __restrict__ err_nonpos) {
+__device__ __forceinline__ void k_sum_body(const double* __restrict__ x, int64_t n, int count, int k,
+                                           double* __restrict__ out, int* __restrict__ err_nonpos) {
     __shared__ double scratch[32];
-    const int k = blockIdx.x;
     double s = 0.0;
     for (int64_t b = threadIdx.x; b < n; b += 1024) s += x[b * count + k];
     s = block_sum<1024>(s, scratch);
@@ -132,6 +138,10 @@ __global__ void __launch_bounds__(1024) k_sum(const double* __restrict__ x, int6
         out[k] = s;
         if (err_nonpos && !(s > 0.0)) atomicOr(err_nonpos, ERR_DEGENERATE);
     }
+}
+__global__ void __launch_bounds__(1024) k_sum(const double* __restrict__ x, int64_t n, int count,
+                                              double* __restrict__ out, int* __restrict__ err_nonpos) {
+    k_sum_body(x, n, count, (int)blockIdx.x, out, err_nonpos);
 }
 
 // ---------------------------------------------------------------- narrow band
@@ -298,9 +308,9 @@ __device__ __forceinline__ R wave(int n, R tp) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, FreqSrc fs, const double* __restrict__ psf,
+__device__ __forceinline__ void k_scatter_body(const Cx<R>* __restrict__ S, FreqSrc fs, const double* __restrict__ psf,
                                                 int kind, const double* __restrict__ d_norm, double tpx, double tpy,
-                                                double tpz, double inv_VL, Cx<R>* __restrict__ spec) {
+                                                double tpz, double inv_VL, Cx<R>* __restrict__ spec, int64_t blk, int64_t nblk) {
     __shared__ R s_scale;  // one FP64 division per block, not per frequency
     __shared__ R s_c[9];
     if (threadIdx.x == 0) s_scale = (R)(inv_VL / *d_norm);
@@ -308,7 +318,7 @@ __global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, Fre
     __syncthreads();
     const int64_t M = fs.dM ? *fs.dM : fs.M;
     // grid-stride, so that the per-block set-up above is paid by few blocks
-    for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M; m += (int64_t)gridDim.x * NT) {
+    for (int64_t m = blk * NT + threadIdx.x; m < M; m += nblk * NT) {
         const int64_t idx = fs.idx ? (int64_t)fs.idx[m] : m;
         int nx, ny, nz;
         decode_h(idx, fs, nx, ny, nz);
@@ -322,15 +332,21 @@ __global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, Fre
         spec[idx] = Cx<R>{s.x * sc, s.y * sc};
     }
 }
+template <class R>
+__global__ void __launch_bounds__(NT) k_scatter(const Cx<R>* __restrict__ S, FreqSrc fs, const double* __restrict__ psf,
+                                                int kind, const double* __restrict__ d_norm, double tpx, double tpy,
+                                                double tpz, double inv_VL, Cx<R>* __restrict__ spec) {
+    k_scatter_body<R>(S, fs, psf, kind, d_norm, tpx, tpy, tpz, inv_VL, spec, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
 
 template <class R>
-__global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* __restrict__ T, int64_t n, int kind,
-                                             R* __restrict__ resid, double* __restrict__ partial, double inv_n) {
+__device__ __forceinline__ void k_loss_body(const R* __restrict__ I, const R* __restrict__ T, int64_t n, int kind,
+                                             R* __restrict__ resid, double* __restrict__ partial, double inv_n, int64_t blk, int64_t nblk) {
     __shared__ double scratch[32];
     // per voxel in the path's precision R, per-thread sums as TSum, the block sum in FP64
     TSum<R> lsum;
     const R s = kind == 1 ? (R)(2.0 * inv_n) : (R)2;
-    for (int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x; j < n; j += (int64_t)gridDim.x * NT) {
+    for (int64_t j = blk * NT + threadIdx.x; j < n; j += nblk * NT) {
         const R t = T[j];
         const R d = I[j] - t;
         const R w = kind == 2 ? t : (R)1;
@@ -340,7 +356,12 @@ __global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* _
     }
     double l = block_sum_t<NT>(lsum, scratch);
     if (kind == 1) l *= inv_n;
-    if (threadIdx.x == 0) partial[blockIdx.x] = l;
+    if (threadIdx.x == 0) partial[blk] = l;
+}
+template <class R>
+__global__ void __launch_bounds__(NT) k_loss(const R* __restrict__ I, const R* __restrict__ T, int64_t n, int kind,
+                                             R* __restrict__ resid, double* __restrict__ partial, double inv_n) {
+    k_loss_body<R>(I, T, n, kind, resid, partial, inv_n, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
 // Adjoint record of frequency m: lane m % 2 of pair record m / 2 (FP32), or record m (FP64).
@@ -413,11 +434,11 @@ __device__ __forceinline__ void put_rec(FreqF64* fr, int64_t m, int nx, int ny, 
 constexpr int NPART = 8;
 
 template <class R, class FR>
-__global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ S,
+__device__ __forceinline__ void k_gather_body(int mode, const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ S,
                                                FreqSrc fs, const double* __restrict__ psf, int kind,
                                                const double* __restrict__ d_norm, double tpx, double tpy, double tpz,
                                                double inv_VL, FR* __restrict__ fr, int64_t M_pad,
-                                               double* __restrict__ partial) {
+                                               double* __restrict__ partial, int64_t blk, int64_t nblk) {
     // Per frequency in the path's precision R; the sums over frequencies in FP64. Grid-stride over
     // the padded band, so each block reduces its partial sums once.
     __shared__ double scratch[7 * NT / 32];  // >= 32 doubles for the FP64 block sums
@@ -433,7 +454,7 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
     const R s0 = s_c[0], s1 = s_c[1], s2 = s_c[2];
     const R tx = (R)tpx, ty = (R)tpy, tz = (R)tpz;
     TSum<R> part[7];
-    for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < M_pad; m += (int64_t)gridDim.x * NT) {
+    for (int64_t m = blk * NT + threadIdx.x; m < M_pad; m += nblk * NT) {
         // padding records (m >= M) are zeros; every lane of a warp runs the same iterations (M_pad
         // is a multiple of 256), as the paired record write below needs
         int nx = 0, ny = 0, nz = 0;
@@ -493,14 +514,22 @@ __global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict
             pc[k] = part[k].c;
         }
         const double v = block_sums_comp<NT, 7>(ps, pc, scratch);
-        if (threadIdx.x < 7) partial[blockIdx.x * NPART + threadIdx.x] = v;
+        if (threadIdx.x < 7) partial[blk * NPART + threadIdx.x] = v;
     } else {
         for (int k = 0; k < 7; ++k) {
             const double v = block_sum_t<NT>(part[k], scratch);
-            if (threadIdx.x == 0) partial[blockIdx.x * NPART + k] = v;
+            if (threadIdx.x == 0) partial[blk * NPART + k] = v;
         }
     }
-    if (threadIdx.x == 0) partial[blockIdx.x * NPART + 7] = 0.0;
+    if (threadIdx.x == 0) partial[blk * NPART + 7] = 0.0;
+}
+template <class R, class FR>
+__global__ void __launch_bounds__(NT) k_gather(int mode, const Cx<R>* __restrict__ spec, const Cx<R>* __restrict__ S,
+                                               FreqSrc fs, const double* __restrict__ psf, int kind,
+                                               const double* __restrict__ d_norm, double tpx, double tpy, double tpz,
+                                               double inv_VL, FR* __restrict__ fr, int64_t M_pad,
+                                               double* __restrict__ partial) {
+    k_gather_body<R, FR>(mode, spec, S, fs, psf, kind, d_norm, tpx, tpy, tpz, inv_VL, fr, M_pad, partial, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
 template <class R, class FR>
@@ -548,24 +577,24 @@ __global__ void __launch_bounds__(NT) k_prep_raw(int mode, const Cx<R>* __restri
 // left out.
 constexpr int RC_WARPS = 16;
 template <class R>
-__global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __restrict__ partial, int n_chunks, int nacc,
+__device__ __forceinline__ void k_reduce_chunks_body(const R* __restrict__ partial, int n_chunks, int nacc,
                                                                  int64_t n_t, int64_t n_t_pad,
                                                                  double* __restrict__ acc,
                                                                  const int64_t* __restrict__ dM, int64_t M_max,
-                                                                 double* __restrict__ out_slices) {
+                                                                 double* __restrict__ out_slices, int bx, int by, int bz, int gz) {
     __shared__ double sh[RC_WARPS][32];
-    const int slice_len = (n_chunks + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int slice_len = (n_chunks + gz - 1) / gz;
     if (M_max >= 0) {
         const int64_t M = dM ? *dM : M_max;
         const int64_t tiles = (M + ADJ_FTILE - 1) / ADJ_FTILE;
         const int64_t tpc = (tiles + n_chunks - 1) / n_chunks;
         n_chunks = tpc > 0 ? (int)min((int64_t)n_chunks, (tiles + tpc - 1) / tpc) : 0;
     }
-    const int c0 = (int)blockIdx.z * slice_len;
+    const int c0 = bz * slice_len;
     const int c1 = min(n_chunks, c0 + slice_len);
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int64_t t = (int64_t)blockIdx.x * 32 + lane;
-    const int k = (int)blockIdx.y;
+    const int64_t t = (int64_t)bx * 32 + lane;
+    const int k = by;
     const int64_t cs = (int64_t)nacc * n_t_pad;  // stride between chunks
     TSum<R> s0, s1, s2, s3;  // per-thread sums in the path's precision (compensated in FP32)
     if (t < n_t) {
@@ -585,22 +614,34 @@ __global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __rest
         double r = 0.0;
 #pragma unroll
         for (int i = 0; i < RC_WARPS; ++i) r += sh[i][lane];
-        if (gridDim.z == 1)
+        if (gz == 1)
             acc[t * nacc + k] = r;
         else
-            out_slices[((int64_t)blockIdx.z * nacc + k) * n_t + t] = r;
+            out_slices[((int64_t)bz * nacc + k) * n_t + t] = r;
     }
+}
+template <class R>
+__global__ void __launch_bounds__(32 * RC_WARPS) k_reduce_chunks(const R* __restrict__ partial, int n_chunks, int nacc,
+                                                                 int64_t n_t, int64_t n_t_pad,
+                                                                 double* __restrict__ acc,
+                                                                 const int64_t* __restrict__ dM, int64_t M_max,
+                                                                 double* __restrict__ out_slices) {
+    k_reduce_chunks_body<R>(partial, n_chunks, nacc, n_t, n_t_pad, acc, dM, M_max, out_slices, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.z);
 }
 
 // acc[t][k] = sum over slices s (in order) of slices[s][k][t].
-__global__ void __launch_bounds__(NT) k_reduce_slices(const double* __restrict__ slices, int n_slices, int nacc,
-                                                      int64_t n_t, double* __restrict__ acc) {
-    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+__device__ __forceinline__ void k_reduce_slices_body(const double* __restrict__ slices, int n_slices, int nacc,
+                                                      int64_t n_t, double* __restrict__ acc, int64_t blk, int64_t nblk) {
+    const int64_t i = blk * NT + threadIdx.x;
     if (i >= n_t * nacc) return;
     const int64_t k = i / n_t, t = i - k * n_t;
     double r = 0.0;
     for (int s = 0; s < n_slices; ++s) r += slices[((int64_t)s * nacc + k) * n_t + t];
     acc[t * nacc + k] = r;
+}
+__global__ void __launch_bounds__(NT) k_reduce_slices(const double* __restrict__ slices, int n_slices, int nacc,
+                                                      int64_t n_t, double* __restrict__ acc) {
+    k_reduce_slices_body(slices, n_slices, nacc, n_t, acc, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
 // ---------------------------------------------------------------- gradient assembly
@@ -611,11 +652,11 @@ __device__ __forceinline__ void cross(const double* a, const double* b, double* 
 }
 
 // contrib[t][p][3]: the corner (t, p) share of dL/dv_p (Eq. 6, 9).
-__global__ void __launch_bounds__(NT) k_assemble(int mode, const double* __restrict__ V, const int32_t* __restrict__ F,
+__device__ __forceinline__ void k_assemble_body(int mode, const double* __restrict__ V, const int32_t* __restrict__ F,
                                                  int64_t n_t, int64_t n_v, const float* __restrict__ wts, Geom g,
                                                  const double* __restrict__ acc, const double* __restrict__ d_coef,
-                                                 double* __restrict__ contrib) {
-    const int64_t t = (int64_t)blockIdx.x * NT + threadIdx.x;
+                                                 double* __restrict__ contrib, int64_t blk, int64_t nblk) {
+    const int64_t t = blk * NT + threadIdx.x;
     if (t >= n_t) return;
     double out[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     int32_t id[3] = {F[3 * t], F[3 * t + 1], F[3 * t + 2]};
@@ -662,6 +703,12 @@ __global__ void __launch_bounds__(NT) k_assemble(int mode, const double* __restr
     }
     for (int p = 0; p < 3; ++p)
         for (int a = 0; a < 3; ++a) contrib[(3 * t + p) * 3 + a] = out[p][a];
+}
+__global__ void __launch_bounds__(NT) k_assemble(int mode, const double* __restrict__ V, const int32_t* __restrict__ F,
+                                                 int64_t n_t, int64_t n_v, const float* __restrict__ wts, Geom g,
+                                                 const double* __restrict__ acc, const double* __restrict__ d_coef,
+                                                 double* __restrict__ contrib) {
+    k_assemble_body(mode, V, F, n_t, n_v, wts, g, acc, d_coef, contrib, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
 __global__ void __launch_bounds__(NT) k_csr_count(const int32_t* __restrict__ F, int64_t n3, int64_t n_v,
@@ -728,10 +775,10 @@ __global__ void __launch_bounds__(NT) k_csr_sort(const int32_t* __restrict__ ptr
     }
 }
 
-__global__ void __launch_bounds__(NT) k_vertex_gather(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+__device__ __forceinline__ void k_vertex_gather_body(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
                                                       const double* __restrict__ contrib, int64_t n_v,
-                                                      double* __restrict__ dV) {
-    const int64_t v = (int64_t)blockIdx.x * NT + threadIdx.x;
+                                                      double* __restrict__ dV, int64_t blk, int64_t nblk) {
+    const int64_t v = blk * NT + threadIdx.x;
     if (v >= n_v) return;
     double s0 = 0, s1 = 0, s2 = 0;
     for (int32_t i = ptr[v]; i < ptr[v + 1]; ++i) {
@@ -744,8 +791,27 @@ __global__ void __launch_bounds__(NT) k_vertex_gather(const int32_t* __restrict_
     dV[3 * v + 1] = s1;
     dV[3 * v + 2] = s2;
 }
+__global__ void __launch_bounds__(NT) k_vertex_gather(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+                                                      const double* __restrict__ contrib, int64_t n_v,
+                                                      double* __restrict__ dV) {
+    k_vertex_gather_body(ptr, ent, contrib, n_v, dV, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
 
 // ---------------------------------------------------------------- Adam
+// One Adam update of element i; bc1 = 1 - b1^t and bc2 = 1 - b2^t are the bias corrections of step t.
+__device__ __forceinline__ void adam_elem(double* __restrict__ p, const double* __restrict__ g, double* __restrict__ m,
+                                          double* __restrict__ v, int64_t i, double lr, double b1, double b2,
+                                          double eps, double bc1, double bc2) {
+    const double gi = g[i];
+    const double mi = b1 * m[i] + (1.0 - b1) * gi;
+    const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const double mh = mi / bc1;
+    const double vh = vi / bc2;
+    p[i] -= lr * mh / (sqrt(vh) + eps);
+}
+
 __global__ void __launch_bounds__(NT) k_adam(double* __restrict__ p, const double* __restrict__ g, double* __restrict__ m,
                                              double* __restrict__ v, int64_t n, double lr, double b1, double b2,
                                              double eps, int64_t step, const int64_t* __restrict__ d_step,
@@ -754,14 +820,7 @@ __global__ void __launch_bounds__(NT) k_adam(double* __restrict__ p, const doubl
     if (i >= n) return;
     const double t = (double)(d_step ? *d_step : step);
     if (decay != 1.0) lr *= pow(decay, t - 1.0);  // step t takes the rate lr decay^(t-1)
-    const double gi = g[i];
-    const double mi = b1 * m[i] + (1.0 - b1) * gi;
-    const double vi = b2 * v[i] + (1.0 - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const double mh = mi / (1.0 - pow(b1, t));
-    const double vh = vi / (1.0 - pow(b2, t));
-    p[i] -= lr * mh / (sqrt(vh) + eps);
+    adam_elem(p, g, m, v, i, lr, b1, b2, eps, 1.0 - pow(b1, t), 1.0 - pow(b2, t));
 }
 
 // End of one fit step: hist[t - step0 - 1] = loss of the step, then t += 1 (t: the Adam step on the
@@ -800,6 +859,162 @@ cudaError_t one_wave(int* out) {
     }
     *out = w;
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- batched stages (fit server)
+// Block b of a batched launch belongs to the largest job j with offs[j] <= b (offs[0] = 0 and offs[nj]
+// = the launch's blocks; a job without blocks in the stage has offs[j] = offs[j + 1] and is never
+// found), as its block b - offs[j] of offs[j + 1] - offs[j].
+struct BatchBlock {
+    int j;
+    int64_t b, nb;
+};
+__device__ __forceinline__ BatchBlock batch_block(const int* __restrict__ offs, int nj) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = nj;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (offs[mid] <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return {lo, (int64_t)(b - offs[lo]), (int64_t)(offs[lo + 1] - offs[lo])};
+}
+
+__device__ __forceinline__ double two_pi_over(double L) { return 2.0 * M_PI / L; }
+
+__global__ void __launch_bounds__(NT) kb_tri_prep(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                  int nj, int* err) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    k_tri_prep_body<TriF32>(J.mode, J.V, J.n_v, J.F, J.n_t, J.wts, J.g, J.tris, J.n_t_pad, J.partial, err, q.b, q.nb);
+}
+
+// Zero the half spectrum of a narrow-band job (the scatter writes the band entries only).
+__global__ void __launch_bounds__(NT) kb_zero(const StageJob* __restrict__ jobs, const int* __restrict__ offs, int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    float4* p = reinterpret_cast<float4*>(J.spec);
+    const int64_t n4 = J.nH / 2;  // two complex values per float4
+    for (int64_t i = q.b * NT + threadIdx.x; i < n4; i += q.nb * NT) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if ((J.nH & 1) && q.b == 0 && threadIdx.x == 0) J.spec[J.nH - 1] = Cx<float>{0.f, 0.f};
+}
+
+__global__ void __launch_bounds__(NT) kb_scatter(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                 int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    const Geom g = J.g;
+    k_scatter_body<float>((const Cx<float>*)J.S, J.fs, J.params, J.psf_kind, J.params + 16, two_pi_over(g.L[0]),
+                          two_pi_over(g.L[1]), two_pi_over(g.L[2]), 1.0 / (g.L[0] * g.L[1] * g.L[2]), J.spec, q.b,
+                          q.nb);
+}
+
+__global__ void __launch_bounds__(NT) kb_loss(const StageJob* __restrict__ jobs, const int* __restrict__ offs, int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    k_loss_body<float>(J.image, J.target, J.N, J.loss_kind, J.resid, J.partial, 1.0 / (double)J.N, q.b, q.nb);
+}
+
+__global__ void __launch_bounds__(NT) kb_gather(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    const Geom g = J.g;
+    k_gather_body<float, FreqPairF32>(J.mode, J.spec, (const Cx<float>*)J.S, J.fs, J.params, J.psf_kind,
+                                      J.params + 16, two_pi_over(g.L[0]), two_pi_over(g.L[1]), two_pi_over(g.L[2]),
+                                      1.0 / (g.L[0] * g.L[1] * g.L[2]), J.fr, J.M_pad, J.partial, q.b, q.nb);
+}
+
+// params[dst + k] = sum over the job's blocks b of the producing stage of partial[b * count + k]
+// (block = (job, k), the single-job k_sum's order).
+__global__ void __launch_bounds__(1024) kb_sum(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                               int count, int dst, int* __restrict__ err_nonpos) {
+    const int j = (int)blockIdx.x / count, k = (int)blockIdx.x - j * count;
+    const StageJob& J = jobs[j];
+    k_sum_body(J.partial, offs[j + 1] - offs[j], count, k, J.params + dst, err_nonpos);
+}
+
+// Chunk reduction: the job's blocks are its single-job grid (tb, nacc, slices) in x-fastest order.
+__global__ void __launch_bounds__(32 * RC_WARPS) kb_reduce_chunks(const StageJob* __restrict__ jobs,
+                                                                  const int* __restrict__ offs, int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    const int tb = (int)((J.n_t + 31) / 32);
+    const int bx = (int)(q.b % tb), rest = (int)(q.b / tb);
+    const int by = rest % J.nacc, bz = rest / J.nacc;
+    k_reduce_chunks_body<float>(J.adjp, J.n_chunks, J.nacc, J.n_t, J.n_t_pad, J.acc, nullptr, -1, J.red, bx, by, bz,
+                                J.rc_slices);
+}
+
+__global__ void __launch_bounds__(NT) kb_reduce_slices(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                       int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    k_reduce_slices_body(J.red, J.rc_slices, J.nacc, J.n_t, J.acc, q.b, q.nb);
+}
+
+__global__ void __launch_bounds__(NT) kb_assemble(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                  int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    k_assemble_body(J.mode, J.V, J.F, J.n_t, J.n_v, J.wts, J.g, J.acc, J.params + 30, J.contrib, q.b, q.nb);
+}
+
+__global__ void __launch_bounds__(NT) kb_vertex_gather(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                       int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    k_vertex_gather_body(J.ptr, J.ent, J.contrib, J.n_v, J.dV, q.b, q.nb);
+}
+
+// Split sums of the forward for the jobs with triangle splits: per element the order of the single-job
+// k_fwd_reduce (compensated FP32 over the splits in order).
+__global__ void __launch_bounds__(256) kb_fwd_reduce(const StageJob* __restrict__ jobs, const int* __restrict__ offs,
+                                                     int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    const int64_t M = J.fs.dM ? *J.fs.dM : J.fs.M;
+    for (int64_t m = q.b * 256 + threadIdx.x; m < M; m += q.nb * 256) {
+        TSum<float> sx, sy;
+        for (int ts = 0; ts < J.fsplits; ++ts) {
+            const float2 v = J.S_part[(int64_t)ts * M + m];
+            sx.add(v.x);
+            sy.add(v.y);
+        }
+        J.S[m] = make_float2(sx.s, sy.s);
+    }
+}
+
+// Adam on the vertices with the job's step t (on the device) and rate lr decay^(t-1).
+__global__ void __launch_bounds__(NT) kb_adam(const StageJob* __restrict__ jobs, const int* __restrict__ offs, int nj) {
+    const BatchBlock q = batch_block(offs, nj);
+    const StageJob& J = jobs[q.j];
+    const int64_t i = q.b * NT + threadIdx.x;
+    if (i >= 3 * J.n_v) return;
+    const double t = (double)*J.d_step;
+    const double lr = J.decay != 1.0 ? J.lr_v * pow(J.decay, t - 1.0) : J.lr_v;
+    adam_elem(J.V, J.dV, J.mV, J.vV, i, lr, J.b1, J.b2, J.eps, 1.0 - pow(J.b1, t), 1.0 - pow(J.b2, t));
+}
+
+// End of a step, one thread per job: Adam on sigma (lr_psf > 0) with the gradient params[24..26],
+// the loss into the history and the engine's array, and the step counter advanced.
+__global__ void kb_tick(const StageJob* __restrict__ jobs, int nj, double* __restrict__ losses) {
+    const int j = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= nj) return;
+    const StageJob& J = jobs[j];
+    const int64_t step = *J.d_step;
+    const double t = (double)step;
+    if (J.lr_psf > 0) {
+        const double lr = J.decay != 1.0 ? J.lr_psf * pow(J.decay, t - 1.0) : J.lr_psf;
+        const double bc1 = 1.0 - pow(J.b1, t), bc2 = 1.0 - pow(J.b2, t);
+        for (int a = 0; a < 3; ++a) adam_elem(J.params, J.params + 24, J.ms, J.vs, a, lr, J.b1, J.b2, J.eps, bc1, bc2);
+    }
+    const double L = J.params[17];
+    J.hist[step - J.step0 - 1] = L;
+    losses[j] = L;
+    *J.d_step = step + 1;
 }
 
 }  // namespace
@@ -937,12 +1152,7 @@ cudaError_t launch_reduce_chunks(const R* partial, int n_chunks, int nacc, int64
     const int64_t tb = (n_t + 31) / 32;
     // few triangles: split the chunks into slices so that about 4 blocks per SM run (the scratch
     // holds reduce_scratch_elems(sm_count) doubles, enough for slices * nacc * n_t at that count)
-    int64_t slices = 1;
-    if (scratch && sm_count > 0 && tb * nacc < 4LL * sm_count) {
-        slices = (4LL * sm_count + tb * nacc - 1) / (tb * nacc);
-        slices = std::min<int64_t>(slices, std::max(1, n_chunks / (4 * RC_WARPS)));
-        if (slices * nacc * n_t > reduce_scratch_elems(sm_count)) slices = 1;
-    }
+    const int64_t slices = scratch ? reduce_slices_for(n_t, nacc, n_chunks, sm_count) : 1;
     const dim3 grid((unsigned)tb, (unsigned)nacc, (unsigned)slices), block(32, RC_WARPS);
     k_reduce_chunks<R><<<grid, block, 0, st>>>(partial, n_chunks, nacc, n_t, n_t_pad, acc, dM, M_max, scratch);
     if (slices > 1) k_reduce_slices<<<nblk(n_t * nacc), NT, 0, st>>>(scratch, (int)slices, nacc, n_t, acc);
@@ -998,6 +1208,71 @@ cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* 
 
 cudaError_t launch_fit_tick(double* hist, const double* d_loss, int64_t* d_step, int64_t step0, cudaStream_t st) {
     k_fit_tick<<<1, 32, 0, st>>>(hist, d_loss, d_step, step0);
+    return cudaGetLastError();
+}
+
+void batch_stage_blocks(const StageJob& J, int sm_count, int counts[BS_COUNT]) {
+    int w_scatter = 0, w_loss = 0, w_gather = 0;
+    one_wave<k_scatter<float>>(&w_scatter);
+    one_wave<k_loss<float>>(&w_loss);
+    one_wave<k_gather<float, FreqPairF32>>(&w_gather);
+    for (int s = 0; s < BS_COUNT; ++s) counts[s] = 0;
+    counts[BS_PREP] = (int)nblk(J.n_t_pad);
+    counts[BS_FWDRED] = J.fsplits > 1 ? (int)std::min<int64_t>(nblk(J.nH), 4LL * sm_count) : 0;
+    counts[BS_ZERO] = J.band ? (int)std::min<int64_t>(nblk((J.nH + 1) / 2), 8LL * sm_count) : 0;
+    // the single-job launches' grids: one wave of resident blocks at most
+    counts[BS_SCATTER] = (int)std::min<int64_t>(nblk(J.nH), std::max(1, w_scatter));
+    counts[BS_LOSS] = (int)std::min<int64_t>(nblk(J.N), std::min(std::max(1, w_loss), 4096));
+    counts[BS_GATHER] = (int)std::min<int64_t>(nblk(J.M_pad), std::max(1, w_gather));
+    counts[BS_REDUCE] = (int)((J.n_t + 31) / 32) * J.nacc * J.rc_slices;
+    counts[BS_SLICES] = J.rc_slices > 1 ? (int)nblk(J.n_t * J.nacc) : 0;
+    counts[BS_ASSEMBLE] = (int)nblk(J.n_t);
+    counts[BS_VGATHER] = (int)nblk(J.n_v);
+    counts[BS_ADAM] = J.vertex_adam ? (int)nblk(3 * J.n_v) : 0;
+}
+
+int reduce_slices_for(int64_t n_t, int nacc, int n_chunks, int sm_count) {
+    const int64_t tb = (n_t + 31) / 32;
+    int64_t slices = 1;
+    if (sm_count > 0 && tb * nacc < 4LL * sm_count) {
+        slices = (4LL * sm_count + tb * nacc - 1) / (tb * nacc);
+        slices = std::min<int64_t>(slices, std::max(1, n_chunks / (4 * RC_WARPS)));
+        if (slices * nacc * n_t > (int64_t)reduce_scratch_elems(sm_count)) slices = 1;
+    }
+    return (int)slices;
+}
+
+cudaError_t launch_batch_stage(int stage, const StageJob* jobs, const int* offsets, int nj, int total, int* d_err,
+                               cudaStream_t st) {
+    if (total <= 0 || nj <= 0) return cudaSuccess;
+    const int* o = offsets + (size_t)stage * (nj + 1);
+    switch (stage) {
+        case BS_PREP: kb_tri_prep<<<total, NT, 0, st>>>(jobs, o, nj, d_err); break;
+        case BS_FWDRED: kb_fwd_reduce<<<total, 256, 0, st>>>(jobs, o, nj); break;
+        case BS_ZERO: kb_zero<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_SCATTER: kb_scatter<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_LOSS: kb_loss<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_GATHER: kb_gather<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_REDUCE: kb_reduce_chunks<<<total, dim3(32, RC_WARPS), 0, st>>>(jobs, o, nj); break;
+        case BS_SLICES: kb_reduce_slices<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_ASSEMBLE: kb_assemble<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_VGATHER: kb_vertex_gather<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        case BS_ADAM: kb_adam<<<total, NT, 0, st>>>(jobs, o, nj); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sum(const StageJob* jobs, const int* stage_offsets, int nj, int count, int dst, int* flag_err,
+                             cudaStream_t st) {
+    if (nj <= 0) return cudaSuccess;
+    kb_sum<<<nj * count, 1024, 0, st>>>(jobs, stage_offsets, count, dst, flag_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_tick(const StageJob* jobs, int nj, double* losses, cudaStream_t st) {
+    if (nj <= 0) return cudaSuccess;
+    kb_tick<<<(nj + 63) / 64, 64, 0, st>>>(jobs, nj, losses);
     return cudaGetLastError();
 }
 
