@@ -99,8 +99,10 @@ def parse():
                    "step time against grid size and triangle count (the paper's GPU timing figure) and a "
                    "narrow-band case")
     p.add_argument("--rounds", type=int, default=4, help="staggered rounds in the stagger mode")
-    p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 10)")
+    p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 100)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
+    p.add_argument("--legs", default="fifo,shortest,sequential",
+                   help="serve modes: which legs to run (fifo, shortest, sequential one-at-a-time FP32)")
     p.add_argument("--lr-decay", type=float, default=0.998, help="per-step learning-rate factor in the robust mode")
     p.add_argument("--clip-target", type=int, default=1, help="robust mode: clip noisy targets at zero")
     p.add_argument("--rates", default="10,20,50,100,200,500", help="Poisson arrival rates (1/s) in serve-c5")
@@ -338,7 +340,8 @@ def serving_jobs(r32, n_jobs, seed, levels, sides, steps):
 
 
 def _queue_latencies(arrivals, durations):
-    """One job at a time in arrival order: completion = max(arrival, previous completion) + duration."""
+    """One job at a time in arrival order, from measured durations: completion = max(arrival, previous
+    completion) + duration (used only where running the leg would take too long, and labelled so)."""
     t, lat = 0.0, []
     for a, d in zip(arrivals, durations):
         t = max(t, a) + d
@@ -346,12 +349,51 @@ def _queue_latencies(arrivals, durations):
     return np.array(lat), t - arrivals[0]
 
 
+def _one_at_a_time_run(r, jobs, arrivals, dev):
+    """The one-fit-at-a-time path, run open loop: requests arrive at `arrivals` (seconds) into a FIFO
+    queue that one worker drains, each job through dm_fit alone (inputs copied from the host first, as
+    the server copies them at admission). Returns (latencies, span) as observed on the wall clock."""
+    import queue
+    import threading
+
+    import torch
+
+    q = queue.Queue()
+    done = [0.0] * len(jobs)
+
+    def worker():
+        while True:
+            k = q.get()
+            if k is None:
+                return
+            j = jobs[k]
+            Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
+            Td = torch.as_tensor(j["target"]).to(dev)
+            r.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=j["steps"], lr_vertex=j["lr_vertex"])
+            torch.cuda.synchronize(dev)
+            done[k] = time.perf_counter()
+
+    torch.cuda.synchronize(dev)
+    th = threading.Thread(target=worker)
+    th.start()
+    t0 = time.perf_counter()
+    for k, a in enumerate(arrivals):
+        delay = t0 + a - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        q.put(k)
+    q.put(None)
+    th.join()
+    lat = np.array([done[k] - (t0 + arrivals[k]) for k in range(len(jobs))])
+    return lat, max(done) - t0
+
+
 def _stats(lat, span, n):
     return {"fits_per_s": n / span, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "span_s": span}
 
 
-def _served_run(jobs, arrivals, dev, **server_kw):
+def _served_run(jobs, arrivals, dev, keep=False, **server_kw):
     import threading
 
     from paper_2303_10440_b300.serve import FitServer
@@ -372,48 +414,36 @@ def _served_run(jobs, arrivals, dev, **server_kw):
     th.join()
     res = []
     for i in ids:
-        srv.wait(i, timeout=600)
+        srv.wait(i, timeout=7200)
         res.append(srv.result(i))
     st = srv.stats()
     srv.shutdown()
     lat = np.array([r.latency for r in res])
     span = max(r.t_end for r in res) - min(r.t_submit for r in res)
-    return dict(_stats(lat, span, len(jobs)), peak_batch=int(st["peak_active"]), iterations=int(st["iterations"]))
+    out = dict(_stats(lat, span, len(jobs)), peak_batch=int(st["peak_active"]), iterations=int(st["iterations"]))
+    if keep:
+        out["results"] = res
+    return out
 
 
 def serving_leg(args, dev, n_jobs=16, rates=(10.0, 50.0, 100.0, 500.0), steps=10, levels=(2, 3), sides=(32, 48, 64),
                 with_fp64=True):
     """Served fits/s and p50/p99 latency vs one-job-at-a-time FP32 and plain FP64 at each arrival rate.
 
-    The one-at-a-time durations are measured once per job; their latencies at each rate follow
-    from the same arrival times (completion = max(arrival, previous completion) + duration)."""
-    import torch
-
+    Every leg runs open loop on the wall clock: the served legs through the fit server, the one-at-a-time
+    FP32 leg through a worker that runs dm_fit on one job at a time. The plain FP64 leg (about 100x slower)
+    runs once, at the highest rate, where every request is queued at once."""
     from paper_2303_10440_b300 import Renderer
 
     r32 = Renderer("fp32", device=dev.index or 0)
     jobs = serving_jobs(r32, n_jobs, 5, levels, sides, steps)
-    legs = [("sequential_fp32", r32)]
-    if with_fp64:
-        legs.append(("plain_fp64", Renderer("fp64", device=dev.index or 0)))
-    durations = {}
-    for name, r in legs:
-        durs = []
-        for j in jobs:
-            Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
-            Td = torch.as_tensor(j["target"]).to(dev)
-            torch.cuda.synchronize(dev)
-            t = time.perf_counter()
-            r.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=steps, lr_vertex=j["lr_vertex"])
-            torch.cuda.synchronize(dev)
-            durs.append(time.perf_counter() - t)
-        durations[name] = durs
+    _one_at_a_time_run(r32, jobs[:2], [0.0, 0.0], dev)  # warm-up (modules, FFT tables)
     out = {
         "workload": f"{n_jobs} fit requests, icosphere levels {list(levels)}, cubic grids {list(sides)} of "
         f"(0.5, 0.5, 1) um, sigma_xy~U(0.15,0.3) um, sigma_z~U(0.4,0.9) um, {steps} Adam steps each, "
         f"open-loop Poisson arrivals",
-        "one_at_a_time_note": "sequential_fp32 / plain_fp64: each job alone through dm_fit (FP32 / FP64 context), "
-        "durations measured once, queued in arrival order",
+        "one_at_a_time_note": "sequential_fp32 / plain_fp64: each job alone through dm_fit (FP32 / FP64 context) "
+        "by one worker draining an open-loop FIFO queue, latencies observed on the wall clock",
         "rates": {},
     }
     for rate in rates:
@@ -422,12 +452,18 @@ def serving_leg(args, dev, n_jobs=16, rates=(10.0, 50.0, 100.0, 500.0), steps=10
         arrivals -= arrivals[0]
         entry = {"served_fp32": _served_run(jobs, arrivals, dev),
                  "served_fp32_shortest_first": _served_run(jobs, arrivals, dev, policy="shortest", batch_terms=3e9)}
-        for name, durs in durations.items():
-            lat, span = _queue_latencies(arrivals, durs)
-            entry[name] = _stats(lat, span, n_jobs)
+        lat, span = _one_at_a_time_run(r32, jobs, arrivals, dev)
+        entry["sequential_fp32"] = _stats(lat, span, n_jobs)
+        if with_fp64 and rate == max(rates):
+            r64 = Renderer("fp64", device=dev.index or 0)
+            lat, span = _one_at_a_time_run(r64, jobs, arrivals, dev)
+            entry["plain_fp64"] = _stats(lat, span, n_jobs)
+            r64.close()
         out["rates"][f"{rate:g}/s"] = entry
     if with_fp64:
-        r64 = legs[-1][1]
+        import torch
+
+        r64 = Renderer("fp64", device=dev.index or 0)
         errs = []
         for j in jobs:
             Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
@@ -674,39 +710,59 @@ def _poisson_arrivals(rate, n, seed=7):
     return a - a[0]
 
 
-def _one_at_a_time(r, jobs, dev):
-    import torch
-
-    durs = []
-    for j in jobs:
-        Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
-        Td = torch.as_tensor(j["target"]).to(dev)
-        torch.cuda.synchronize(dev)
-        t = time.perf_counter()
-        r.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=j["steps"], lr_vertex=j["lr_vertex"])
-        torch.cuda.synchronize(dev)
-        durs.append(time.perf_counter() - t)
-    return durs
-
-
-def _fp64_rate(jobs, dev):
-    """Plain FP64 terms/s measured on one step of the smallest job (the FP64 path is ~100x slower)."""
+def _fp64_alone(jobs, dev, k_small=2):
+    """The plain FP64 path on the k_small cheapest jobs, each run alone through dm_fit (FP64 context):
+    measured durations, and the FP64 terms/s they imply (used for the other jobs, labelled)."""
     import torch
 
     from paper_2303_10440_b300 import Renderer
 
-    j = min(jobs, key=_job_terms)
     r64 = Renderer("fp64", device=dev.index or 0)
-    Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
-    Td = torch.as_tensor(j["target"]).to(dev)
-    r64.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=1, lr_vertex=j["lr_vertex"])
-    torch.cuda.synchronize(dev)
-    t = time.perf_counter()
-    r64.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=2, lr_vertex=j["lr_vertex"])
-    torch.cuda.synchronize(dev)
-    dt = time.perf_counter() - t
+    order = sorted(range(len(jobs)), key=lambda k: _job_terms(jobs[k]))[:k_small]
+    durs = {}
+    for k in order:
+        j = jobs[k]
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        Vd, Fd = torch.as_tensor(j["V"]).to(dev), torch.as_tensor(j["F"]).to(dev)
+        Td = torch.as_tensor(j["target"]).to(dev)
+        r64.fit(Vd, Fd, j["grid"], j["psf"], Td, steps=j["steps"], lr_vertex=j["lr_vertex"])
+        torch.cuda.synchronize(dev)
+        durs[k] = time.perf_counter() - t
     r64.close()
-    return _job_terms(dict(j, steps=2)) / dt
+    rate = sum(_job_terms(jobs[k]) for k in order) / sum(durs.values())
+    return durs, rate
+
+
+def _sampled_spectrum_errors(jobs, results, dev, n_freq=256):
+    """Per job: the fitted mesh's spectrum on seeded random band frequencies, FP32 path against the FP64
+    path (relative L2, and weighted by the transfer function, i.e. the image's Fourier coefficients)."""
+    import torch
+
+    from paper_2303_10440_b300 import Renderer
+
+    r32, r64 = Renderer("fp32", device=dev.index or 0), Renderer("fp64", device=dev.index or 0)
+    errs = []
+    for k, (j, res) in enumerate(zip(jobs, results)):
+        g = j["grid"]
+        band = r32.band(g, j["psf"]).numpy().astype(np.int64)
+        sel = band[np.sort(np.random.default_rng(100 + k).choice(len(band), size=min(n_freq, len(band)),
+                                                                     replace=False))]
+        nzh = g.n[2] // 2 + 1
+        iz, t = sel % nzh, sel // nzh
+        iy, ix = t % g.n[1], t // g.n[1]
+        fn = np.stack([np.where(ix < (g.n[0] + 1) // 2, ix, ix - g.n[0]),
+                       np.where(iy < (g.n[1] + 1) // 2, iy, iy - g.n[1]), iz], axis=1).astype(np.int32)
+        Vd, Fd, fd = (torch.as_tensor(x).to(dev) for x in (res.V, j["F"], fn))
+        a = r32.meshft(Vd, Fd, g, fd).cpu().numpy().astype(np.complex128)
+        b = r64.meshft(Vd, Fd, g, fd).cpu().numpy()
+        xi = 2 * np.pi * fn / np.asarray(g.L)
+        hh = np.exp(-0.5 * (xi ** 2 * np.asarray(j["psf"].sigma) ** 2).sum(1))
+        errs.append({"job": k, "spectrum": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+                     "image_coefficients": float(np.linalg.norm((a - b) * hh) / np.linalg.norm(b * hh))})
+    r32.close()
+    r64.close()
+    return errs
 
 
 def run_serve_mode(args):
@@ -727,13 +783,12 @@ def run_serve_mode(args):
             noisy, scale = synth.add_poisson_gaussian_noise(T, 200.0, 2.0, seed=500 + k)
             jobs.append(dict(V=c["V_init"], F=c["F"], target=noisy / scale, grid=c["grid"], psf=c["psf"], steps=steps,
                              lr_vertex=1e-2 * min(c["grid"].h)))
-        arrivals = np.zeros(len(jobs))
         workload = (f"32 SH-deformed cells packed in a 256^3 tissue (levels 3-5, radii 8-20 um), one fit per cell "
                     f"on its 64^3-128^3 crop, Poisson(peak 200) + N(0, 2^2) noise, {steps} Adam steps, all jobs "
                     f"submitted together (one persistent batched launch per iteration)")
-        rates = {"batch": arrivals}
+        rates = {"batch": np.zeros(len(jobs))}
     else:
-        steps = args.fit_steps or 10
+        steps = args.fit_steps or 100
         rng = np.random.default_rng(55)
         jobs = []
         for k in range(args.jobs):
@@ -742,32 +797,46 @@ def run_serve_mode(args):
                            c["psf"]).cpu().numpy()
             jobs.append(dict(V=c["V_init"], F=c["F"], target=T, grid=c["grid"], psf=c["psf"], steps=steps,
                              lr_vertex=1e-2 * min(c["grid"].h)))
-        workload = (f"{len(jobs)} serving requests (levels 2-6 = 320-81920 triangles, cubic grids 64-256 of "
-                    f"(0.5, 0.5, 1) um, random anisotropic sigma), {steps} Adam steps each (reduced from 100, and "
-                    f"from ~200 requests, to bound the run), open-loop Poisson arrivals")
+        workload = (f"the first {len(jobs)} requests of the seeded serving stream (levels 2-6 = 320-81920 triangles, "
+                    f"cubic grids 64-256 of (0.5, 0.5, 1) um, random anisotropic sigma), {steps} Adam steps each, "
+                    f"open-loop Poisson arrivals")
         rates = {f"{rate:g}/s": _poisson_arrivals(rate, len(jobs)) for rate in
                  (float(x) for x in args.rates.split(",") if x)}
+    legs_wanted = set(args.legs.split(","))
     total_terms = sum(_job_terms(j) for j in jobs)
-    durs = _one_at_a_time(r32, jobs, dev)
-    fp64 = _fp64_rate(jobs, dev)
+    _one_at_a_time_run(r32, jobs[:1], [0.0], dev)  # warm-up
+    fp64_durs, fp64_rate = _fp64_alone(jobs, dev)
     out = {"metric": "served fits/s and p50/p99 latency vs one-at-a-time FP32 and plain FP64", "mode": args.mode,
-           "workload": workload, "n_jobs": len(jobs), "total_terms": total_terms, "results": {}}
-    fp64_durs = [_job_terms(j) / fp64 for j in jobs]
+           "workload": workload, "n_jobs": len(jobs), "total_terms": total_terms,
+           "job_terms": [_job_terms(j) for j in jobs], "results": {},
+           "plain_fp64_measured": {"jobs": sorted(fp64_durs), "seconds": [fp64_durs[k] for k in sorted(fp64_durs)],
+                                   "terms_per_s": fp64_rate},
+           "one_at_a_time_note": "sequential_fp32: one worker drains an open-loop FIFO queue, each job alone "
+                                 "through dm_fit, latencies observed; plain_fp64: the measured FP64 durations of the "
+                                 "two cheapest jobs and, for the others, their terms at the FP64 terms/s those two "
+                                 "measured, queued in arrival order (labelled: an FP64 run of the rest would take hours)"}
+    fp64_durs_all = [fp64_durs.get(k, _job_terms(j) / fp64_rate) for k, j in enumerate(jobs)]
+    first_served = None
 
     def legs(arr, rate=None):
-        served = _served_run(jobs, arr, dev)
-        served["terms_per_s"] = total_terms / served["span_s"]
-        # least-remaining-work scheduling within a per-iteration term budget (about 10 ms of work)
-        shortest = _served_run(jobs, arr, dev, policy="shortest", batch_terms=3e9)
-        shortest["terms_per_s"] = total_terms / shortest["span_s"]
-        lat, span = _queue_latencies(arr, durs)
-        lat64, span64 = _queue_latencies(arr, fp64_durs)
-        e = {
-            "served_fp32": served,
-            "served_fp32_shortest_first": shortest,
-            "sequential_fp32": dict(_stats(lat, span, len(jobs)), terms_per_s=total_terms / span),
-            "plain_fp64_from_measured_rate": dict(_stats(lat64, span64, len(jobs)), terms_per_s=fp64),
-        }
+        nonlocal first_served
+        e = {}
+        if "fifo" in legs_wanted:
+            served = _served_run(jobs, arr, dev, keep=first_served is None)
+            if first_served is None:
+                first_served = served.pop("results")
+            served["terms_per_s"] = total_terms / served["span_s"]
+            e["served_fp32"] = served
+        if "shortest" in legs_wanted:
+            # least-remaining-work scheduling within a per-iteration term budget (about 10 ms of work)
+            shortest = _served_run(jobs, arr, dev, policy="shortest", batch_terms=3e9)
+            shortest["terms_per_s"] = total_terms / shortest["span_s"]
+            e["served_fp32_shortest_first"] = shortest
+        if "sequential" in legs_wanted:
+            lat, span = _one_at_a_time_run(r32, jobs, arr, dev)
+            e["sequential_fp32"] = dict(_stats(lat, span, len(jobs)), terms_per_s=total_terms / span)
+        lat64, span64 = _queue_latencies(arr, fp64_durs_all)
+        e["plain_fp64_from_measured"] = dict(_stats(lat64, span64, len(jobs)), terms_per_s=fp64_rate)
         if rate is not None:
             e["arrival_rate_per_s"] = rate
         return e
@@ -777,12 +846,14 @@ def run_serve_mode(args):
     fracs = [float(x) for x in args.capacity_fracs.split(",") if x] if args.mode == "serve-c5" else []
     if fracs:
         # capacity = the best served throughput seen at the saturating rates above
-        cap = max(max(e["served_fp32"]["fits_per_s"], e["served_fp32_shortest_first"]["fits_per_s"])
+        cap = max(max(e.get("served_fp32", {}).get("fits_per_s", 0.0),
+                      e.get("served_fp32_shortest_first", {}).get("fits_per_s", 0.0))
                   for e in out["results"].values())
         out["capacity_fits_per_s"] = cap
         for f in fracs:
             out["results"][f"{f:g}x capacity"] = legs(_poisson_arrivals(f * cap, len(jobs)), rate=f * cap)
-    out["plain_fp64_terms_per_s_measured"] = fp64
+    if first_served is not None:
+        out["per_job_error_fp32_vs_fp64_sampled"] = _sampled_spectrum_errors(jobs, first_served, dev)
     print(json.dumps(out), flush=True)
 
 

@@ -61,7 +61,8 @@ typedef int32_t dm_status;
 #define DM_ERR_OPEN_MESH (-4)   /* volume mode on a mesh that is not edge-manifold closed */
 #define DM_ERR_TIMEOUT (-5)     /* a bounded device-side wait expired */
 #define DM_ERR_CUDA (-6)        /* a CUDA runtime call failed */
-#define DM_ERR_UNSUPPORTED (-7) /* grid axis longer than 1024 or with a prime factor > 5 */
+#define DM_ERR_UNSUPPORTED (-7) /* grid axis longer than 4096 (FP64: 2048) or with a prime factor > 13,
+                                   or a half spectrum of 2^31 entries or more */
 
 #define DM_FP64 0
 #define DM_FP32_MIXED 1
@@ -87,7 +88,8 @@ typedef struct {
 } dm_options;
 
 typedef struct {
-    int32_t n[3];      /* voxels per axis; each axis 1..1024 with prime factors 2, 3, 5 */
+    int32_t n[3];      /* voxels per axis; each axis 1..4096 (FP64 path: 1..2048) with prime factors
+                          2, 3, 5, 7, 11, 13; Nx * Ny * (Nz/2 + 1) < 2^31 */
     double h[3];       /* voxel size per axis (> 0) */
     double origin[3];  /* position of voxel (0,0,0) */
 } dm_grid;

@@ -210,10 +210,16 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // FFT plans: twiddle tables are computed on the host in double and cached per length.
 dm_status fft_axes(dm_ctx* ctx, const int n[3], FFTAxis ax[3]) {
     const bool f64 = ctx->precision == DM_FP64;
+    int max_smem = 0;
+    CK(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     for (int a = 0; a < 3; ++a) {
         if (!fft_factor(n[a], ax[a]))
-            return fail(ctx, DM_ERR_UNSUPPORTED, "grid axis %d has length %d (need 1..1024 with factors 2,3,5)", a,
-                        n[a]);
+            return fail(ctx, DM_ERR_UNSUPPORTED,
+                        "grid axis %d has length %d (need 1..%d with prime factors 2, 3, 5, 7, 11, 13)", a, n[a],
+                        FFT_MAX_N);
+        if (fft_smem_bytes(n[a], f64 ? 16 : 8) > (size_t)max_smem)
+            return fail(ctx, DM_ERR_UNSUPPORTED, "grid axis %d of length %d is too long for the %s FFT", a, n[a],
+                        f64 ? "FP64" : "FP32");
         auto& cache = f64 ? ctx->tw64 : ctx->tw32;
         auto it = cache.find(n[a]);
         if (it == cache.end()) {
@@ -248,6 +254,9 @@ dm_status check_grid(dm_ctx* ctx, const dm_grid* g) {
         if (!(g->h[a] > 0) || !std::isfinite(g->h[a])) return fail(ctx, DM_ERR_ARG, "grid.h[%d] must be > 0", a);
         if (!std::isfinite(g->origin[a])) return fail(ctx, DM_ERR_ARG, "grid.origin is not finite");
     }
+    // half-spectrum indices are 32-bit
+    if ((int64_t)g->n[0] * g->n[1] * (g->n[2] / 2 + 1) >= ((int64_t)1 << 31))
+        return fail(ctx, DM_ERR_UNSUPPORTED, "grid of %d x %d x %d: half spectrum too large", g->n[0], g->n[1], g->n[2]);
     return DM_OK;
 }
 

@@ -337,6 +337,9 @@ cudaError_t launch_c2r(const Cx<R>* spec_in, Cx<R>* work, R* out, int Nx, int Ny
                        cudaStream_t st);
 template <class R>
 cudaError_t launch_r2c(const R* in, Cx<R>* spec_out, int Nx, int Ny, int Nz, const FFTAxis* ax, cudaStream_t st);
+// Axis lengths the FFT takes: 1..FFT_MAX_N with prime factors 2, 3, 5, 7, 11, 13 (the shared memory of a
+// pass, fft_smem_bytes, also has to fit the device: FP64 lines up to 2048).
+constexpr int FFT_MAX_N = 4096;
 bool fft_factor(int N, FFTAxis& a);
 size_t fft_smem_bytes(int N, int elem_bytes);
 

@@ -38,6 +38,76 @@ __device__ __forceinline__ void dft4(Cx<R>* v, int dir) {
     v[3] = {d02.x - wd.x, d02.y - wd.y};
 }
 
+// cos(2 pi k / P) (sine = false) or sin(2 pi k / P) (sine = true) for the odd primes P = 7, 11, 13 and
+// k = 1 .. (P - 1) / 2 (the rest follow by symmetry); the arguments are compile-time constants where
+// dft_prime uses it, so each call folds to a literal.
+__host__ __device__ constexpr double prime_root(int P, int k, bool sine) {
+    if (P == 7) {
+        switch (k) {
+            case 1: return sine ? 0.78183148246802980363 : 0.62348980185873359439;
+            case 2: return sine ? 0.97492791218182361934 : -0.22252093395631433737;
+            case 3: return sine ? 0.43388373911755823142 : -0.90096886790241903498;
+        }
+    }
+    if (P == 11) {
+        switch (k) {
+            case 1: return sine ? 0.54064081745559755543 : 0.84125353283118120551;
+            case 2: return sine ? 0.90963199535451833011 : 0.41541501300188643508;
+            case 3: return sine ? 0.98982144188093279524 : -0.14231483827328500480;
+            case 4: return sine ? 0.75574957435425826890 : -0.65486073394528498959;
+            case 5: return sine ? 0.28173255684142967104 : -0.95949297361449736865;
+        }
+    }
+    if (P == 13) {
+        switch (k) {
+            case 1: return sine ? 0.46472317204376850652 : 0.88545602565320991051;
+            case 2: return sine ? 0.82298386589365635224 : 0.56806474673115592289;
+            case 3: return sine ? 0.99270887409805397272 : 0.12053668025532300601;
+            case 4: return sine ? 0.93501624268541483342 : -0.35460488704253545489;
+            case 5: return sine ? 0.66312265824079519305 : -0.74851074817110119231;
+            case 6: return sine ? 0.23931566428755768339 : -0.97094181742605201180;
+        }
+    }
+    return sine ? 0.0 : 1.0;
+}
+
+// Direct P-point DFT for an odd prime P, y[m] = sum_q v[q] w^(q m) with w = exp(dir 2 pi i / P): the
+// inputs are paired as s_q = v[q] + v[P-q], d_q = v[q] - v[P-q] (q = 1 .. (P-1)/2), so that
+// y[m] = v[0] + sum_q (s_q cos(2 pi q m / P) + dir i d_q sin(2 pi q m / P)).
+template <class R, int P>
+__device__ __forceinline__ void dft_prime(Cx<R>* v, int dir) {
+    constexpr int H = (P - 1) / 2;
+    Cx<R> sq[H + 1], dq[H + 1];
+    Cx<R> y0 = v[0];
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+        sq[q] = {v[q].x + v[P - q].x, v[q].y + v[P - q].y};
+        dq[q] = {v[q].x - v[P - q].x, v[q].y - v[P - q].y};
+        y0.x += sq[q].x;
+        y0.y += sq[q].y;
+    }
+    Cx<R> y[P];
+    y[0] = y0;
+#pragma unroll
+    for (int m = 1; m < P; ++m) {
+        R ax = v[0].x, ay = v[0].y;
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            const int k = (q * m) % P;
+            const R c = (R)(k <= H ? prime_root(P, k, false) : prime_root(P, P - k, false));
+            const R sn = (R)(k <= H ? prime_root(P, k, true) : -prime_root(P, P - k, true)) * (R)dir;
+            ax += sq[q].x * c - dq[q].y * sn;
+            ay += sq[q].y * c + dq[q].x * sn;
+        }
+        y[m] = {ax, ay};
+    }
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = y[m];
+}
+
+// Largest radix a stage may take (fft_factor's radices: 2, 3, 4, 5, 7, 11, 13; 8 in the power-of-two path).
+constexpr int MAX_RADIX = 13;
+
 // y[m] = sum_q v[q] exp(dir 2 pi i q m / r), in place.
 template <class R>
 __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
@@ -73,6 +143,12 @@ __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
         v[6] = {e[2].x - t2.x, e[2].y - t2.y};
         v[3] = {e[3].x + t3.x, e[3].y + t3.y};
         v[7] = {e[3].x - t3.x, e[3].y - t3.y};
+    } else if (r == 7) {
+        dft_prime<R, 7>(v, dir);
+    } else if (r == 11) {
+        dft_prime<R, 11>(v, dir);
+    } else if (r == 13) {
+        dft_prime<R, 13>(v, dir);
     } else {  // r == 5: direct 5-point DFT
         const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
         const R s1 = (R)0.95105651629515357212 * (R)dir, s2 = (R)0.58778525229247312917 * (R)dir;
@@ -114,19 +190,19 @@ __device__ Cx<R>* fft_lines(Cx<R>* a, Cx<R>* b, const FFTAxis ax, int LS, int nl
         for (int w = threadIdx.x; w < nb * nl; w += blockDim.x) {
             const int line = w % nl, j = w / nl;
             const int k = j % Ns;
-            Cx<R> v[5];
+            Cx<R> v[MAX_RADIX];
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
+            for (int q = 0; q < MAX_RADIX; ++q)
                 if (q < r) v[q] = a[(j + q * nb) * LS + line];
             if (Ns > 1) {
 #pragma unroll
-                for (int q = 1; q < 5; ++q)
+                for (int q = 1; q < MAX_RADIX; ++q)
                     if (q < r) v[q] = cmul(v[q], twiddle(tw, q * k * tstride, dir));
             }
             small_dft(v, r, dir);
             const int base = (j / Ns) * Ns * r + k;
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
+            for (int q = 0; q < MAX_RADIX; ++q)
                 if (q < r) b[(base + q * Ns) * LS + line] = v[q];
         }
         __syncthreads();
@@ -341,11 +417,11 @@ bool fft_factor(int N, FFTAxis& a) {
     a.N = N;
     a.nf = 0;
     int n = N;
-    if (N < 1 || N > 1024) return false;
+    if (N < 1 || N > FFT_MAX_N) return false;
     while (n % 4 == 0 && a.nf < 16) { a.radix[a.nf++] = 4; n /= 4; }
     while (n % 2 == 0 && a.nf < 16) { a.radix[a.nf++] = 2; n /= 2; }
-    while (n % 3 == 0 && a.nf < 16) { a.radix[a.nf++] = 3; n /= 3; }
-    while (n % 5 == 0 && a.nf < 16) { a.radix[a.nf++] = 5; n /= 5; }
+    for (const int p : {3, 5, 7, 11, 13})
+        while (n % p == 0 && a.nf < 16) { a.radix[a.nf++] = p; n /= p; }
     return n == 1;
 }
 
@@ -392,6 +468,8 @@ cudaError_t pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, i
         case 256: return run_pass<R, 256>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         case 512: return run_pass<R, 512>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         case 1024: return run_pass<R, 1024>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 2048: return run_pass<R, 2048>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        case 4096: return run_pass<R, 4096>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         default: return run_pass<R, 0>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
     }
 }
@@ -431,6 +509,8 @@ cudaError_t launch_fft_batch(int kind, int N, const FFTJob* jobs, const int* off
         case 256: return run_batch_pass<256>(kind, jobs, offsets, nj, total, N, dir, st);
         case 512: return run_batch_pass<512>(kind, jobs, offsets, nj, total, N, dir, st);
         case 1024: return run_batch_pass<1024>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 2048: return run_batch_pass<2048>(kind, jobs, offsets, nj, total, N, dir, st);
+        case 4096: return run_batch_pass<4096>(kind, jobs, offsets, nj, total, N, dir, st);
         default: return run_batch_pass<0>(kind, jobs, offsets, nj, total, N, dir, st);
     }
 }

@@ -964,6 +964,7 @@ dm_status validate_job(const dm_job* j) {
         FFTAxis ax;
         if (!fft_factor(j->grid.n[a], ax)) return DM_ERR_UNSUPPORTED;
     }
+    if ((int64_t)j->grid.n[0] * j->grid.n[1] * (j->grid.n[2] / 2 + 1) >= ((int64_t)1 << 31)) return DM_ERR_UNSUPPORTED;
     for (int64_t i = 0; i < 3 * j->n_t; ++i)
         if (j->F[i] < 0 || j->F[i] >= j->n_v) return DM_ERR_ARG;
     for (int64_t i = 0; i < 3 * j->n_v; ++i)

@@ -117,7 +117,8 @@ def test_meshft_adjoint_matches_oracle(label, prec, r64, r32):
     assert rel(dV, ref) < (1e-10 if prec == "fp64" else 1e-4)
 
 
-@pytest.mark.parametrize("n", [(16, 16, 16), (12, 10, 9), (8, 6, 15), (32, 24, 20), (1, 4, 8), (96, 8, 6)])
+@pytest.mark.parametrize("n", [(16, 16, 16), (12, 10, 9), (8, 6, 15), (32, 24, 20), (1, 4, 8), (96, 8, 6),
+                               (14, 11, 26), (7, 13, 22), (2048, 2, 4)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_fft_matches_direct_definition(n, prec, r64, r32):
     r = r64 if prec == "fp64" else r32
@@ -133,6 +134,25 @@ def test_fft_matches_direct_definition(n, prec, r64, r32):
     refG = np.fft.fftn(R)[nvec[:, 0] % n[0], nvec[:, 1] % n[1], nvec[:, 2] % n[2]]
     spec = r.r2c(grid, torch.as_tensor(R).cuda()).cpu().numpy().ravel()
     assert rel(spec, refG) < tol
+
+
+def test_fft_longest_axes_and_refused_lengths(r64, r32):
+    """An FP32 axis of 4096 (the longest; the FP64 lines of that length do not fit in shared memory and are
+    refused), and a length with the prime factor 17 (refused by both paths)."""
+    from paper_2303_10440_b300 import DeltaMicError
+
+    n = (2, 4096, 3)
+    grid = synth.Grid(n=n, h=(1, 1, 1))
+    X = synth.random_half_spectrum(n, seed=6)
+    nvec, c = oracle.half_spectrum(n)
+    ref = oracle.spectrum_to_image(X.ravel(), nvec, c, grid) * np.prod(grid.L)
+    assert rel(r32.c2r(grid, torch.as_tensor(X).cuda()).cpu().numpy(), ref) < 2e-6
+    with pytest.raises(DeltaMicError, match="UNSUPPORTED"):
+        r64.c2r(grid, torch.as_tensor(X).cuda())
+    bad = synth.Grid(n=(17, 4, 4), h=(1, 1, 1))
+    for r in (r64, r32):
+        with pytest.raises(DeltaMicError, match="UNSUPPORTED"):
+            r.r2c(bad, torch.zeros(bad.n, dtype=r.real).cuda())
 
 
 @pytest.mark.parametrize("tau", [1e-3, 1e-2, 0.3])
@@ -272,7 +292,7 @@ def test_argument_errors_are_reported(r32):
     with pytest.raises(DeltaMicError, match="DM_ERR_ARG"):
         r32.render(_cuda(V), _cuda(F), grid, synth.Psf(sigma=(1.0, -1.0, 1.0)))
     with pytest.raises(DeltaMicError, match="DM_ERR_UNSUPPORTED"):
-        r32.render(_cuda(V), _cuda(F), synth.Grid(n=(14, 14, 14), h=(1, 1, 1)), psf)
+        r32.render(_cuda(V), _cuda(F), synth.Grid(n=(17, 17, 17), h=(1, 1, 1)), psf)
     # an out-of-range index in device memory is caught by the kernels' bounds checks
     with pytest.raises(DeltaMicError, match="DM_ERR_ARG"):
         r32.loss_and_grad(_cuda(V), _cuda(bad), grid, psf, torch.as_tensor(T), "mse")

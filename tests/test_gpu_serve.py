@@ -152,7 +152,7 @@ def test_invalid_jobs_are_refused(setup):
     bad["F"] = F
     with pytest.raises(RuntimeError, match="DM_ERR_ARG"):
         s.submit(**bad)
-    bad = dict(jobs[1], grid=synth.Grid(n=(14, 14, 14), h=(1, 1, 1)))
+    bad = dict(jobs[1], grid=synth.Grid(n=(17, 17, 17), h=(1, 1, 1)))
     with pytest.raises(RuntimeError, match="DM_ERR_UNSUPPORTED"):
         s.submit(**bad)
     n_t = jobs[1]["F"].shape[0]
