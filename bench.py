@@ -89,7 +89,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 path's step beside the FP32 one")
-    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "stagger", "robust", "fft", "scaling", "mufu"],
+    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "serve-batch", "stagger", "robust", "fft",
+                                      "scaling", "mufu"],
                    default="step",
                    help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
                    "serve-c5: Poisson stream of serving requests; stagger: the staggered shape/PSF fit "
@@ -101,6 +102,7 @@ def parse():
     p.add_argument("--rounds", type=int, default=4, help="staggered rounds in the stagger mode")
     p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 100)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
+    p.add_argument("--graphs", type=int, default=1, help="serve-batch: replay iterations as CUDA graphs (0: direct)")
     p.add_argument("--legs", default="fifo,shortest,sequential",
                    help="serve modes: which legs to run (fifo, shortest, sequential one-at-a-time FP32)")
     p.add_argument("--lr-decay", type=float, default=0.998, help="per-step learning-rate factor in the robust mode")
@@ -857,6 +859,31 @@ def run_serve_mode(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve_batch_mode(args):
+    """The serving leg's 16 small requests (levels 2-3, 32-64^3, 10 Adam steps) submitted together to the fit
+    server; prints the server's statistics (engine time per iteration). With --graphs 0 every kernel launches
+    directly, for a launch list."""
+    import torch
+
+    from paper_2303_10440_b300 import Renderer
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32 = Renderer("fp32")
+    jobs = serving_jobs(r32, 16, 5, (2, 3), (32, 48, 64), args.fit_steps or 10)
+    torch.cuda.synchronize()
+    srv = FitServer(device=0, max_jobs=32, graphs=bool(args.graphs))
+    t0 = srv.clock()
+    ids = [srv.submit(**j) for j in jobs]
+    for i in ids:
+        srv.wait(i, timeout=600)
+    span = srv.clock() - t0
+    st = srv.stats()
+    srv.shutdown()
+    print(json.dumps({"mode": "serve-batch", "jobs": len(jobs), "span_s": span,
+                      **{k: st[k] for k in ("iterations", "busy_s", "job_steps", "peak_active", "graph_replays")}}),
+          flush=True)
+
+
 def run_stagger_mode(args):
     """Times the staggered fit: per shape step (narrow band, large-steps update with its two smoothing
     solves) and per PSF step (whole half spectrum, no vertex adjoint), with the library's stage split."""
@@ -1161,6 +1188,9 @@ def main():
         return
     if args.mode == "stagger":
         run_stagger_mode(args)
+        return
+    if args.mode == "serve-batch":
+        run_serve_batch_mode(args)
         return
     if args.mode != "step":
         run_serve_mode(args)
