@@ -204,6 +204,30 @@ def test_render_matches_oracle(mode, tau, prec, r64, r32):
     assert rel(img, ref) < (1e-10 if prec == "fp64" else 1e-4)
 
 
+@pytest.mark.parametrize("mode", ["surface", "volume"])
+@pytest.mark.parametrize("nz", [24, 32, 33])
+def test_band_that_holds_all_of_the_half_spectrum(mode, nz, r32):
+    """A band that holds every frequency of H (tau far below every h_hat of the grid) gives bitwise the image of
+    tau = 0 (the same frequencies in the same order through the band list), which matches the oracle; and the
+    forward on the explicit list of H (dm_meshft) matches the oracle's spectrum. Even and odd Nz."""
+    grid = synth.Grid(n=(18, 20, nz), h=(1.0, 1.1, 1.2), origin=(0.3, -0.2, 0.1))
+    V, F = synth.sh_deformed_sphere(2, 0.27 * float(min(grid.L)), grid.center, lmax=4, coef_sigma=0.5, seed=21)
+    if mode == "volume":
+        V, F = synth.sh_deformed_sphere(2, 0.27 * float(min(grid.L)), grid.center, lmax=3, coef_sigma=0.3, seed=22)
+    psf0 = synth.Psf(sigma=(0.7, 0.8, 1.1), band_tau=0.0)
+    psf1 = synth.Psf(sigma=(0.7, 0.8, 1.1), band_tau=1e-9)  # every h_hat of this grid is far above 1e-9
+    a = r32.render(_cuda(V), _cuda(F), grid, psf0, label=mode)
+    b = r32.render(_cuda(V), _cuda(F), grid, psf1, label=mode)
+    assert torch.equal(a, b)
+    ref = oracle.render(V, F, grid, psf0, mode)["image"]
+    assert rel(a.cpu().numpy(), ref) < 1e-5
+    nvec, _ = oracle.half_spectrum(grid.n)
+    S_list = r32.meshft(_cuda(V), _cuda(F), grid, _cuda(nvec.astype(np.int32)), label=mode).cpu().numpy()
+    S_ref = oracle.mesh_ft(V - np.asarray(grid.origin), F, oracle.wavevectors(nvec, grid), mode,
+                           c0=0.5 * np.asarray(grid.L) if mode == "volume" else None)
+    assert rel(S_list, S_ref) < 1e-5
+
+
 @pytest.mark.parametrize("kind", ["mse", "l2", "weighted"])
 @pytest.mark.parametrize("mode", ["surface", "volume"])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
