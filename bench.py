@@ -89,8 +89,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 path's step beside the FP32 one")
-    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "serve-batch", "stagger", "robust", "fft",
-                                      "scaling", "mufu"],
+    p.add_argument("--mode", choices=["step", "serve-c4", "serve-c5", "serve-batch", "serve-budget", "stagger", "robust",
+                                      "fft", "scaling", "mufu"],
                    default="step",
                    help="step: the headline fit-step benchmark; serve-c4: 32-cell tissue through the fit server; "
                    "serve-c5: Poisson stream of serving requests; stagger: the staggered shape/PSF fit "
@@ -886,6 +886,28 @@ def run_serve_batch_mode(args):
           flush=True)
 
 
+def run_serve_budget_mode(args):
+    """The serving leg's 16 small requests at 500/s: served FIFO, served shortest-first at per-iteration term
+    budgets of 1e8-3e9, and one at a time (every leg open loop, observed)."""
+    import torch
+
+    from paper_2303_10440_b300 import Renderer
+
+    dev = torch.device("cuda", 0)
+    r32 = Renderer("fp32")
+    jobs = serving_jobs(r32, 16, 5, (2, 3), (32, 48, 64), args.fit_steps or 10)
+    rng = np.random.default_rng(6)
+    arr = np.cumsum(rng.exponential(1.0 / 500, size=16))
+    arr -= arr[0]
+    _served_run(jobs, arr, dev)  # warm-up
+    out = {"mode": "serve-budget", "fifo": _served_run(jobs, arr, dev)}
+    for bt in (1e8, 3e8, 1e9, 3e9):
+        out[f"shortest_{bt:g}"] = _served_run(jobs, arr, dev, policy="shortest", batch_terms=bt)
+    lat, span = _one_at_a_time_run(r32, jobs, arr, dev)
+    out["sequential"] = _stats(lat, span, 16)
+    print(json.dumps(out), flush=True)
+
+
 def run_stagger_mode(args):
     """Times the staggered fit: per shape step (narrow band, large-steps update with its two smoothing
     solves) and per PSF step (whole half spectrum, no vertex adjoint), with the library's stage split."""
@@ -1193,6 +1215,9 @@ def main():
         return
     if args.mode == "serve-batch":
         run_serve_batch_mode(args)
+        return
+    if args.mode == "serve-budget":
+        run_serve_budget_mode(args)
         return
     if args.mode != "step":
         run_serve_mode(args)
