@@ -103,6 +103,9 @@ def parse():
     p.add_argument("--fit-steps", type=int, default=0, help="Adam steps per job in the serve modes (0: 20 / 100)")
     p.add_argument("--jobs", type=int, default=12, help="requests in serve-c5")
     p.add_argument("--graphs", type=int, default=1, help="serve-batch: replay iterations as CUDA graphs (0: direct)")
+    p.add_argument("--capacity-fits-per-s", type=float, default=0.0,
+                   help="serve-c5: the saturated throughput the capacity fractions refer to (0: the best served "
+                   "throughput measured at --rates in the same run)")
     p.add_argument("--legs", default="fifo,shortest,sequential",
                    help="serve modes: which legs to run (fifo, shortest, sequential one-at-a-time FP32)")
     p.add_argument("--lr-decay", type=float, default=0.998, help="per-step learning-rate factor in the robust mode")
@@ -808,7 +811,8 @@ def run_serve_mode(args):
                  (float(x) for x in args.rates.split(",") if x)}
     legs_wanted = set(args.legs.split(","))
     total_terms = sum(_job_terms(j) for j in jobs)
-    _one_at_a_time_run(r32, jobs[:1], [0.0], dev)  # warm-up
+    smallest = min(range(len(jobs)), key=lambda k: _job_terms(jobs[k]))
+    _one_at_a_time_run(r32, [jobs[smallest]], [0.0], dev)  # warm-up (modules, FFT tables)
     fp64_durs, fp64_rate = _fp64_alone(jobs, dev)
     out = {"metric": "served fits/s and p50/p99 latency vs one-at-a-time FP32 and plain FP64", "mode": args.mode,
            "workload": workload, "n_jobs": len(jobs), "total_terms": total_terms,
@@ -845,17 +849,23 @@ def run_serve_mode(args):
             e["arrival_rate_per_s"] = rate
         return e
 
+    def report(name, entry):
+        # one line per finished arrival schedule, so that a run cut short keeps the legs it finished
+        print(json.dumps({"partial": name, **entry}), flush=True)
+
     for name, arr in rates.items():
         out["results"][name] = legs(arr)
+        report(name, out["results"][name])
     fracs = [float(x) for x in args.capacity_fracs.split(",") if x] if args.mode == "serve-c5" else []
     if fracs:
-        # capacity = the best served throughput seen at the saturating rates above
-        cap = max(max(e.get("served_fp32", {}).get("fits_per_s", 0.0),
-                      e.get("served_fp32_shortest_first", {}).get("fits_per_s", 0.0))
-                  for e in out["results"].values())
+        # capacity = the best served throughput seen at the saturating rates above, or the one given
+        cap = args.capacity_fits_per_s or max(
+            max(e.get("served_fp32", {}).get("fits_per_s", 0.0),
+                e.get("served_fp32_shortest_first", {}).get("fits_per_s", 0.0)) for e in out["results"].values())
         out["capacity_fits_per_s"] = cap
         for f in fracs:
             out["results"][f"{f:g}x capacity"] = legs(_poisson_arrivals(f * cap, len(jobs)), rate=f * cap)
+            report(f"{f:g}x capacity", out["results"][f"{f:g}x capacity"])
     if first_served is not None:
         out["per_job_error_fp32_vs_fp64_sampled"] = _sampled_spectrum_errors(jobs, first_served, dev)
     print(json.dumps(out), flush=True)
