@@ -187,7 +187,8 @@ dm_status dm_meshft_adjoint(dm_ctx* ctx, const dm_mesh* mesh, const dm_grid* gri
                             int64_t M, const void* G, double* dV_out, void* stream);
 
 /* Unnormalised inverse real 3D DFT: out_j = sum_{n in H} c_n Re(spec_n exp(2 pi i n.j/N)).
- * spec: [Nx][Ny][Nz/2+1] complex, image: [Nx][Ny][Nz] real (double or float). */
+ * spec: [Nx][Ny][Nz/2+1] complex, image: [Nx][Ny][Nz] real (double or float). spec is only read; a
+ * device spectrum that does not overlap the image is read in place, any other is copied first. */
 dm_status dm_c2r(dm_ctx* ctx, const dm_grid* grid, const void* spec, void* image, void* stream);
 /* Unnormalised forward real 3D DFT onto H: spec_n = sum_j image_j exp(-2 pi i n.j/N). */
 dm_status dm_r2c(dm_ctx* ctx, const dm_grid* grid, const void* image, void* spec, void* stream);

@@ -521,13 +521,21 @@ static dm_status fft_call(dm_ctx* ctx, const dm_grid* grid, const void* in, void
     char* img = A.take<char>(N * R);
     const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
     if (inverse) {
-        CK(cudaMemcpyAsync(spec, in, nH * 2 * R, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        // a device spectrum is read in place by the first pass (and left unchanged) unless it overlaps the
+        // image; a host one, or an overlapping one, is copied into the workspace first
+        const char* ib = (const char*)in;
+        const char* ob = (const char*)out;
+        const bool overlap = out_dev && ib < ob + N * R && ob < ib + nH * 2 * R;
+        const bool direct = in_dev && !overlap;
+        if (!direct)
+            CK(cudaMemcpyAsync(spec, in, nH * 2 * R, in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        const void* sin = direct ? in : spec;
         void* dst = out_dev ? out : img;
         if (f64)
-            LAUNCH(3, launch_c2r<double>((Cx<double>*)spec, (Cx<double>*)spec, (double*)dst, grid->n[0], grid->n[1],
-                                         grid->n[2], ax, st));
+            LAUNCH(3, launch_c2r<double>((const Cx<double>*)sin, (Cx<double>*)spec, (double*)dst, grid->n[0],
+                                         grid->n[1], grid->n[2], ax, st));
         else
-            LAUNCH(3, launch_c2r<float>((Cx<float>*)spec, (Cx<float>*)spec, (float*)dst, grid->n[0], grid->n[1],
+            LAUNCH(3, launch_c2r<float>((const Cx<float>*)sin, (Cx<float>*)spec, (float*)dst, grid->n[0], grid->n[1],
                                         grid->n[2], ax, st));
         if (!out_dev) {
             CK(cudaMemcpyAsync(out, img, N * R, cudaMemcpyDeviceToHost, st));

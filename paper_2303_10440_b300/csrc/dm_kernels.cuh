@@ -325,7 +325,7 @@ cudaError_t launch_adam_dev_step(double* p, const double* g, double* m, double* 
 // hist[*d_step - step0 - 1] = *d_loss; ++*d_step (one thread)
 cudaError_t launch_fit_tick(double* hist, const double* d_loss, int64_t* d_step, int64_t step0, cudaStream_t st);
 
-// FFT (own radix-2/3/4/5 Stockham in shared memory).
+// FFT (own: FP32 power-of-two lines in registers, otherwise a mixed-radix Stockham in shared memory).
 struct FFTAxis {
     int N;
     int nf;

@@ -1,15 +1,19 @@
 // 3D real <-> half-spectrum DFTs for the image stage (the inverse transform that
 // turns I_hat = u_hat h_hat into voxels, Eq. 1, and its adjoint).
 //
-// Each pass transforms every line along one axis. A block stages a batch of lines
-// into shared memory (coalesced along the contiguous axis), runs a mixed-radix
-// (2, 3, 4, 5) Stockham autosort FFT there (ping-pong buffers, one __syncthreads
-// per radix stage), and writes the batch back. The z pass of the inverse builds
-// the Hermitian-completed line (real parts of the self-conjugate n_z = 0 and
-// Nyquist coefficients) before a complex inverse transform; the z pass of the
-// forward keeps the first Nz/2+1 outputs. All transforms are unnormalised.
+// Each pass transforms every line along one axis. FP32 lines of a power-of-two
+// length 16 .. 1024 are held in registers (a four-step split N = N1 N2 with one
+// exchange through shared memory; see "FP32 power-of-two lines in registers").
+// Other lengths, and FP64, stage a batch of lines in shared memory (coalesced
+// along the contiguous axis), run a Stockham autosort FFT there (radices 2, 3, 4,
+// 5, 7, 11, 13, or 8 for compile-time powers of two; ping-pong buffers, one
+// __syncthreads per radix stage), and write the batch back. The z pass of the
+// inverse reads the Hermitian-completed line (real parts of the self-conjugate
+// n_z = 0 and Nyquist coefficients) for a complex inverse transform; the z pass
+// of the forward keeps the first Nz/2+1 outputs. All transforms are unnormalised.
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 
 #include "dm_kernels.cuh"
 
@@ -258,8 +262,8 @@ __device__ __forceinline__ Cx<R>* transform_lines(Cx<R>* a, Cx<R>* b, const FFTA
 // Complex transform of all lines along an axis with element stride `inner`:
 // element (o, k, c) at o*N*inner + k*inner + c, lines indexed by (o, c).
 template <class R, int NC>
-__device__ __forceinline__ void k_fft_strided_body(Cx<R>* data, const FFTAxis ax, int64_t inner,
-                                                             int dir, int64_t blk, int64_t nblk) {
+__device__ __forceinline__ void k_fft_strided_body(const Cx<R>* src, Cx<R>* dst, const FFTAxis ax, int64_t inner,
+                                                   int dir, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N = NC ? NC : ax.N;
     const int nl = lines_per_block(N);
@@ -270,22 +274,24 @@ __device__ __forceinline__ void k_fft_strided_body(Cx<R>* data, const FFTAxis ax
     const int64_t o = blk / col_blocks;
     const int64_t c0 = (blk % col_blocks) * nl;
     const int ncols = (int)min((int64_t)nl, inner - c0);
-    Cx<R>* base = data + o * N * inner + c0;
+    // every read of the block's lines precedes the barrier and every write follows it, so src == dst is fine
+    const Cx<R>* sbase = src + o * N * inner + c0;
+    Cx<R>* dbase = dst + o * N * inner + c0;
     for (int i = threadIdx.x; i < N * nl; i += blockDim.x) {
         const int c = i % nl, k = i / nl;
-        a[k * LS + c] = c < ncols ? base[(int64_t)k * inner + c] : Cx<R>{0, 0};
+        a[k * LS + c] = c < ncols ? sbase[(int64_t)k * inner + c] : Cx<R>{0, 0};
     }
     __syncthreads();
     Cx<R>* res = transform_lines<R, NC>(a, b, ax, LS, nl, dir);
     for (int i = threadIdx.x; i < N * nl; i += blockDim.x) {
         const int c = i % nl, k = i / nl;
-        if (c < ncols) base[(int64_t)k * inner + c] = res[k * LS + c];
+        if (c < ncols) dbase[(int64_t)k * inner + c] = res[k * LS + c];
     }
 }
 template <class R, int NC>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(Cx<R>* data, const FFTAxis ax, int64_t inner,
-                                                             int dir) {
-    k_fft_strided_body<R, NC>(data, ax, inner, dir, (int64_t)blockIdx.x, (int64_t)gridDim.x);
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_strided(const Cx<R>* src, Cx<R>* dst, const FFTAxis ax,
+                                                             int64_t inner, int dir) {
+    k_fft_strided_body<R, NC>(src, dst, ax, inner, dir, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
 // Inverse z pass: lines of Nzh complex (contiguous) -> Nz reals (contiguous).
@@ -352,6 +358,264 @@ __global__ void __launch_bounds__(FFT_THREADS) k_fft_z_r2c(const R* in, Cx<R>* s
     k_fft_z_r2c_body<R, NC>(in, spec, ax, Nzh_, nlines, (int64_t)blockIdx.x, (int64_t)gridDim.x);
 }
 
+// ---------------------------------------------------------------- FP32 power-of-two lines in registers
+// For N = 16 .. 1024 the FP32 passes split N = N1 N2 (N2 = 2^floor(log2(N) / 2), N1 = N / N2, so N1 is N2
+// or 2 N2) and keep each line in the registers of T = N2 threads. With k = k2 + N2 k1 and m = m1 + N1 m2,
+//   X[m1 + N1 m2] = sum_k2 w_N2^(k2 m2) [ w_N^(k2 m1) sum_k1 x[k2 + N2 k1] w_N1^(k1 m1) ]
+// (w_M = exp(dir 2 pi i / M); the four-step factorisation of the DFT): thread k2 loads x[k2 + N2 k1]
+// (k1 < N1) from global memory, runs the N1-point DFT in registers and applies the twiddles w_N^(k2 m1);
+// one exchange through shared memory gives thread t the values of m1 = t, t + T, .. for its N2-point
+// DFTs, whose outputs go straight to global memory. One shared-memory round trip per pass instead of
+// one per radix stage, and no staging copy of the lines.
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+__host__ __device__ constexpr bool p2_reg(int N) { return N >= 16 && N <= 1024 && (N & (N - 1)) == 0; }
+
+template <int N>
+struct P2 {
+    static constexpr int N2 = 1 << (ilog2c(N) / 2);
+    static constexpr int N1 = N / N2;
+    static constexpr int T = N2;                // threads per line
+    static constexpr int NL = FFT_THREADS / T;  // lines per block
+    // Strided passes (consecutive lanes take consecutive lines, so that the global accesses coalesce):
+    // value (k2, m1) of line c at k2 * ROW + m1 * NL + c. z passes (consecutive lanes run along a line):
+    // at c * LINE + k2 * RS + m1. The paddings make both sides of the exchange free of bank conflicts
+    // (each half-warp's 8-byte accesses fall on 16 distinct bank pairs).
+    static constexpr int ROW = N1 * NL + (NL < 16 ? 8 : 0);
+    static constexpr int RS = N1 + 1;
+    static constexpr int LINE = N2 * RS;
+    static constexpr size_t SMEM_STRIDED = (size_t)N2 * ROW * sizeof(Cx<float>);
+    static constexpr size_t SMEM_Z = (size_t)NL * LINE * sizeof(Cx<float>);
+};
+int p2_lines_per_block(int N) { return FFT_THREADS / (1 << (ilog2c(N) / 2)); }
+
+// cos(j pi / 16) for j = 0 .. 8: the first octant of the 32nd roots of unity.
+__host__ __device__ constexpr float cos_pi16(int j) {
+    switch (j) {
+        case 0: return 1.0f;
+        case 1: return 0.98078528040323044913f;
+        case 2: return 0.92387953251128675613f;
+        case 3: return 0.83146961230254523708f;
+        case 4: return 0.70710678118654752440f;
+        case 5: return 0.55557023301960222474f;
+        case 6: return 0.38268343236508977173f;
+        case 7: return 0.19509032201612826785f;
+        default: return 0.0f;
+    }
+}
+// cos(k pi / 16) for any k in 0 .. 31, by the symmetries of the cosine.
+__host__ __device__ constexpr float cos_k32(int k) {
+    return k <= 8 ? cos_pi16(k) : k <= 16 ? -cos_pi16(16 - k) : k <= 24 ? -cos_pi16(k - 16) : cos_pi16(32 - k);
+}
+// a exp(DIR 2 pi i k / 32) for 0 <= k < 32 (k is a constant once the caller's loops are unrolled; the
+// multiples of a quarter turn are exact).
+template <int DIR>
+__device__ __forceinline__ Cx<float> rot32(Cx<float> a, int k) {
+    if (k == 0) return a;
+    if (k == 8) return DIR > 0 ? Cx<float>{-a.y, a.x} : Cx<float>{a.y, -a.x};
+    if (k == 16) return {-a.x, -a.y};
+    if (k == 24) return DIR > 0 ? Cx<float>{a.y, -a.x} : Cx<float>{-a.y, a.x};
+    const Cx<float> w = {cos_k32(k), (float)DIR * cos_k32((40 - k) % 32)};  // sin(x) = cos(pi/2 - x)
+    return cmul(a, w);
+}
+
+__host__ __device__ constexpr int bit_reverse(int i, int bits) {
+    int r = 0;
+    for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+    return r;
+}
+
+// y[m] = sum_q v[q] exp(DIR 2 pi i q m / M) in place, M a power of two up to 32: radix-2 decimation in
+// time on the bit-reversed inputs, every index and twiddle a constant after unrolling.
+template <int M, int DIR>
+__device__ __forceinline__ void dft_reg(Cx<float>* v) {
+    constexpr int B = ilog2c(M);
+    static_assert((1 << B) == M && M <= 32, "dft_reg takes powers of two up to 32");
+    Cx<float> u[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) u[bit_reverse(i, B)] = v[i];
+#pragma unroll
+    for (int h = 1; h < M; h *= 2) {  // DFTs of length h combined into length 2h
+#pragma unroll
+        for (int s0 = 0; s0 < M; s0 += 2 * h) {
+#pragma unroll
+            for (int j = 0; j < h; ++j) {
+                const Cx<float> a = u[s0 + j], b = rot32<DIR>(u[s0 + j + h], j * (16 / h));
+                u[s0 + j] = {a.x + b.x, a.y + b.y};
+                u[s0 + j + h] = {a.x - b.x, a.y - b.y};
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = u[i];
+}
+
+// v[m] *= exp(DIR 2 pi i t m / N) for m < E (t E <= N), from the table tw[j] = exp(-2 pi i j / N): the
+// factors for m = 2^b are table values, the others products of those of m's binary digits.
+template <int E, int DIR>
+__device__ __forceinline__ void twiddle_pow(Cx<float>* v, int t, const Cx<float>* __restrict__ tw) {
+    constexpr int B = ilog2c(E);
+    Cx<float> p[B > 0 ? B : 1];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const Cx<float> w = tw[t << b];
+        p[b] = DIR > 0 ? Cx<float>{w.x, -w.y} : w;
+    }
+#pragma unroll
+    for (int m = 1; m < E; ++m) {
+        Cx<float> f = {1.f, 0.f};
+        bool first = true;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if ((m >> b) & 1) {
+                f = first ? p[b] : cmul(f, p[b]);
+                first = false;
+            }
+        }
+        v[m] = cmul(v[m], f);
+    }
+}
+
+// Complex pass over nlines lines of N elements with element stride `inner`: line L = o * inner + c
+// (o = L / inner) starts at o * N * inner + c. src == dst is allowed (all reads of a block's lines
+// precede its barrier, all writes follow it, and no two blocks share a line).
+template <int N, int DIR>
+__device__ __forceinline__ void p2_strided_body(const Cx<float>* src, Cx<float>* dst, int64_t inner, int64_t nlines,
+                                                const Cx<float>* __restrict__ tw, int64_t blk) {
+    using P = P2<N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<float>* Y = (Cx<float>*)smem_raw;
+    const int c = threadIdx.x % P::NL, t = threadIdx.x / P::NL;
+    const int64_t L = blk * P::NL + c;
+    const bool act = L < nlines;
+    const int64_t o = act ? L / inner : 0;
+    const int64_t off = act ? o * N * inner + (L - o * inner) : 0;
+    Cx<float> v[P::N1];
+#pragma unroll
+    for (int k1 = 0; k1 < P::N1; ++k1)
+        v[k1] = act ? src[off + (int64_t)(t + P::N2 * k1) * inner] : Cx<float>{0.f, 0.f};
+    dft_reg<P::N1, DIR>(v);
+    twiddle_pow<P::N1, DIR>(v, t, tw);
+#pragma unroll
+    for (int m1 = 0; m1 < P::N1; ++m1) Y[t * P::ROW + m1 * P::NL + c] = v[m1];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < P::N1 / P::N2; ++r) {
+        const int m1 = t + P::T * r;
+        Cx<float> u[P::N2];
+#pragma unroll
+        for (int k2 = 0; k2 < P::N2; ++k2) u[k2] = Y[k2 * P::ROW + m1 * P::NL + c];
+        dft_reg<P::N2, DIR>(u);
+        if (act) {
+#pragma unroll
+            for (int m2 = 0; m2 < P::N2; ++m2) dst[off + (int64_t)(m1 + P::N1 * m2) * inner] = u[m2];
+        }
+    }
+}
+
+// Inverse z pass: nlines lines of N/2 + 1 coefficients (contiguous) -> N reals; the Hermitian half
+// (k > N/2) is read as conj(X[N - k]), and the n_z = 0 and Nyquist coefficients count by their real parts.
+template <int N>
+__device__ __forceinline__ void p2_z_c2r_body(const Cx<float>* spec, float* out, int64_t nlines,
+                                              const Cx<float>* __restrict__ tw, int64_t blk) {
+    using P = P2<N>;
+    constexpr int H = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<float>* Y = (Cx<float>*)smem_raw;
+    const int t = threadIdx.x % P::T, c = threadIdx.x / P::T;
+    const int64_t L = blk * P::NL + c;
+    const bool act = L < nlines;
+    const Cx<float>* s = spec + (act ? L : 0) * (H + 1);
+    Cx<float> v[P::N1];
+#pragma unroll
+    for (int k1 = 0; k1 < P::N1; ++k1) {
+        const int k = t + P::N2 * k1;
+        Cx<float> x = {0.f, 0.f};
+        if (act) {
+            if (k <= H) {
+                x = s[k];
+                if (k == 0 || k == H) x.y = 0.f;
+            } else {
+                x = s[N - k];
+                x.y = -x.y;
+            }
+        }
+        v[k1] = x;
+    }
+    dft_reg<P::N1, 1>(v);
+    twiddle_pow<P::N1, 1>(v, t, tw);
+    Cx<float>* Yc = Y + c * P::LINE;
+#pragma unroll
+    for (int m1 = 0; m1 < P::N1; ++m1) Yc[t * P::RS + m1] = v[m1];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < P::N1 / P::N2; ++r) {
+        const int m1 = t + P::T * r;
+        Cx<float> u[P::N2];
+#pragma unroll
+        for (int k2 = 0; k2 < P::N2; ++k2) u[k2] = Yc[k2 * P::RS + m1];
+        dft_reg<P::N2, 1>(u);
+        if (act) {
+#pragma unroll
+            for (int m2 = 0; m2 < P::N2; ++m2) out[L * N + m1 + P::N1 * m2] = u[m2].x;
+        }
+    }
+}
+
+// Forward z pass: nlines lines of N reals (contiguous) -> the first N/2 + 1 coefficients.
+template <int N>
+__device__ __forceinline__ void p2_z_r2c_body(const float* in, Cx<float>* spec, int64_t nlines,
+                                              const Cx<float>* __restrict__ tw, int64_t blk) {
+    using P = P2<N>;
+    constexpr int H = N / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<float>* Y = (Cx<float>*)smem_raw;
+    const int t = threadIdx.x % P::T, c = threadIdx.x / P::T;
+    const int64_t L = blk * P::NL + c;
+    const bool act = L < nlines;
+    const float* s = in + (act ? L : 0) * N;
+    Cx<float> v[P::N1];
+#pragma unroll
+    for (int k1 = 0; k1 < P::N1; ++k1) v[k1] = {act ? s[t + P::N2 * k1] : 0.f, 0.f};
+    dft_reg<P::N1, -1>(v);
+    twiddle_pow<P::N1, -1>(v, t, tw);
+    Cx<float>* Yc = Y + c * P::LINE;
+#pragma unroll
+    for (int m1 = 0; m1 < P::N1; ++m1) Yc[t * P::RS + m1] = v[m1];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < P::N1 / P::N2; ++r) {
+        const int m1 = t + P::T * r;
+        Cx<float> u[P::N2];
+#pragma unroll
+        for (int k2 = 0; k2 < P::N2; ++k2) u[k2] = Yc[k2 * P::RS + m1];
+        dft_reg<P::N2, -1>(u);
+        if (act) {
+#pragma unroll
+            for (int m2 = 0; m2 < P::N2; ++m2) {
+                const int m = m1 + P::N1 * m2;
+                if (m <= H) spec[L * (H + 1) + m] = u[m2];
+            }
+        }
+    }
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(FFT_THREADS) k_p2_strided(const Cx<float>* src, Cx<float>* dst, int64_t inner,
+                                                            int64_t nlines, const Cx<float>* __restrict__ tw) {
+    p2_strided_body<N, DIR>(src, dst, inner, nlines, tw, (int64_t)blockIdx.x);
+}
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_p2_z_c2r(const Cx<float>* __restrict__ spec, float* __restrict__ out,
+                                                          int64_t nlines, const Cx<float>* __restrict__ tw) {
+    p2_z_c2r_body<N>(spec, out, nlines, tw, (int64_t)blockIdx.x);
+}
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) k_p2_z_r2c(const float* __restrict__ in, Cx<float>* __restrict__ spec,
+                                                          int64_t nlines, const Cx<float>* __restrict__ tw) {
+    p2_z_r2c_body<N>(in, spec, nlines, tw, (int64_t)blockIdx.x);
+}
+
 // Batched passes (fit server): the jobs of one line length in one launch; block b belongs to the
 // largest job j with offs[j] <= b, as its block b - offs[j] of its single-job grid.
 struct FFTBlock {
@@ -375,7 +639,7 @@ __global__ void __launch_bounds__(FFT_THREADS) kb_fft_strided(const FFTJob* __re
                                                               const int* __restrict__ offs, int nj, int dir) {
     const FFTBlock q = fft_block(offs, nj);
     const FFTJob& J = jobs[q.j];
-    k_fft_strided_body<R, NC>((Cx<R>*)J.dst, J.ax, J.inner, dir, q.b, q.nb);
+    k_fft_strided_body<R, NC>((const Cx<R>*)J.src, (Cx<R>*)J.dst, J.ax, J.inner, dir, q.b, q.nb);
 }
 template <class R, int NC>
 __global__ void __launch_bounds__(FFT_THREADS) kb_fft_z_c2r(const FFTJob* __restrict__ jobs,
@@ -390,6 +654,29 @@ __global__ void __launch_bounds__(FFT_THREADS) kb_fft_z_r2c(const FFTJob* __rest
     const FFTBlock q = fft_block(offs, nj);
     const FFTJob& J = jobs[q.j];
     k_fft_z_r2c_body<R, NC>((const R*)J.src, (Cx<R>*)J.dst, J.ax, J.Nzh, J.lines, q.b, q.nb);
+}
+
+template <int N, int DIR>
+__global__ void __launch_bounds__(FFT_THREADS) kb_p2_strided(const FFTJob* __restrict__ jobs,
+                                                             const int* __restrict__ offs, int nj) {
+    const FFTBlock q = fft_block(offs, nj);
+    const FFTJob& J = jobs[q.j];
+    p2_strided_body<N, DIR>((const Cx<float>*)J.src, (Cx<float>*)J.dst, J.inner, J.lines * J.inner,
+                            (const Cx<float>*)J.ax.tw, q.b);
+}
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) kb_p2_z_c2r(const FFTJob* __restrict__ jobs,
+                                                           const int* __restrict__ offs, int nj) {
+    const FFTBlock q = fft_block(offs, nj);
+    const FFTJob& J = jobs[q.j];
+    p2_z_c2r_body<N>((const Cx<float>*)J.src, (float*)J.dst, J.lines, (const Cx<float>*)J.ax.tw, q.b);
+}
+template <int N>
+__global__ void __launch_bounds__(FFT_THREADS) kb_p2_z_r2c(const FFTJob* __restrict__ jobs,
+                                                           const int* __restrict__ offs, int nj) {
+    const FFTBlock q = fft_block(offs, nj);
+    const FFTJob& J = jobs[q.j];
+    p2_z_r2c_body<N>((const float*)J.src, (Cx<float>*)J.dst, J.lines, (const Cx<float>*)J.ax.tw, q.b);
 }
 
 // Raises kernel FN's dynamic shared-memory limit to the device's opt-in maximum, once per device,
@@ -434,27 +721,64 @@ size_t fft_smem_bytes(int N, int elem_bytes) {
 // power of two up to 1024 (NC = N) and the mixed-radix kernel otherwise (NC = 0).
 enum PassKind { PASS_STRIDED, PASS_Z_C2R, PASS_Z_R2C };
 
+// FP32 power-of-two lengths 16 .. 1024: the register-resident passes.
+template <int N>
+cudaError_t run_p2_pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, int64_t inner, int64_t outer,
+                        int dir, cudaStream_t st) {
+    using P = P2<N>;
+    const Cx<float>* tw = (const Cx<float>*)ax.tw;
+    cudaError_t e;
+    if (kind == PASS_STRIDED) {
+        const int64_t nlines = inner * outer;
+        const unsigned blocks = (unsigned)((nlines + P::NL - 1) / P::NL);
+        if (dir > 0) {
+            if ((e = set_smem<k_p2_strided<N, 1>>(P::SMEM_STRIDED)) != cudaSuccess) return e;
+            k_p2_strided<N, 1><<<blocks, FFT_THREADS, P::SMEM_STRIDED, st>>>((const Cx<float>*)src, (Cx<float>*)dst,
+                                                                              inner, nlines, tw);
+        } else {
+            if ((e = set_smem<k_p2_strided<N, -1>>(P::SMEM_STRIDED)) != cudaSuccess) return e;
+            k_p2_strided<N, -1><<<blocks, FFT_THREADS, P::SMEM_STRIDED, st>>>((const Cx<float>*)src, (Cx<float>*)dst,
+                                                                               inner, nlines, tw);
+        }
+    } else {
+        const unsigned blocks = (unsigned)((outer + P::NL - 1) / P::NL);
+        if (kind == PASS_Z_C2R) {
+            if ((e = set_smem<k_p2_z_c2r<N>>(P::SMEM_Z)) != cudaSuccess) return e;
+            k_p2_z_c2r<N><<<blocks, FFT_THREADS, P::SMEM_Z, st>>>((const Cx<float>*)src, (float*)dst, outer, tw);
+        } else {
+            if ((e = set_smem<k_p2_z_r2c<N>>(P::SMEM_Z)) != cudaSuccess) return e;
+            k_p2_z_r2c<N><<<blocks, FFT_THREADS, P::SMEM_Z, st>>>((const float*)src, (Cx<float>*)dst, outer, tw);
+        }
+    }
+    return cudaGetLastError();
+}
+
 template <class R, int NC>
 cudaError_t run_pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, int64_t inner, int64_t outer,
                      int Nzh, int dir, cudaStream_t st) {
-    const int N = ax.N;
-    const int nl = lines_per_block(N);
-    const size_t sm = fft_smem_bytes(N, sizeof(Cx<R>));
-    cudaError_t e;
-    if (kind == PASS_STRIDED) {
-        if ((e = set_smem<k_fft_strided<R, NC>>(sm)) != cudaSuccess) return e;
-        const int64_t blocks = outer * ((inner + nl - 1) / nl);
-        k_fft_strided<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((Cx<R>*)dst, ax, inner, dir);
-    } else if (kind == PASS_Z_C2R) {
-        if ((e = set_smem<k_fft_z_c2r<R, NC>>(sm)) != cudaSuccess) return e;
-        const int64_t blocks = (outer + nl - 1) / nl;
-        k_fft_z_c2r<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const Cx<R>*)src, (R*)dst, ax, Nzh, outer);
+    if constexpr (std::is_same<R, float>::value && p2_reg(NC)) {
+        return run_p2_pass<NC>(kind, src, dst, ax, inner, outer, dir, st);
     } else {
-        if ((e = set_smem<k_fft_z_r2c<R, NC>>(sm)) != cudaSuccess) return e;
-        const int64_t blocks = (outer + nl - 1) / nl;
-        k_fft_z_r2c<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const R*)src, (Cx<R>*)dst, ax, Nzh, outer);
+        const int N = ax.N;
+        const int nl = lines_per_block(N);
+        const size_t sm = fft_smem_bytes(N, sizeof(Cx<R>));
+        cudaError_t e;
+        if (kind == PASS_STRIDED) {
+            if ((e = set_smem<k_fft_strided<R, NC>>(sm)) != cudaSuccess) return e;
+            const int64_t blocks = outer * ((inner + nl - 1) / nl);
+            k_fft_strided<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const Cx<R>*)src, (Cx<R>*)dst, ax, inner,
+                                                                              dir);
+        } else if (kind == PASS_Z_C2R) {
+            if ((e = set_smem<k_fft_z_c2r<R, NC>>(sm)) != cudaSuccess) return e;
+            const int64_t blocks = (outer + nl - 1) / nl;
+            k_fft_z_c2r<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const Cx<R>*)src, (R*)dst, ax, Nzh, outer);
+        } else {
+            if ((e = set_smem<k_fft_z_r2c<R, NC>>(sm)) != cudaSuccess) return e;
+            const int64_t blocks = (outer + nl - 1) / nl;
+            k_fft_z_r2c<R, NC><<<(unsigned)blocks, FFT_THREADS, sm, st>>>((const R*)src, (Cx<R>*)dst, ax, Nzh, outer);
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 template <class R>
@@ -477,22 +801,47 @@ cudaError_t pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, i
 template <int NC>
 cudaError_t run_batch_pass(int kind, const FFTJob* jobs, const int* offs, int nj, int total, int N, int dir,
                            cudaStream_t st) {
-    const size_t sm = fft_smem_bytes(N, sizeof(Cx<float>));
     cudaError_t e;
-    if (kind == FFT_STRIDED) {
-        if ((e = set_smem<kb_fft_strided<float, NC>>(sm)) != cudaSuccess) return e;
-        kb_fft_strided<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj, dir);
-    } else if (kind == FFT_Z_C2R) {
-        if ((e = set_smem<kb_fft_z_c2r<float, NC>>(sm)) != cudaSuccess) return e;
-        kb_fft_z_c2r<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj);
+    if constexpr (p2_reg(NC)) {
+        using P = P2<NC>;
+        if (kind == FFT_STRIDED) {
+            if (dir > 0) {
+                if ((e = set_smem<kb_p2_strided<NC, 1>>(P::SMEM_STRIDED)) != cudaSuccess) return e;
+                kb_p2_strided<NC, 1><<<total, FFT_THREADS, P::SMEM_STRIDED, st>>>(jobs, offs, nj);
+            } else {
+                if ((e = set_smem<kb_p2_strided<NC, -1>>(P::SMEM_STRIDED)) != cudaSuccess) return e;
+                kb_p2_strided<NC, -1><<<total, FFT_THREADS, P::SMEM_STRIDED, st>>>(jobs, offs, nj);
+            }
+        } else if (kind == FFT_Z_C2R) {
+            if ((e = set_smem<kb_p2_z_c2r<NC>>(P::SMEM_Z)) != cudaSuccess) return e;
+            kb_p2_z_c2r<NC><<<total, FFT_THREADS, P::SMEM_Z, st>>>(jobs, offs, nj);
+        } else {
+            if ((e = set_smem<kb_p2_z_r2c<NC>>(P::SMEM_Z)) != cudaSuccess) return e;
+            kb_p2_z_r2c<NC><<<total, FFT_THREADS, P::SMEM_Z, st>>>(jobs, offs, nj);
+        }
+        return cudaGetLastError();
     } else {
-        if ((e = set_smem<kb_fft_z_r2c<float, NC>>(sm)) != cudaSuccess) return e;
-        kb_fft_z_r2c<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj);
+        const size_t sm = fft_smem_bytes(N, sizeof(Cx<float>));
+        if (kind == FFT_STRIDED) {
+            if ((e = set_smem<kb_fft_strided<float, NC>>(sm)) != cudaSuccess) return e;
+            kb_fft_strided<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj, dir);
+        } else if (kind == FFT_Z_C2R) {
+            if ((e = set_smem<kb_fft_z_c2r<float, NC>>(sm)) != cudaSuccess) return e;
+            kb_fft_z_c2r<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj);
+        } else {
+            if ((e = set_smem<kb_fft_z_r2c<float, NC>>(sm)) != cudaSuccess) return e;
+            kb_fft_z_r2c<float, NC><<<total, FFT_THREADS, sm, st>>>(jobs, offs, nj);
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
 }
 
 int64_t fft_pass_blocks(int kind, const FFTJob& j) {
+    if (p2_reg(j.ax.N)) {
+        const int nl = p2_lines_per_block(j.ax.N);
+        const int64_t lines = kind == FFT_STRIDED ? j.lines * j.inner : j.lines;
+        return (lines + nl - 1) / nl;
+    }
     const int nl = lines_per_block(j.ax.N);
     if (kind == FFT_STRIDED) return j.lines * ((j.inner + nl - 1) / nl);  // lines: the outer count
     return (j.lines + nl - 1) / nl;
@@ -519,17 +868,19 @@ template <class R>
 cudaError_t launch_c2r(const Cx<R>* spec_in, Cx<R>* work, R* out, int Nx, int Ny, int Nz, const FFTAxis* ax,
                        cudaStream_t st) {
     const int Nzh = Nz / 2 + 1;
-    const int64_t nH = (int64_t)Nx * Ny * Nzh;
     cudaError_t e;
-    if (work != spec_in) {
-        e = cudaMemcpyAsync(work, spec_in, nH * sizeof(Cx<R>), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return e;
+    // x pass (stride Ny*Nzh), y pass (stride Nzh), then the real z pass; the first pass that runs reads
+    // spec_in and writes work, so spec_in is left unchanged when it differs from work.
+    const Cx<R>* cur = spec_in;
+    if (Nx > 1) {
+        if ((e = pass<R>(PASS_STRIDED, cur, work, ax[0], (int64_t)Ny * Nzh, 1, Nzh, +1, st)) != cudaSuccess) return e;
+        cur = work;
     }
-    // x pass (stride Ny*Nzh), y pass (stride Nzh), then the real z pass.
-    if (Nx > 1 && (e = pass<R>(PASS_STRIDED, work, work, ax[0], (int64_t)Ny * Nzh, 1, Nzh, +1, st)) != cudaSuccess)
-        return e;
-    if (Ny > 1 && (e = pass<R>(PASS_STRIDED, work, work, ax[1], Nzh, Nx, Nzh, +1, st)) != cudaSuccess) return e;
-    return pass<R>(PASS_Z_C2R, work, out, ax[2], 0, (int64_t)Nx * Ny, Nzh, +1, st);
+    if (Ny > 1) {
+        if ((e = pass<R>(PASS_STRIDED, cur, work, ax[1], Nzh, Nx, Nzh, +1, st)) != cudaSuccess) return e;
+        cur = work;
+    }
+    return pass<R>(PASS_Z_C2R, cur, out, ax[2], 0, (int64_t)Nx * Ny, Nzh, +1, st);
 }
 
 template <class R>

@@ -118,7 +118,8 @@ def test_meshft_adjoint_matches_oracle(label, prec, r64, r32):
 
 
 @pytest.mark.parametrize("n", [(16, 16, 16), (12, 10, 9), (8, 6, 15), (32, 24, 20), (1, 4, 8), (96, 8, 6),
-                               (14, 11, 26), (7, 13, 22), (2048, 2, 4)])
+                               (14, 11, 26), (7, 13, 22), (2048, 2, 4), (64, 128, 256), (512, 16, 32),
+                               (8, 1024, 6), (6, 4, 1024), (1, 1, 64), (1, 512, 3), (33, 256, 128)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_fft_matches_direct_definition(n, prec, r64, r32):
     r = r64 if prec == "fp64" else r32
@@ -127,9 +128,12 @@ def test_fft_matches_direct_definition(n, prec, r64, r32):
     nvec, c = oracle.half_spectrum(n)
     # oracle image definition times the box volume: unnormalised inverse on H with weights c
     ref = oracle.spectrum_to_image(X.ravel(), nvec, c, grid) * np.prod(grid.L)
-    img = r.c2r(grid, torch.as_tensor(X).cuda()).cpu().numpy()
+    Xd = torch.as_tensor(X).to(r.cplx).cuda()
+    X0 = Xd.clone()
+    img = r.c2r(grid, Xd).cpu().numpy()
     tol = 1e-12 if prec == "fp64" else 2e-6
     assert rel(img, ref) < tol
+    assert torch.equal(Xd, X0)  # the input spectrum is only read
     R = np.random.default_rng(5).normal(size=n)
     refG = np.fft.fftn(R)[nvec[:, 0] % n[0], nvec[:, 1] % n[1], nvec[:, 2] % n[2]]
     spec = r.r2c(grid, torch.as_tensor(R).cuda()).cpu().numpy().ravel()
