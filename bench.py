@@ -46,21 +46,29 @@ MUFU_PER_TERM = {"fwd": 7, "adj": 7}
 # DRAM traffic per launch of the dominant kernels (dram__bytes_read.sum + dram__bytes_write.sum from one
 # ncu capture of `python bench.py --workload W --steps 1 --warmup 3 --no-cpu-baseline --no-e2e --no-serve
 # --no-fp64`, one kernel, one launch), keyed by workload and kernel, with the SHA-256 of the mesh-transform
-# sources it was taken on: a capture of other sources is not reported (the traffic is then null).
+# sources it was taken on (comments excluded, kernel_sources_digest): a capture of other code is not
+# reported (the traffic is then null).
 MEASURED_TRAFFIC = {
-    ("c3", "k_adj_f32"): {"bytes": 146.96e6 + 72.33e6, "sources": "4a40b4fe552abdcc"},
-    ("c3", "k_fwd_f32"): {"bytes": 2.70e6 + 9.43e6, "sources": "4a40b4fe552abdcc"},
+    ("c3", "k_adj_f32"): {"bytes": 146.96e6 + 72.33e6, "sources": "74bf4f20cf7c95ca"},
+    ("c3", "k_fwd_f32"): {"bytes": 2.70e6 + 9.43e6, "sources": "74bf4f20cf7c95ca"},
 }
 TRAFFIC_SOURCES = ("meshft_f32.cu", "meshft_math.cuh", "dm_kernels.cuh", "dm_common.cuh")
 
 
 def kernel_sources_digest() -> str:
+    """SHA-256 (first 16 hex digits) of the mesh-transform sources with their comments and blank lines
+    removed, so that an edit of a comment keeps a capture valid and any edit of the code does not."""
     import hashlib
+    import re
 
     h = hashlib.sha256()
     for name in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, "paper_2303_10440_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2303_10440_b300", "csrc", name), encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 
