@@ -140,6 +140,29 @@ def test_fft_matches_direct_definition(n, prec, r64, r32):
     assert rel(spec, refG) < tol
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_c2r_into_the_buffer_that_holds_the_spectrum(prec, r64, r32):
+    """dm_c2r with the image written over its own input spectrum (one buffer): the spectrum is then
+    copied into the workspace before the passes instead of being read in place."""
+    import ctypes
+
+    from paper_2303_10440_b300.api import _grid
+
+    r = r64 if prec == "fp64" else r32
+    n = (32, 16, 64)
+    grid = synth.Grid(n=n, h=(1, 1, 1))
+    X = synth.random_half_spectrum(n, seed=8)
+    nvec, c = oracle.half_spectrum(n)
+    ref = oracle.spectrum_to_image(X.ravel(), nvec, c, grid) * np.prod(grid.L)
+    Xd = torch.as_tensor(X).to(r.cplx).cuda().contiguous()
+    g = _grid(grid)
+    st = r.lib.dm_c2r(r.ctx, ctypes.byref(g), Xd.data_ptr(), Xd.data_ptr(), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    img = Xd.view(r.real).ravel()[: int(np.prod(n))].reshape(n).cpu().numpy()
+    assert rel(img, ref) < (1e-12 if prec == "fp64" else 2e-6)
+
+
 def test_fft_longest_axes_and_refused_lengths(r64, r32):
     """An FP32 axis of 4096 (the longest; the FP64 lines of that length do not fit in shared memory and are
     refused), and a length with the prime factor 17 (refused by both paths)."""
