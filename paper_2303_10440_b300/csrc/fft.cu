@@ -109,11 +109,15 @@ __device__ __forceinline__ void dft_prime(Cx<R>* v, int dir) {
     for (int m = 0; m < P; ++m) v[m] = y[m];
 }
 
-// Largest radix a stage may take (fft_factor's radices: 2, 3, 4, 5, 7, 11, 13; 8 in the power-of-two path).
-constexpr int MAX_RADIX = 13;
+// Largest radix a stage may take: fft_factor's radices are 2, 3, 4, 5 and, for lengths with such a
+// factor, 7, 11, 13 (BIG); the power-of-two path also takes 8. A mixed-radix kernel that may meet 7-13
+// holds 13 values per butterfly and every prime DFT, which takes its registers from 46 to 119: lengths
+// without those factors run a kernel compiled without them.
+template <bool BIG>
+__host__ __device__ constexpr int max_radix() { return BIG ? 13 : 5; }
 
-// y[m] = sum_q v[q] exp(dir 2 pi i q m / r), in place.
-template <class R>
+// y[m] = sum_q v[q] exp(dir 2 pi i q m / r), in place (r = 7, 11, 13 only when BIG).
+template <class R, bool BIG>
 __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
     if (r == 2) {
         const Cx<R> a = v[0], b = v[1];
@@ -147,12 +151,12 @@ __device__ __forceinline__ void small_dft(Cx<R>* v, int r, int dir) {
         v[6] = {e[2].x - t2.x, e[2].y - t2.y};
         v[3] = {e[3].x + t3.x, e[3].y + t3.y};
         v[7] = {e[3].x - t3.x, e[3].y - t3.y};
-    } else if (r == 7) {
-        dft_prime<R, 7>(v, dir);
-    } else if (r == 11) {
-        dft_prime<R, 11>(v, dir);
-    } else if (r == 13) {
-        dft_prime<R, 13>(v, dir);
+    } else if (BIG && r == 7) {
+        if constexpr (BIG) dft_prime<R, 7>(v, dir);
+    } else if (BIG && r == 11) {
+        if constexpr (BIG) dft_prime<R, 11>(v, dir);
+    } else if (BIG && r == 13) {
+        if constexpr (BIG) dft_prime<R, 13>(v, dir);
     } else {  // r == 5: direct 5-point DFT
         const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
         const R s1 = (R)0.95105651629515357212 * (R)dir, s2 = (R)0.58778525229247312917 * (R)dir;
@@ -182,8 +186,9 @@ __host__ __device__ constexpr int lines_per_block(int N) { return 2048 / N > 16 
 __host__ __device__ constexpr int line_stride(int nl) { return nl + 1; }
 
 // Stockham FFT of `nl` lines of length N stored as a[k * LS + line]; returns the buffer holding the result.
-template <class R>
+template <class R, bool BIG>
 __device__ Cx<R>* fft_lines(Cx<R>* a, Cx<R>* b, const FFTAxis ax, int LS, int nl, int dir) {
+    constexpr int MAX_RADIX = max_radix<BIG>();
     const Cx<R>* tw = (const Cx<R>*)ax.tw;
     const int N = ax.N;
     int Ns = 1;
@@ -203,7 +208,7 @@ __device__ Cx<R>* fft_lines(Cx<R>* a, Cx<R>* b, const FFTAxis ax, int LS, int nl
                 for (int q = 1; q < MAX_RADIX; ++q)
                     if (q < r) v[q] = cmul(v[q], twiddle(tw, q * k * tstride, dir));
             }
-            small_dft(v, r, dir);
+            small_dft<R, BIG>(v, r, dir);
             const int base = (j / Ns) * Ns * r + k;
 #pragma unroll
             for (int q = 0; q < MAX_RADIX; ++q)
@@ -240,7 +245,7 @@ __device__ __forceinline__ Cx<R>* stockham_p2(Cx<R>* a, Cx<R>* b, const Cx<R>* t
 #pragma unroll
                 for (int q = 1; q < r; ++q) v[q] = cmul(v[q], twiddle(tw, q * k * tstride, dir));
             }
-            small_dft(v, r, dir);
+            small_dft<R, false>(v, r, dir);
             const int base = (j / NS) * NS * r + k;
 #pragma unroll
             for (int q = 0; q < r; ++q) b[(base + q * NS) * LS + line] = v[q];
@@ -250,13 +255,15 @@ __device__ __forceinline__ Cx<R>* stockham_p2(Cx<R>* a, Cx<R>* b, const Cx<R>* t
     }
 }
 
-// Line transform: the compile-time power-of-two path when NC != 0, else the mixed-radix one.
+// Line transform: the compile-time power-of-two path when NC > 0, else the mixed-radix one (NC = 0:
+// radices up to 5; NC = NC_BIG: also 7, 11, 13).
+constexpr int NC_BIG = -1;
 template <class R, int NC>
 __device__ __forceinline__ Cx<R>* transform_lines(Cx<R>* a, Cx<R>* b, const FFTAxis& ax, int LS, int nl, int dir) {
-    if constexpr (NC != 0)
+    if constexpr (NC > 0)
         return stockham_p2<R, NC, lines_per_block(NC), 1>(a, b, (const Cx<R>*)ax.tw, dir);
     else
-        return fft_lines<R>(a, b, ax, LS, nl, dir);
+        return fft_lines<R, NC == NC_BIG>(a, b, ax, LS, nl, dir);
 }
 
 // Complex transform of all lines along an axis with element stride `inner`:
@@ -265,7 +272,7 @@ template <class R, int NC>
 __device__ __forceinline__ void k_fft_strided_body(const Cx<R>* src, Cx<R>* dst, const FFTAxis ax, int64_t inner,
                                                    int dir, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = NC ? NC : ax.N;
+    const int N = NC > 0 ? NC : ax.N;
     const int nl = lines_per_block(N);
     const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
@@ -299,8 +306,8 @@ template <class R, int NC>
 __device__ __forceinline__ void k_fft_z_c2r_body(const Cx<R>* spec, R* out, const FFTAxis ax, int Nzh_,
                                                            int64_t nlines, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = NC ? NC : ax.N;
-    const int Nzh = NC ? NC / 2 + 1 : Nzh_;
+    const int N = NC > 0 ? NC : ax.N;
+    const int Nzh = NC > 0 ? NC / 2 + 1 : Nzh_;
     const int nl = lines_per_block(N);
     const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
@@ -333,8 +340,8 @@ template <class R, int NC>
 __device__ __forceinline__ void k_fft_z_r2c_body(const R* in, Cx<R>* spec, const FFTAxis ax, int Nzh_,
                                                            int64_t nlines, int64_t blk, int64_t nblk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N = NC ? NC : ax.N;
-    const int Nzh = NC ? NC / 2 + 1 : Nzh_;
+    const int N = NC > 0 ? NC : ax.N;
+    const int Nzh = NC > 0 ? NC / 2 + 1 : Nzh_;
     const int nl = lines_per_block(N);
     const int LS = line_stride(nl);
     Cx<R>* a = (Cx<R>*)smem_raw;
@@ -712,13 +719,21 @@ bool fft_factor(int N, FFTAxis& a) {
     return n == 1;
 }
 
+// Whether an axis's factorisation uses a radix above 5 (the NC_BIG kernels).
+static bool has_big_radix(const FFTAxis& a) {
+    for (int f = 0; f < a.nf; ++f)
+        if (a.radix[f] > 5) return true;
+    return false;
+}
+
 size_t fft_smem_bytes(int N, int elem_bytes) {
     const int nl = lines_per_block(N);
     return (size_t)2 * N * line_stride(nl) * elem_bytes;
 }
 
-// One pass over every line of an axis, with the kernel instantiated for the line length when it is a
-// power of two up to 1024 (NC = N) and the mixed-radix kernel otherwise (NC = 0).
+// One pass over every line of an axis: for FP32 power-of-two lengths 16 .. 1024 the register-resident
+// kernels, for other powers of two up to 4096 the Stockham kernel instantiated for the length (NC = N),
+// otherwise the mixed-radix kernel (NC = 0, or NC_BIG when the length has a factor 7, 11 or 13).
 enum PassKind { PASS_STRIDED, PASS_Z_C2R, PASS_Z_R2C };
 
 // FP32 power-of-two lengths 16 .. 1024: the register-resident passes.
@@ -794,7 +809,9 @@ cudaError_t pass(PassKind kind, const void* src, void* dst, const FFTAxis& ax, i
         case 1024: return run_pass<R, 1024>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         case 2048: return run_pass<R, 2048>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
         case 4096: return run_pass<R, 4096>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
-        default: return run_pass<R, 0>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
+        default:
+            return has_big_radix(ax) ? run_pass<R, NC_BIG>(kind, src, dst, ax, inner, outer, Nzh, dir, st)
+                                     : run_pass<R, 0>(kind, src, dst, ax, inner, outer, Nzh, dir, st);
     }
 }
 
@@ -860,7 +877,12 @@ cudaError_t launch_fft_batch(int kind, int N, const FFTJob* jobs, const int* off
         case 1024: return run_batch_pass<1024>(kind, jobs, offsets, nj, total, N, dir, st);
         case 2048: return run_batch_pass<2048>(kind, jobs, offsets, nj, total, N, dir, st);
         case 4096: return run_batch_pass<4096>(kind, jobs, offsets, nj, total, N, dir, st);
-        default: return run_batch_pass<0>(kind, jobs, offsets, nj, total, N, dir, st);
+        default: {
+            FFTAxis f;
+            if (!fft_factor(N, f)) return cudaErrorInvalidValue;
+            return has_big_radix(f) ? run_batch_pass<NC_BIG>(kind, jobs, offsets, nj, total, N, dir, st)
+                                    : run_batch_pass<0>(kind, jobs, offsets, nj, total, N, dir, st);
+        }
     }
 }
 

@@ -94,6 +94,41 @@ def test_served_fit_matches_the_standalone_fit(setup):
         assert np.allclose(res[k].loss_history, hist.numpy(), rtol=1e-4)
 
 
+def test_served_fit_on_a_grid_with_factors_7_11_13(setup):
+    """A job on a 28 x 26 x 22 grid (the batched FFT passes with radices 7, 13 and 11) served next to a
+    power-of-two job: alone and in the mix bit for bit, and close to the standalone fit."""
+    from paper_2303_10440_b300.serve import FitServer
+
+    r32, jobs = setup
+    grid = synth.Grid(n=(28, 26, 22), h=(0.5, 0.5, 1.0))
+    R = 0.3 * float(min(grid.L))
+    V_t, F = synth.sh_deformed_sphere(2, R, grid.center, lmax=4, coef_sigma=0.04 * R, seed=47)
+    V0, _ = synth.sphere_mesh(2, R, grid.center)
+    psf = synth.Psf(sigma=(0.4, 0.4, 0.9), band_tau=1e-3)
+    T = r32.render(torch.as_tensor(V_t).cuda(), torch.as_tensor(F).cuda(), grid, psf).cpu().numpy()
+    job = dict(V=V0, F=F, target=T, grid=grid, psf=psf, steps=STEPS, lr_vertex=0.02)
+    s1 = FitServer(max_jobs=4)
+    i = s1.submit(**job)
+    assert s1.wait(i, timeout=300)
+    alone = s1.result(i)
+    s1.shutdown()
+    s2 = FitServer(max_jobs=4)
+    ids = [s2.submit(**jobs[1]), s2.submit(**job)]
+    for k in ids:
+        assert s2.wait(k, timeout=300)
+    mix = s2.result(ids[1])
+    s2.shutdown()
+    assert np.array_equal(alone.V, mix.V)
+    assert np.array_equal(alone.loss_history, mix.loss_history)
+    Vf, _, hist = r32.fit(torch.as_tensor(V0).cuda(), torch.as_tensor(F).cuda(), grid, psf, torch.as_tensor(T).cuda(),
+                          steps=STEPS, lr_vertex=job["lr_vertex"])
+    Vf = Vf.cpu().numpy()
+    moved = np.linalg.norm(Vf - V0)
+    assert moved > 0
+    assert np.linalg.norm(alone.V - Vf) < 1e-3 * moved
+    assert np.allclose(alone.loss_history, hist.numpy(), rtol=1e-4)
+
+
 def test_late_arrivals_join_running_batches(setup):
     from paper_2303_10440_b300.serve import FitServer
 
